@@ -1,0 +1,312 @@
+#!/usr/bin/env python
+"""Benchmark: RNS-CKKS public-key encryptions per second on GB300, vanilla
+(Eq. 8) and Zinc (Algorithm 1), at N = 2^14 (60 + 6 x 50 + 60-bit chain,
+Delta = 2^50, 4096 vectors of 8192 slots U[-1, 1]) by default.
+
+One step = encrypt the whole batch once with vanilla CKKS and once with Zinc
+(encoding, sampling, NTTs and the key multiply-add / cache add all inside),
+inputs resident in HBM.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+  python bench.py --impl reference ...   (the CPU oracle on a bounded sample)
+
+Multi-GPU: one process per GPU (torchrun); every rank runs an independent
+replica on its own ct_index range (no collective on the data path).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2408_07304_gb300 import workloads  # noqa: E402
+
+METRIC = "encryptions/s, vanilla CKKS vs Zinc, at N=2^14, 1 GB300; HBM roofline %; p99 ms"
+UNIT = "encryptions/s"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        try:
+            with open(self.path) as f:
+                for ln in f:
+                    p = [x.strip() for x in ln.split(",")]
+                    if len(p) >= 9:
+                        rows.append(p)
+            os.unlink(self.path)
+        except Exception:
+            return None
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------- CPU oracle
+def oracle_sample(w, reps=1):
+    """Time the CPU oracle on a bounded sample of workload `w`: prime 0 of one
+    vanilla and one Zinc ciphertext (encode, sampling, schoolbook products,
+    definitional NTT of both components).  Returns (seconds per sample,
+    threads used, description)."""
+    from oracle import ckks as O
+    from oracle import ring
+    P1 = O.Params(w.log_n, w.bits[:1], w.log2_delta)       # same first prime as the full chain
+    K = O.keygen(P1, workloads.KEYGEN_SEED)
+    zero = O.zinc_precompute_coeff(P1, K, workloads.CACHE_SEED)
+    z = workloads.slots(w, batch=1)[0]
+    t0 = time.perf_counter()
+    for r in range(reps):
+        O.ct_ntt(P1, O.encrypt_coeff(P1, K, z, w.seed, r))
+        O.ct_ntt(P1, O.zinc_encrypt_coeff(P1, zero, z, w.seed, r))
+    dt = (time.perf_counter() - t0) / reps
+    desc = (f"prime 0 of {w.L} of one vanilla + one Zinc ciphertext at N={w.n} (all residues of that prime), "
+            f"scaled x{w.L} to whole ciphertexts")
+    return dt, ring.threads(), desc
+
+
+def run_reference(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_sample(w)
+    times = []
+    for _ in range(args.steps):
+        dt, cores, desc = oracle_sample(w)
+        times.append(dt)
+    per_step = sum(times) / len(times)
+    value = 2.0 / (per_step * w.L)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic", "config": {"workload": w.describe(), "parallelism": "cpu oracle"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def modmuls_per_ct(w, zinc):
+    """Shoup multiplications per ciphertext: (N/2) log2 N per NTT, 3 NTTs and
+    2 key products per prime (vanilla) or 2 NTTs (Zinc)."""
+    ntt = (w.n // 2) * w.log_n
+    return w.L * (2 * ntt if zinc else 3 * ntt + 2 * w.n)
+
+
+def run_ours(args, w):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2408_07304_gb300 import api
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    ctx = api.Context(w.log_n, w.bits, w.log2_delta, device=local)
+    sk, pk = api.ckks_keygen(ctx, workloads.KEYGEN_SEED)
+    zc = api.zinc_precompute(ctx, pk, workloads.CACHE_SEED)
+    B = w.batch
+    z = workloads.slots(w, batch=B, first=rank * B)
+    slots = torch.tensor(z, dtype=torch.float64, device=dev)
+    idx = torch.arange(rank * B, (rank + 1) * B, dtype=torch.int64, device=dev)
+    out_v = torch.empty((B, 2, w.L, w.n), dtype=torch.int64, device=dev)
+    out_z = torch.empty_like(out_v)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        api.ckks_encrypt(ctx, pk, slots, w.seed, idx, out=out_v, stream=stream)
+        api.zinc_encrypt(ctx, zc, slots, w.seed, idx, out=out_z, stream=stream)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    api.zn_sync_status(ctx, stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+
+    # ---- device-timed steps (inputs resident in HBM)
+    api.zn_timing_enable(ctx, True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps + 1)]
+    torch.cuda.synchronize(dev)
+    barrier()
+    evs[0].record(stream)
+    for k in range(args.steps):
+        api.ckks_encrypt(ctx, pk, slots, w.seed, idx, out=out_v, stream=stream)
+        evs[2 * k + 1].record(stream)
+        api.zinc_encrypt(ctx, zc, slots, w.seed, idx, out=out_z, stream=stream)
+        evs[2 * k + 2].record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    clk = clocks.stop()
+    total_ms = evs[0].elapsed_time(evs[-1])
+    van_ms = sum(evs[2 * k].elapsed_time(evs[2 * k + 1]) for k in range(args.steps))
+    zin_ms = sum(evs[2 * k + 1].elapsed_time(evs[2 * k + 2]) for k in range(args.steps))
+    enc_ms, enc_n = api.zn_timing_read(ctx, api.TIME_ENCODE)
+    kv_ms, kv_n = api.zn_timing_read(ctx, api.TIME_ENCRYPT)
+    kz_ms, kz_n = api.zn_timing_read(ctx, api.TIME_ZINC)
+    api.zn_timing_enable(ctx, False)
+    api.zn_sync_status(ctx, stream)
+    launches = enc_n + kv_n + kz_n
+
+    t = torch.tensor([total_ms, van_ms, zin_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms, van_ms, zin_ms = [float(x) for x in t.tolist()]
+    cts = 2 * B * world * args.steps
+    value = cts / (total_ms / 1e3)
+    van_rate = B * world * args.steps / (van_ms / 1e3)
+    zin_rate = B * world * args.steps / (zin_ms / 1e3)
+
+    # ---- roofline of the dominant kernel (the vanilla encrypt kernel)
+    hbm_peak, peak_src = peaks()
+    ct_bytes = 2 * w.L * w.n * 8
+    per_ct_bytes = ct_bytes + w.n_slots * 8
+    chunk_cts = B * args.steps / max(kv_n, 1)
+    kv_avg = kv_ms / max(kv_n, 1)
+    kz_avg = kz_ms / max(kz_n, 1)
+    dom_is_vanilla = kv_ms >= kz_ms
+    avg = kv_avg if dom_is_vanilla else kz_avg
+    achieved = chunk_cts * ct_bytes / (avg / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": None,
+                "kernel": "k_encrypt<14,vanilla>" if dom_is_vanilla else "k_encrypt<14,zinc>",
+                "peak_source": peak_src,
+                "modmul_rate_G": chunk_cts * modmuls_per_ct(w, not dom_is_vanilla) / (avg / 1e3) / 1e9}
+
+    # ---- end to end: host slots in, host ciphertexts out (pinned), per step
+    e2e = None
+    if not args.no_e2e:
+        e2e_steps = max(1, min(args.steps, 3))
+        host_slots = torch.tensor(z, dtype=torch.float64).pin_memory()
+        host_v = torch.empty(out_v.shape, dtype=torch.int64, pin_memory=True)
+        host_z = torch.empty(out_z.shape, dtype=torch.int64, pin_memory=True)
+        torch.cuda.synchronize(dev)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(e2e_steps):
+            slots.copy_(host_slots, non_blocking=True)
+            api.ckks_encrypt(ctx, pk, slots, w.seed, idx, out=out_v, stream=stream)
+            host_v.copy_(out_v, non_blocking=True)
+            api.zinc_encrypt(ctx, zc, slots, w.seed, idx, out=out_z, stream=stream)
+            host_z.copy_(out_z, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        t = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+        e2e = {"value": 2 * B * world * e2e_steps / (e2e_ms / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": int(host_slots.numel() * 8),
+               "d2h_bytes_per_step": int(2 * host_v.numel() * 8),
+               "steps": e2e_steps}
+        del host_v, host_z
+
+    # ---- CPU baseline: the oracle on a bounded sample (rank 0, one GPU only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        dt, cores, desc = oracle_sample(w)
+        cpu = {"value": 2.0 / (dt * w.L), "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": f"{w.name}: {w.describe()}", "global_batch": 2 * B * world,
+                       "parallelism": f"replicas x{world}",
+                       "l2": "working set above L2: slots 256 MiB read and 16 GiB of ciphertexts written per step"
+                             if w.name == "throughput" else "see workload"},
+            "vanilla_enc_s": van_rate, "zinc_enc_s": zin_rate, "zinc_speedup": zin_rate / van_rate,
+            "hbm_roofline_frac": value * per_ct_bytes / (hbm_peak * 1e9),
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "kernel_ms_per_launch": {"encode": enc_ms / max(enc_n, 1), "encrypt_vanilla": kv_avg,
+                                     "encrypt_zinc": kz_avg},
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="throughput", choices=sorted(workloads.WORKLOADS))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    w = workloads.WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_ours(args, w)
+
+
+if __name__ == "__main__":
+    main()

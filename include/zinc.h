@@ -1,0 +1,206 @@
+/*
+ * zinc.h — C ABI of the GB300 (sm_103a) RNS-CKKS encryption library:
+ * vanilla CKKS public-key encryption and the Zinc cached-ciphertext
+ * encryption of arXiv 2408.07304.
+ *
+ * Conventions for every entry point
+ * ---------------------------------
+ *  - Return value: ZN_OK (0) or a negative ZN_E* status; zn_strerror() names it.
+ *  - Pointers marked "device" are CUDA device pointers owned by the caller
+ *    (e.g. torch tensors' data_ptr()); "host" pointers are ordinary host memory.
+ *    The library never frees caller memory.  Handles (zn_ctx, zn_sk, zn_pk,
+ *    zn_zcache) are owned by the library and released by their destroy call.
+ *  - Work is enqueued on the caller's cudaStream_t (passed as void*, 0 = the
+ *    legacy default stream) and is asynchronous unless stated otherwise.
+ *    Errors detected on the device (encode overflow) are latched in a status
+ *    word of the context and reported by zn_sync_status().
+ *  - Layouts (all residues are uint64 in [0, q_i), NTT form, bit-reversed
+ *    evaluation order unless stated):
+ *      plaintext coefficients  int64  [B][N]
+ *      ciphertext              uint64 [B][2][L][N]   (c0 = message part, c1)
+ *      public key / Zinc cache uint64 [2][L][N]
+ *    where N = 2^log_n is the ring degree and L the number of RNS primes.
+ *  - The paper writes the ciphertext as (c_1, c_2) and the public key as
+ *    (pk_1, pk_2); here they are (c0, c1) and (pk0, pk1).
+ *  - Sampling is counter based (Philox4x32-10 keyed by the seed, counter =
+ *    (block, domain<<24 | poly<<16 | prime, lo32 ct_index, hi32 ct_index)),
+ *    so a ciphertext depends only on (key, seed, ct_index, message), never on
+ *    its batch position or the launch shape.
+ */
+#ifndef ZINC_H
+#define ZINC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ZN_MAX_PRIMES 16
+
+enum {
+  ZN_OK = 0,
+  ZN_EINVAL = -1,     /* invalid argument or parameter set */
+  ZN_ENOMEM = -2,     /* device allocation failed or HBM budget exceeded */
+  ZN_EOVERFLOW = -3,  /* an encoded coefficient reached |m_k| >= 2^62 (or was not finite) */
+  ZN_ECUDA = -4,      /* a CUDA runtime call failed */
+  ZN_ETIMEOUT = -5,   /* a bounded device wait gave up */
+  ZN_ENOPRIME = -6    /* no prime q < 2^b with q = 1 mod 2N is left for a chain entry */
+};
+
+typedef struct zn_ctx zn_ctx;
+typedef struct zn_sk zn_sk;
+typedef struct zn_pk zn_pk;
+typedef struct zn_zcache zn_zcache;
+
+/* Parameter set.  log_n in [4, 15]; n_primes in [1, ZN_MAX_PRIMES];
+ * prime_bits[i] in [20, 61]; log2_delta in [1, 62].  The error distribution
+ * chi is fixed by the paper (Section "Polynomials and Distributions"):
+ * discrete Gaussian with sigma = 3.2, read as the rounded normal truncated to
+ * [-19, 19]. */
+typedef struct {
+  uint32_t log_n;
+  uint32_t n_primes;
+  uint32_t prime_bits[ZN_MAX_PRIMES];
+  uint32_t log2_delta;
+} zn_params;
+
+/* ---------------------------------------------------------------- context */
+
+/* Build the prime chain (for each entry b: the largest unused prime q < 2^b,
+ * q = 1 mod 2N), the minimal primitive 2N-th roots psi_i, the NTT twiddle and
+ * Shoup tables and the encoder twiddles, and upload them to `device`
+ * (synchronous).  The paper takes the modulus from SEAL (Section "System
+ * Implementation"); the chain rule is this library's reading. */
+int zn_ctx_create(const zn_params* params, int device, zn_ctx** out);
+void zn_ctx_destroy(zn_ctx* ctx);
+
+/* Copy the chain to host arrays of n_primes entries (either may be NULL). */
+int zn_ctx_primes(const zn_ctx* ctx, uint64_t* primes, uint64_t* psis);
+
+/* Read and clear the device status word after synchronising `stream`;
+ * returns ZN_OK, ZN_EOVERFLOW, ZN_ETIMEOUT or ZN_ECUDA. */
+int zn_sync_status(zn_ctx* ctx, void* stream);
+
+const char* zn_strerror(int status);
+
+/* ------------------------------------------------------------------ Gen */
+
+/* Gen, paper Eq. 7: sk = s <- R_2, a <- R_q, e <- chi;
+ * pk0 = -a*s + e, pk1 = a (NTT form).  Sampling domain 2, ct_index 0.
+ * Synchronous. */
+int ckks_keygen(zn_ctx* ctx, uint64_t seed, zn_sk** sk, zn_pk** pk);
+void zn_sk_destroy(zn_sk* sk);
+void zn_pk_destroy(zn_pk* pk);
+
+/* Export / import (checkpointing).  pk: host uint64 [2][L][N] NTT form.
+ * sk: host int8 [N] ternary coefficients.  Imports rebuild the NTT and Shoup
+ * forms on the device (synchronous). */
+int zn_pk_export(const zn_pk* pk, uint64_t* host_out);
+int zn_pk_import(zn_ctx* ctx, const uint64_t* host_in, zn_pk** out);
+int zn_sk_export(const zn_sk* sk, int8_t* host_out);
+int zn_sk_import(zn_ctx* ctx, const int8_t* host_in, zn_sk** out);
+
+/* --------------------------------------------------------------- encode */
+
+/* CKKS encoding (canonical embedding; the paper assumes a pre-encoded message,
+ * Section "Construction").  slots: device double [batch][n_slots] (real
+ * slots; slots n_slots..N/2-1 are zero); out: device int64 [batch][N],
+ * m_k = rint(2^(log2_delta+1-log_n) * Re sum_j z_j zeta^(-5^j k)), computed by
+ * a radix-2 FP64 FFT with a fixed IEEE operation order (bit-reproducible).
+ * n_slots <= N/2.  Overflow (|m_k| >= 2^62) is latched for zn_sync_status. */
+int ckks_encode(zn_ctx* ctx, const double* slots, uint32_t n_slots, uint32_t batch,
+                int64_t* out, void* stream);
+
+/* -------------------------------------------------------------- encrypt */
+
+/* Vanilla public-key encryption, paper Eq. 8 (second component with pk1):
+ * u <- R_2, e0, e1 <- chi (domain 0, keyed by seed and ct_index[b]);
+ * c0 = pk0*u + e0 + m, c1 = pk1*u + e1 (mod each q_i), NTT form.
+ * slots: device double [batch][n_slots]; ct_index: device uint64 [batch];
+ * ct: device uint64 [batch][2][L][N].  May grow the context's encode scratch
+ * (a cudaMalloc) when batch exceeds what earlier calls used. */
+int ckks_encrypt(zn_ctx* ctx, const zn_pk* pk, const double* slots, uint32_t n_slots,
+                 uint32_t batch, uint64_t seed, const uint64_t* ct_index, uint64_t* ct,
+                 void* stream);
+
+/* Zinc precomputation (Section "Precomputation"): cache one Enc(0) — a vanilla
+ * encryption of the zero plaintext under pk with sampling domain 3,
+ * ct_index 0.  Synchronous. */
+int zinc_precompute(zn_ctx* ctx, const zn_pk* pk, uint64_t seed, zn_zcache** out);
+void zn_zcache_destroy(zn_zcache* zc);
+/* Cache export / import: host uint64 [2][L][N] NTT form. */
+int zn_zcache_export(const zn_zcache* zc, uint64_t* host_out);
+int zn_zcache_import(zn_ctx* ctx, const uint64_t* host_in, zn_zcache** out);
+
+/* Zinc encryption, paper Algorithm 1 / Eq. 9: c = zero + m; e1', e2' <- chi
+ * (domain 1, keyed by seed and ct_index[b]); c' = (c0 + e1', c1 + e2').
+ * Arguments as ckks_encrypt, with the cache in place of the public key. */
+int zinc_encrypt(zn_ctx* ctx, const zn_zcache* zc, const double* slots, uint32_t n_slots,
+                 uint32_t batch, uint64_t seed, const uint64_t* ct_index, uint64_t* ct,
+                 void* stream);
+
+/* -------------------------------------------------------------- decrypt */
+
+/* Dec, paper Eq. 10: c0 + c1*s (mod each q_i), returned in the coefficient
+ * domain.  ct: device uint64 [batch][2][L][N]; out: device uint64 [batch][L][N]. */
+int ckks_decrypt(zn_ctx* ctx, const zn_sk* sk, const uint64_t* ct, uint32_t batch,
+                 uint64_t* out, void* stream);
+
+/* Dec followed by decoding: CRT over the first two primes (one if L = 1),
+ * centred, then z_j = Delta^-1 m(zeta^(5^j)).  out: device double
+ * [batch][n_slots] (real parts).  Verification path; not tuned. */
+int ckks_decrypt_decode(zn_ctx* ctx, const zn_sk* sk, const uint64_t* ct, uint32_t batch,
+                        uint32_t n_slots, double* out, void* stream);
+
+/* Homomorphic addition (paper Eq. 2): out = a + b (mod each q_i); each
+ * device uint64 [batch][2][L][N]; out may alias a or b. */
+int ckks_add(zn_ctx* ctx, const uint64_t* a, const uint64_t* b, uint32_t batch,
+             uint64_t* out, void* stream);
+
+/* ------------------------------------------- building blocks (for tests) */
+
+/* Forward / inverse negacyclic NTT per prime, in place, on device uint64
+ * [batch][L][N] residues in [0, q_i):
+ *   ahat[i] = sum_j a_j psi^((2 brv(i) + 1) j) mod q  (RNS "DFT",
+ *   Section "Theoretical Analysis"). */
+int zn_ntt_forward(zn_ctx* ctx, uint64_t* data, uint32_t batch, void* stream);
+int zn_ntt_inverse(zn_ctx* ctx, uint64_t* data, uint32_t batch, void* stream);
+
+/* Sampler (Section "Polynomials and Distributions"): kind 0 = R_2 (ternary),
+ * 1 = chi, 2 = R_q residues for `prime`.  out: device int64 [count][N] for
+ * polynomial (domain, poly, prime) and ct_index = ct_index0 + c. */
+int zn_sample(zn_ctx* ctx, int kind, uint64_t seed, uint32_t domain, uint32_t poly,
+              uint32_t prime, uint64_t ct_index0, uint32_t count, int64_t* out, void* stream);
+
+/* ---------------------------------------------------- launch timing (bench) */
+
+/* Kernel kinds that can be timed. */
+enum { ZN_TIME_ENCODE = 0, ZN_TIME_ENCRYPT = 1, ZN_TIME_ZINC = 2, ZN_TIME_KINDS = 3 };
+
+/* on != 0: every later encode / vanilla-encrypt / Zinc-encrypt kernel launch
+ * of this context is bracketed by CUDA events recorded on its launch stream.
+ * Recording stays on until switched off; on = 0 also discards pending
+ * records. */
+int zn_timing_enable(zn_ctx* ctx, int on);
+
+/* Synchronise the recorded events of `kind`, return their summed duration
+ * (milliseconds) and launch count, and clear them. */
+int zn_timing_read(zn_ctx* ctx, int kind, double* ms, uint64_t* launches);
+
+/* ------------------------------------------------ host-side tables (no GPU) */
+
+/* The host computations behind zn_ctx_create, exposed so that they can be
+ * checked without a GPU. */
+int zn_host_primes(uint32_t log_n, const uint32_t* bits, uint32_t n_primes, uint64_t* out);
+uint64_t zn_host_psi(uint64_t q, uint32_t log_n);
+/* T[k] = cos(pi k/N) - i sin(pi k/N), k < N, each part correctly rounded. */
+int zn_host_encoder_twiddles(uint32_t log_n, double* re, double* im);
+/* The 38 chi thresholds T_j = floor(2^64 F(j - 20)), j = 1..38. */
+int zn_host_cdt(uint64_t* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ZINC_H */

@@ -1,0 +1,411 @@
+"""ctypes binding of include/zinc.h, with the same entry-point names.
+
+Argument marshalling only: every step of encoding, sampling, transforming and
+encrypting runs in the sm_103a kernels of libzinc.so.  Device buffers are
+torch CUDA tensors (uint64 residues are carried in int64 tensors, bit for
+bit); torch supplies memory and streams, nothing else.  There is no CPU
+fallback: if libzinc.so has not been built, the first call raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libzinc.so")
+MAX_PRIMES = 16
+
+ZN_OK, ZN_EINVAL, ZN_ENOMEM, ZN_EOVERFLOW, ZN_ECUDA, ZN_ETIMEOUT, ZN_ENOPRIME = 0, -1, -2, -3, -4, -5, -6
+
+# sampler kinds for zn_sample
+KIND_TERNARY, KIND_GAUSSIAN, KIND_UNIFORM = 0, 1, 2
+# sampling domains (counter word 1, bits 24..31)
+DOM_ENC, DOM_ZINC, DOM_KEYGEN, DOM_CACHE = 0, 1, 2, 3
+
+
+class ZincError(RuntimeError):
+    def __init__(self, status, what):
+        self.status = status
+        super().__init__(f"{what}: {strerror(status)} ({status})")
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("log_n", ctypes.c_uint32), ("n_primes", ctypes.c_uint32),
+                ("prime_bits", ctypes.c_uint32 * MAX_PRIMES), ("log2_delta", ctypes.c_uint32)]
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_u32 = ctypes.c_uint32
+_u64 = ctypes.c_uint64
+_i32 = ctypes.c_int
+_pp = ctypes.POINTER(ctypes.c_void_p)
+
+_SIGS = {
+    "zn_ctx_create": (_i32, [ctypes.POINTER(_Params), _i32, _pp]),
+    "zn_ctx_destroy": (None, [_vp]),
+    "zn_ctx_primes": (_i32, [_vp, _vp, _vp]),
+    "zn_sync_status": (_i32, [_vp, _vp]),
+    "zn_strerror": (ctypes.c_char_p, [_i32]),
+    "ckks_keygen": (_i32, [_vp, _u64, _pp, _pp]),
+    "zn_sk_destroy": (None, [_vp]),
+    "zn_pk_destroy": (None, [_vp]),
+    "zn_pk_export": (_i32, [_vp, _vp]),
+    "zn_pk_import": (_i32, [_vp, _vp, _pp]),
+    "zn_sk_export": (_i32, [_vp, _vp]),
+    "zn_sk_import": (_i32, [_vp, _vp, _pp]),
+    "ckks_encode": (_i32, [_vp, _vp, _u32, _u32, _vp, _vp]),
+    "ckks_encrypt": (_i32, [_vp, _vp, _vp, _u32, _u32, _u64, _vp, _vp, _vp]),
+    "zinc_precompute": (_i32, [_vp, _vp, _u64, _pp]),
+    "zn_zcache_destroy": (None, [_vp]),
+    "zn_zcache_export": (_i32, [_vp, _vp]),
+    "zn_zcache_import": (_i32, [_vp, _vp, _pp]),
+    "zinc_encrypt": (_i32, [_vp, _vp, _vp, _u32, _u32, _u64, _vp, _vp, _vp]),
+    "ckks_decrypt": (_i32, [_vp, _vp, _vp, _u32, _vp, _vp]),
+    "ckks_decrypt_decode": (_i32, [_vp, _vp, _vp, _u32, _u32, _vp, _vp]),
+    "ckks_add": (_i32, [_vp, _vp, _vp, _u32, _vp, _vp]),
+    "zn_ntt_forward": (_i32, [_vp, _vp, _u32, _vp]),
+    "zn_ntt_inverse": (_i32, [_vp, _vp, _u32, _vp]),
+    "zn_sample": (_i32, [_vp, _i32, _u64, _u32, _u32, _u32, _u64, _u32, _vp, _vp]),
+    "zn_timing_enable": (_i32, [_vp, _i32]),
+    "zn_timing_read": (_i32, [_vp, _i32, _vp, _vp]),
+    "zn_host_primes": (_i32, [_u32, _vp, _u32, _vp]),
+    "zn_host_psi": (_u64, [_u64, _u32]),
+    "zn_host_encoder_twiddles": (_i32, [_u32, _vp, _vp]),
+    "zn_host_cdt": (_i32, [_vp]),
+}
+
+
+def lib():
+    """Load libzinc.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libzinc.so is not built ({LIB_PATH}); run "
+                              "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def strerror(status):
+    return lib().zn_strerror(status).decode()
+
+
+def _check(status, what):
+    if status != ZN_OK:
+        raise ZincError(status, what)
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dev(t, dtype, shape, what):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{what}: expected a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{what}: expected dtype {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{what}: tensor must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{what}: expected shape {tuple(shape)}, got {tuple(t.shape)}")
+    return t.data_ptr()
+
+
+# ----------------------------------------------------------------- handles
+
+class Context:
+    """A parameter set resident on one device (zn_ctx)."""
+
+    def __init__(self, log_n, prime_bits, log2_delta, device=0):
+        if len(prime_bits) > MAX_PRIMES or len(prime_bits) == 0:
+            raise ZincError(ZN_EINVAL, "zn_ctx_create")
+        p = _Params()
+        p.log_n = log_n
+        p.n_primes = len(prime_bits)
+        for i, b in enumerate(prime_bits):
+            p.prime_bits[i] = b
+        p.log2_delta = log2_delta
+        h = ctypes.c_void_p()
+        _check(lib().zn_ctx_create(ctypes.byref(p), device, ctypes.byref(h)), "zn_ctx_create")
+        self._h = h
+        self.log_n = log_n
+        self.n = 1 << log_n
+        self.prime_bits = tuple(prime_bits)
+        self.L = len(prime_bits)
+        self.log2_delta = log2_delta
+        self.device = device
+        qs = (ctypes.c_uint64 * self.L)()
+        ps = (ctypes.c_uint64 * self.L)()
+        _check(lib().zn_ctx_primes(h, qs, ps), "zn_ctx_primes")
+        self.primes = [int(x) for x in qs]
+        self.psis = [int(x) for x in ps]
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            lib().zn_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _Handle:
+    _destroy = None
+
+    def __init__(self, ctx, h):
+        self.ctx = ctx
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            getattr(lib(), self._destroy)(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class SecretKey(_Handle):
+    _destroy = "zn_sk_destroy"
+
+
+class PublicKey(_Handle):
+    _destroy = "zn_pk_destroy"
+
+
+class ZincCache(_Handle):
+    _destroy = "zn_zcache_destroy"
+
+
+# ------------------------------------------------------------ entry points
+
+def zn_ctx_create(log_n, prime_bits, log2_delta, device=0):
+    return Context(log_n, prime_bits, log2_delta, device)
+
+
+def zn_sync_status(ctx, stream=None):
+    _check(lib().zn_sync_status(ctx.handle, _stream(stream)), "device status")
+
+
+def ckks_keygen(ctx, seed):
+    sk, pk = ctypes.c_void_p(), ctypes.c_void_p()
+    _check(lib().ckks_keygen(ctx.handle, seed, ctypes.byref(sk), ctypes.byref(pk)), "ckks_keygen")
+    return SecretKey(ctx, sk), PublicKey(ctx, pk)
+
+
+def zn_pk_export(pk):
+    ctx = pk.ctx
+    out = np.empty((2, ctx.L, ctx.n), dtype=np.uint64)
+    _check(lib().zn_pk_export(pk.handle, out.ctypes.data), "zn_pk_export")
+    return out
+
+
+def zn_pk_import(ctx, arr):
+    arr = np.ascontiguousarray(arr, dtype=np.uint64).reshape(2, ctx.L, ctx.n)
+    h = ctypes.c_void_p()
+    _check(lib().zn_pk_import(ctx.handle, arr.ctypes.data, ctypes.byref(h)), "zn_pk_import")
+    return PublicKey(ctx, h)
+
+
+def zn_sk_export(sk):
+    out = np.empty(sk.ctx.n, dtype=np.int8)
+    _check(lib().zn_sk_export(sk.handle, out.ctypes.data), "zn_sk_export")
+    return out
+
+
+def zn_sk_import(ctx, arr):
+    arr = np.ascontiguousarray(arr, dtype=np.int8).reshape(ctx.n)
+    h = ctypes.c_void_p()
+    _check(lib().zn_sk_import(ctx.handle, arr.ctypes.data, ctypes.byref(h)), "zn_sk_import")
+    return SecretKey(ctx, h)
+
+
+def _out(out, shape, dtype, device):
+    import torch
+    if out is None:
+        return torch.empty(shape, dtype=dtype, device=device)
+    return out
+
+
+def ckks_encode(ctx, slots, out=None, stream=None):
+    """slots: CUDA float64 [B, n_slots] -> int64 [B, N] plaintext coefficients."""
+    import torch
+    B, ns = slots.shape
+    out = _out(out, (B, ctx.n), torch.int64, slots.device)
+    _dev(slots, torch.float64, None, "slots")
+    _dev(out, torch.int64, (B, ctx.n), "out")
+    _check(lib().ckks_encode(ctx.handle, slots.data_ptr(), ns, B, out.data_ptr(), _stream(stream)), "ckks_encode")
+    return out
+
+
+def _enc(fn, ctx, key, slots, seed, ct_index, out, stream, name):
+    import torch
+    B, ns = slots.shape
+    out = _out(out, (B, 2, ctx.L, ctx.n), torch.int64, slots.device)
+    _dev(slots, torch.float64, None, "slots")
+    _dev(ct_index, torch.int64, (B,), "ct_index")
+    _dev(out, torch.int64, (B, 2, ctx.L, ctx.n), "out")
+    _check(fn(ctx.handle, key.handle, slots.data_ptr(), ns, B, seed, ct_index.data_ptr(), out.data_ptr(),
+              _stream(stream)), name)
+    return out
+
+
+def ckks_encrypt(ctx, pk, slots, seed, ct_index, out=None, stream=None):
+    """Vanilla encryption (Eq. 8): CUDA float64 [B, n_slots] -> int64 [B, 2, L, N] (uint64 residues)."""
+    return _enc(lib().ckks_encrypt, ctx, pk, slots, seed, ct_index, out, stream, "ckks_encrypt")
+
+
+def zinc_precompute(ctx, pk, seed):
+    h = ctypes.c_void_p()
+    _check(lib().zinc_precompute(ctx.handle, pk.handle, seed, ctypes.byref(h)), "zinc_precompute")
+    return ZincCache(ctx, h)
+
+
+def zn_zcache_export(zc):
+    ctx = zc.ctx
+    out = np.empty((2, ctx.L, ctx.n), dtype=np.uint64)
+    _check(lib().zn_zcache_export(zc.handle, out.ctypes.data), "zn_zcache_export")
+    return out
+
+
+def zn_zcache_import(ctx, arr):
+    arr = np.ascontiguousarray(arr, dtype=np.uint64).reshape(2, ctx.L, ctx.n)
+    h = ctypes.c_void_p()
+    _check(lib().zn_zcache_import(ctx.handle, arr.ctypes.data, ctypes.byref(h)), "zn_zcache_import")
+    return ZincCache(ctx, h)
+
+
+def zinc_encrypt(ctx, zc, slots, seed, ct_index, out=None, stream=None):
+    """Zinc encryption (Algorithm 1): same shapes as ckks_encrypt."""
+    return _enc(lib().zinc_encrypt, ctx, zc, slots, seed, ct_index, out, stream, "zinc_encrypt")
+
+
+def ckks_decrypt(ctx, sk, ct, out=None, stream=None):
+    """Dec (Eq. 10): int64 [B, 2, L, N] -> coefficient residues int64 [B, L, N]."""
+    import torch
+    B = ct.shape[0]
+    out = _out(out, (B, ctx.L, ctx.n), torch.int64, ct.device)
+    _dev(ct, torch.int64, (B, 2, ctx.L, ctx.n), "ct")
+    _dev(out, torch.int64, (B, ctx.L, ctx.n), "out")
+    _check(lib().ckks_decrypt(ctx.handle, sk.handle, ct.data_ptr(), B, out.data_ptr(), _stream(stream)),
+           "ckks_decrypt")
+    return out
+
+
+def ckks_decrypt_decode(ctx, sk, ct, n_slots, out=None, stream=None):
+    import torch
+    B = ct.shape[0]
+    out = _out(out, (B, n_slots), torch.float64, ct.device)
+    _dev(ct, torch.int64, (B, 2, ctx.L, ctx.n), "ct")
+    _dev(out, torch.float64, (B, n_slots), "out")
+    _check(lib().ckks_decrypt_decode(ctx.handle, sk.handle, ct.data_ptr(), B, n_slots, out.data_ptr(),
+                                     _stream(stream)), "ckks_decrypt_decode")
+    return out
+
+
+def ckks_add(ctx, a, b, out=None, stream=None):
+    import torch
+    B = a.shape[0]
+    out = _out(out, tuple(a.shape), torch.int64, a.device)
+    for t, nm in ((a, "a"), (b, "b"), (out, "out")):
+        _dev(t, torch.int64, (B, 2, ctx.L, ctx.n), nm)
+    _check(lib().ckks_add(ctx.handle, a.data_ptr(), b.data_ptr(), B, out.data_ptr(), _stream(stream)), "ckks_add")
+    return out
+
+
+def zn_ntt_forward(ctx, data, stream=None):
+    import torch
+    B = data.shape[0]
+    _dev(data, torch.int64, (B, ctx.L, ctx.n), "data")
+    _check(lib().zn_ntt_forward(ctx.handle, data.data_ptr(), B, _stream(stream)), "zn_ntt_forward")
+    return data
+
+
+def zn_ntt_inverse(ctx, data, stream=None):
+    import torch
+    B = data.shape[0]
+    _dev(data, torch.int64, (B, ctx.L, ctx.n), "data")
+    _check(lib().zn_ntt_inverse(ctx.handle, data.data_ptr(), B, _stream(stream)), "zn_ntt_inverse")
+    return data
+
+
+def zn_sample(ctx, kind, seed, domain, poly, prime, ct_index0, count, out=None, device="cuda", stream=None):
+    import torch
+    out = _out(out, (count, ctx.n), torch.int64, device)
+    _dev(out, torch.int64, (count, ctx.n), "out")
+    _check(lib().zn_sample(ctx.handle, kind, seed, domain, poly, prime, ct_index0, count, out.data_ptr(),
+                           _stream(stream)), "zn_sample")
+    return out
+
+
+TIME_ENCODE, TIME_ENCRYPT, TIME_ZINC = 0, 1, 2
+
+
+def zn_timing_enable(ctx, on=True):
+    _check(lib().zn_timing_enable(ctx.handle, 1 if on else 0), "zn_timing_enable")
+
+
+def zn_timing_read(ctx, kind):
+    """(summed milliseconds, launch count) of the recorded launches of `kind`; clears them."""
+    ms = ctypes.c_double()
+    n = ctypes.c_uint64()
+    _check(lib().zn_timing_read(ctx.handle, kind, ctypes.byref(ms), ctypes.byref(n)), "zn_timing_read")
+    return ms.value, n.value
+
+
+# --------------------------------------------------- host-side (no GPU)
+
+def zn_host_primes(log_n, bits):
+    arr = (ctypes.c_uint32 * len(bits))(*bits)
+    out = (ctypes.c_uint64 * len(bits))()
+    _check(lib().zn_host_primes(log_n, arr, len(bits), out), "zn_host_primes")
+    return [int(x) for x in out]
+
+
+def zn_host_psi(q, log_n):
+    return int(lib().zn_host_psi(q, log_n))
+
+
+def zn_host_encoder_twiddles(log_n):
+    n = 1 << log_n
+    re = np.empty(n)
+    im = np.empty(n)
+    _check(lib().zn_host_encoder_twiddles(log_n, re.ctypes.data, im.ctypes.data), "zn_host_encoder_twiddles")
+    return re, im
+
+
+def zn_host_cdt():
+    out = np.empty(38, dtype=np.uint64)
+    _check(lib().zn_host_cdt(out.ctypes.data), "zn_host_cdt")
+    return [int(x) for x in out]
+
+
+def as_u64(t):
+    """int64 torch tensor (any device) -> numpy uint64 view of the same bits."""
+    return t.detach().cpu().numpy().view(np.uint64)

@@ -1,0 +1,672 @@
+// C ABI of the library (include/zinc.h): contexts, key/cache handles,
+// argument checking, scratch management and kernel launches.
+#include <cuda_runtime.h>
+
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/zinc.h"
+#include "zn_host.h"
+#include "zn_kernels.h"
+
+using zn::DevParams;
+using zn::i64;
+using zn::u64;
+
+struct zn_ctx {
+  int device;
+  zn_params prm;
+  uint32_t n, L;
+  u64 q[ZN_MAX_PRIMES], psi[ZN_MAX_PRIMES];
+  DevParams dp;
+  // device allocations owned by the context
+  u64* d_tw;          // tw, tws, itw, itws: 4 [L][N] tables, one allocation
+  double* d_etw;      // [2][N]
+  int* d_slot;        // [N/2]
+  unsigned* d_status;
+  i64* d_m;           // encode scratch [m_cap][N]
+  size_t m_cap;
+  double* d_fft;      // FFT scratch for large rings [fft_cap][N]
+  size_t fft_cap;
+  // launch timing (benchmark instrumentation)
+  bool timing;
+  std::vector<cudaEvent_t> ev[ZN_TIME_KINDS];   // start/stop pairs
+};
+
+struct zn_pk {
+  zn_ctx* ctx;
+  u64* d;    // [2][L][N] then Shoup companions [2][L][N]
+};
+struct zn_sk {
+  zn_ctx* ctx;
+  u64* d;                    // [L][N] NTT form
+  std::vector<int8_t> s;     // coefficients
+};
+struct zn_zcache {
+  zn_ctx* ctx;
+  u64* d;    // [2][L][N]
+};
+
+namespace {
+
+inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+inline size_t limb(const zn_ctx* c) { return (size_t)c->n; }
+inline size_t ring_words(const zn_ctx* c) { return (size_t)c->L * c->n; }
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+#define ZN_CUDA(call)                      \
+  do {                                     \
+    if ((call) != cudaSuccess) {           \
+      cudaGetLastError();                  \
+      return ZN_ECUDA;                     \
+    }                                      \
+  } while (0)
+
+int ensure_m(zn_ctx* c, size_t cts) {
+  if (cts <= c->m_cap) return ZN_OK;
+  if (c->d_m) cudaFree(c->d_m);
+  c->d_m = nullptr;
+  c->m_cap = 0;
+  if (cudaMalloc(&c->d_m, sizeof(i64) * cts * c->n) != cudaSuccess) {
+    cudaGetLastError();
+    return ZN_ENOMEM;
+  }
+  c->m_cap = cts;
+  return ZN_OK;
+}
+
+int ensure_fft(zn_ctx* c, size_t cts) {
+  if (cts <= c->fft_cap) return ZN_OK;
+  if (c->d_fft) cudaFree(c->d_fft);
+  c->d_fft = nullptr;
+  c->fft_cap = 0;
+  if (cudaMalloc(&c->d_fft, sizeof(double) * cts * c->n) != cudaSuccess) {
+    cudaGetLastError();
+    return ZN_ENOMEM;
+  }
+  c->fft_cap = cts;
+  return ZN_OK;
+}
+
+// Event pair around one launch (no-op unless timing is on).
+struct TimedLaunch {
+  zn_ctx* c;
+  int kind;
+  cudaStream_t st;
+  TimedLaunch(zn_ctx* c_, int kind_, cudaStream_t st_) : c(c_), kind(kind_), st(st_) { mark(); }
+  ~TimedLaunch() { mark(); }
+  void mark() {
+    if (!c->timing) return;
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+    cudaEventRecord(e, st);
+    c->ev[kind].push_back(e);
+  }
+};
+
+// Messages encoded per launch pair: keeps the int64 scratch within ~32 MiB
+// (L2-resident between the encode and encrypt launches).
+uint32_t encode_chunk(const zn_ctx* c) {
+  size_t per = sizeof(i64) * c->n;
+  size_t k = (32ull << 20) / per;
+  if (k < 1) k = 1;
+  if (k > 65535) k = 65535;
+  return (uint32_t)k;
+}
+
+int encrypt_common(zn_ctx* c, bool zinc, const u64* key, const u64* keys, const double* slots, uint32_t n_slots,
+                   uint32_t batch, uint64_t seed, const uint64_t* ct_index, uint64_t* ct, void* stream) {
+  if (!c || !key || !ct || !ct_index || n_slots > c->n / 2 || (n_slots && !slots)) return ZN_EINVAL;
+  if (batch == 0) return ZN_OK;
+  DeviceGuard g(c->device);
+  const uint32_t chunk = encode_chunk(c);
+  const uint32_t first = batch < chunk ? batch : chunk;
+  int rc = ensure_m(c, first);
+  if (rc) return rc;
+  if (c->prm.log_n > 14 && (rc = ensure_fft(c, first))) return rc;
+  for (uint32_t b0 = 0; b0 < batch; b0 += chunk) {
+    const uint32_t nb = (batch - b0) < chunk ? (batch - b0) : chunk;
+    {
+      TimedLaunch t(c, ZN_TIME_ENCODE, S(stream));
+      ZN_CUDA(zn::launch_encode(c->dp, slots + (size_t)b0 * n_slots, n_slots, nb, c->d_m, c->d_fft, S(stream)));
+    }
+    zn::EncArgs A;
+    A.key = key;
+    A.keys = keys;
+    A.m = c->d_m;
+    A.ct_index = ct_index + b0;
+    A.ct_index0 = 0;
+    A.seed = seed;
+    A.domain = zinc ? 1u : 0u;
+    A.out = ct + (size_t)b0 * 2 * ring_words(c);
+    TimedLaunch t(c, zinc ? ZN_TIME_ZINC : ZN_TIME_ENCRYPT, S(stream));
+    ZN_CUDA(zn::launch_encrypt(c->dp, A, zinc, nb, S(stream)));
+  }
+  return ZN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* zn_strerror(int status) {
+  switch (status) {
+    case ZN_OK: return "ok";
+    case ZN_EINVAL: return "invalid argument";
+    case ZN_ENOMEM: return "out of device memory";
+    case ZN_EOVERFLOW: return "encoded coefficient overflow (|m_k| >= 2^62 or not finite)";
+    case ZN_ECUDA: return "CUDA runtime error";
+    case ZN_ETIMEOUT: return "device wait timed out";
+    case ZN_ENOPRIME: return "no NTT-friendly prime left for a chain entry";
+    default: return "unknown status";
+  }
+}
+
+int zn_host_primes(uint32_t log_n, const uint32_t* bits, uint32_t n_primes, uint64_t* out) {
+  if (!bits || !out || log_n < 1 || log_n > 20) return ZN_EINVAL;
+  for (uint32_t i = 0; i < n_primes; ++i)
+    if (bits[i] < 2 || bits[i] > 62) return ZN_EINVAL;
+  return zn::gen_primes(log_n, bits, n_primes, out) ? ZN_ENOPRIME : ZN_OK;
+}
+
+uint64_t zn_host_psi(uint64_t q, uint32_t log_n) { return zn::find_psi(q, log_n); }
+
+int zn_host_encoder_twiddles(uint32_t log_n, double* re, double* im) {
+  if (!re || !im || log_n < 2 || log_n > 20) return ZN_EINVAL;
+  return zn::encoder_twiddles(log_n, re, im);
+}
+
+int zn_host_cdt(uint64_t* out) {
+  if (!out) return ZN_EINVAL;
+  return zn::cdt_thresholds(out);
+}
+
+int zn_ctx_create(const zn_params* p, int device, zn_ctx** out) {
+  if (!p || !out) return ZN_EINVAL;
+  *out = nullptr;
+  if (p->log_n < 4 || p->log_n > 15 || p->n_primes < 1 || p->n_primes > ZN_MAX_PRIMES || p->log2_delta < 1 ||
+      p->log2_delta > 62)
+    return ZN_EINVAL;
+  for (uint32_t i = 0; i < p->n_primes; ++i)
+    if (p->prime_bits[i] < 20 || p->prime_bits[i] > 61) return ZN_EINVAL;
+  const uint32_t n = 1u << p->log_n, L = p->n_primes;
+  zn_ctx* c = new (std::nothrow) zn_ctx();
+  if (!c) return ZN_ENOMEM;
+  c->device = device;
+  c->prm = *p;
+  c->n = n;
+  c->L = L;
+  if (zn::gen_primes(p->log_n, p->prime_bits, L, c->q)) {
+    delete c;
+    return ZN_ENOPRIME;
+  }
+  for (uint32_t i = 0; i < L; ++i) c->psi[i] = zn::find_psi(c->q[i], p->log_n);
+
+  // host tables
+  std::vector<u64> tabs(4 * (size_t)L * n);
+  u64* tw = tabs.data();
+  u64* tws = tw + (size_t)L * n;
+  u64* itw = tws + (size_t)L * n;
+  u64* itws = itw + (size_t)L * n;
+  for (uint32_t i = 0; i < L; ++i)
+    zn::ntt_tables(c->q[i], c->psi[i], p->log_n, tw + (size_t)i * n, tws + (size_t)i * n, itw + (size_t)i * n,
+                   itws + (size_t)i * n);
+  std::vector<double> etw(2 * (size_t)n);
+  zn::encoder_twiddles(p->log_n, etw.data(), etw.data() + n);
+  std::vector<int> slot(n / 2);
+  {
+    u64 g = 1;
+    for (uint32_t j = 0; j < n / 2; ++j) {
+      slot[(g - 1) / 4] = (int)j;
+      g = (g * 5) % (2ull * n);
+    }
+  }
+  DevParams& dp = c->dp;
+  std::memset(&dp, 0, sizeof(dp));
+  dp.log_n = (int)p->log_n;
+  dp.L = (int)L;
+  dp.log2_delta = (int)p->log2_delta;
+  for (uint32_t i = 0; i < L; ++i) {
+    const u64 q = c->q[i];
+    dp.q[i] = q;
+    dp.mu[i] = (u64)((((unsigned __int128)1) << 64) / q);
+    dp.ninv[i] = zn::powmod(n % q, q - 2, q);
+    dp.ninvs[i] = zn::shoup(dp.ninv[i], q);
+  }
+  dp.q0inv_mod_q1 = L > 1 ? zn::powmod(c->q[0] % c->q[1], c->q[1] - 2, c->q[1]) : 0;
+  zn::cdt_thresholds(dp.cdt);
+
+  DeviceGuard g(device);
+  int rc = ZN_OK;
+  if (cudaMalloc(&c->d_tw, sizeof(u64) * tabs.size()) != cudaSuccess ||
+      cudaMalloc(&c->d_etw, sizeof(double) * etw.size()) != cudaSuccess ||
+      cudaMalloc(&c->d_slot, sizeof(int) * slot.size()) != cudaSuccess ||
+      cudaMalloc(&c->d_status, sizeof(unsigned)) != cudaSuccess) {
+    rc = ZN_ENOMEM;
+  } else if (cudaMemcpy(c->d_tw, tabs.data(), sizeof(u64) * tabs.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+             cudaMemcpy(c->d_etw, etw.data(), sizeof(double) * etw.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+             cudaMemcpy(c->d_slot, slot.data(), sizeof(int) * slot.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+             cudaMemset(c->d_status, 0, sizeof(unsigned)) != cudaSuccess) {
+    rc = ZN_ECUDA;
+  }
+  if (rc) {
+    cudaGetLastError();
+    zn_ctx_destroy(c);
+    return rc;
+  }
+  dp.tw = c->d_tw;
+  dp.tws = c->d_tw + (size_t)L * n;
+  dp.itw = c->d_tw + 2 * (size_t)L * n;
+  dp.itws = c->d_tw + 3 * (size_t)L * n;
+  dp.etw = c->d_etw;
+  dp.slot_of_t = c->d_slot;
+  dp.status = c->d_status;
+  *out = c;
+  return ZN_OK;
+}
+
+void zn_ctx_destroy(zn_ctx* c) {
+  if (!c) return;
+  DeviceGuard g(c->device);
+  zn_timing_enable(c, 0);
+  cudaFree(c->d_tw);
+  cudaFree(c->d_etw);
+  cudaFree(c->d_slot);
+  cudaFree(c->d_status);
+  cudaFree(c->d_m);
+  cudaFree(c->d_fft);
+  delete c;
+}
+
+int zn_ctx_primes(const zn_ctx* c, uint64_t* primes, uint64_t* psis) {
+  if (!c) return ZN_EINVAL;
+  for (uint32_t i = 0; i < c->L; ++i) {
+    if (primes) primes[i] = c->q[i];
+    if (psis) psis[i] = c->psi[i];
+  }
+  return ZN_OK;
+}
+
+int zn_sync_status(zn_ctx* c, void* stream) {
+  if (!c) return ZN_EINVAL;
+  DeviceGuard g(c->device);
+  unsigned st = 0;
+  ZN_CUDA(cudaStreamSynchronize(S(stream)));
+  ZN_CUDA(cudaMemcpy(&st, c->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  ZN_CUDA(cudaMemset(c->d_status, 0, sizeof(unsigned)));
+  if (st & zn::kStatusOverflow) return ZN_EOVERFLOW;
+  if (st & zn::kStatusTimeout) return ZN_ETIMEOUT;
+  return ZN_OK;
+}
+
+int zn_timing_enable(zn_ctx* c, int on) {
+  if (!c) return ZN_EINVAL;
+  DeviceGuard g(c->device);
+  if (!on) {
+    for (auto& v : c->ev) {
+      for (cudaEvent_t e : v) cudaEventDestroy(e);
+      v.clear();
+    }
+  }
+  c->timing = on != 0;
+  return ZN_OK;
+}
+
+int zn_timing_read(zn_ctx* c, int kind, double* ms, uint64_t* launches) {
+  if (!c || kind < 0 || kind >= ZN_TIME_KINDS) return ZN_EINVAL;
+  DeviceGuard g(c->device);
+  auto& v = c->ev[kind];
+  double total = 0.0;
+  int rc = ZN_OK;
+  for (size_t k = 0; k + 1 < v.size(); k += 2) {
+    float t = 0.f;
+    if (cudaEventSynchronize(v[k + 1]) != cudaSuccess || cudaEventElapsedTime(&t, v[k], v[k + 1]) != cudaSuccess)
+      rc = ZN_ECUDA;
+    total += t;
+  }
+  if (ms) *ms = total;
+  if (launches) *launches = v.size() / 2;
+  for (cudaEvent_t e : v) cudaEventDestroy(e);
+  v.clear();
+  cudaGetLastError();
+  return rc;
+}
+
+// ------------------------------------------------------------------ keys
+
+int ckks_keygen(zn_ctx* c, uint64_t seed, zn_sk** sk, zn_pk** pk) {
+  if (!c || !sk || !pk) return ZN_EINVAL;
+  *sk = nullptr;
+  *pk = nullptr;
+  DeviceGuard g(c->device);
+  zn_sk* s = new (std::nothrow) zn_sk();
+  zn_pk* k = new (std::nothrow) zn_pk();
+  if (!s || !k) {
+    delete s;
+    delete k;
+    return ZN_ENOMEM;
+  }
+  s->ctx = c;
+  k->ctx = c;
+  const size_t rw = ring_words(c);
+  i64* d_s = nullptr;
+  if (cudaMalloc(&s->d, sizeof(u64) * rw) != cudaSuccess || cudaMalloc(&k->d, sizeof(u64) * 4 * rw) != cudaSuccess ||
+      cudaMalloc(&d_s, sizeof(i64) * c->n) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(s->d);
+    cudaFree(k->d);
+    cudaFree(d_s);
+    delete s;
+    delete k;
+    return ZN_ENOMEM;
+  }
+  int rc = ZN_OK;
+  if (zn::launch_keygen(c->dp, seed, s->d, k->d, k->d + 2 * rw, 0) != cudaSuccess ||
+      zn::launch_sample(c->dp, 0, seed, 2, 0, 0, 0, 1, d_s, 0) != cudaSuccess ||
+      cudaDeviceSynchronize() != cudaSuccess) {
+    rc = ZN_ECUDA;
+  } else {
+    std::vector<i64> tmp(c->n);
+    if (cudaMemcpy(tmp.data(), d_s, sizeof(i64) * c->n, cudaMemcpyDeviceToHost) != cudaSuccess) rc = ZN_ECUDA;
+    s->s.resize(c->n);
+    for (uint32_t j = 0; j < c->n; ++j) s->s[j] = (int8_t)tmp[j];
+  }
+  cudaFree(d_s);
+  if (rc) {
+    cudaGetLastError();
+    zn_sk_destroy(s);
+    zn_pk_destroy(k);
+    return rc;
+  }
+  *sk = s;
+  *pk = k;
+  return ZN_OK;
+}
+
+void zn_sk_destroy(zn_sk* s) {
+  if (!s) return;
+  DeviceGuard g(s->ctx->device);
+  cudaFree(s->d);
+  delete s;
+}
+
+void zn_pk_destroy(zn_pk* k) {
+  if (!k) return;
+  DeviceGuard g(k->ctx->device);
+  cudaFree(k->d);
+  delete k;
+}
+
+int zn_pk_export(const zn_pk* k, uint64_t* host_out) {
+  if (!k || !host_out) return ZN_EINVAL;
+  DeviceGuard g(k->ctx->device);
+  ZN_CUDA(cudaMemcpy(host_out, k->d, sizeof(u64) * 2 * ring_words(k->ctx), cudaMemcpyDeviceToHost));
+  return ZN_OK;
+}
+
+int zn_pk_import(zn_ctx* c, const uint64_t* host_in, zn_pk** out) {
+  if (!c || !host_in || !out) return ZN_EINVAL;
+  *out = nullptr;
+  const size_t rw = ring_words(c);
+  for (uint32_t i = 0; i < c->L; ++i)
+    for (int p = 0; p < 2; ++p)
+      for (uint32_t j = 0; j < c->n; ++j)
+        if (host_in[(size_t)p * rw + (size_t)i * c->n + j] >= c->q[i]) return ZN_EINVAL;
+  DeviceGuard g(c->device);
+  zn_pk* k = new (std::nothrow) zn_pk();
+  if (!k) return ZN_ENOMEM;
+  k->ctx = c;
+  if (cudaMalloc(&k->d, sizeof(u64) * 4 * rw) != cudaSuccess) {
+    cudaGetLastError();
+    delete k;
+    return ZN_ENOMEM;
+  }
+  if (cudaMemcpy(k->d, host_in, sizeof(u64) * 2 * rw, cudaMemcpyHostToDevice) != cudaSuccess ||
+      zn::launch_shoup(c->dp, k->d, k->d + 2 * rw, 2, 0) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+    zn_pk_destroy(k);
+    return ZN_ECUDA;
+  }
+  *out = k;
+  return ZN_OK;
+}
+
+int zn_sk_export(const zn_sk* s, int8_t* host_out) {
+  if (!s || !host_out) return ZN_EINVAL;
+  std::memcpy(host_out, s->s.data(), s->s.size());
+  return ZN_OK;
+}
+
+int zn_sk_import(zn_ctx* c, const int8_t* host_in, zn_sk** out) {
+  if (!c || !host_in || !out) return ZN_EINVAL;
+  *out = nullptr;
+  for (uint32_t j = 0; j < c->n; ++j)
+    if (host_in[j] < -1 || host_in[j] > 1) return ZN_EINVAL;
+  DeviceGuard g(c->device);
+  zn_sk* s = new (std::nothrow) zn_sk();
+  if (!s) return ZN_ENOMEM;
+  s->ctx = c;
+  s->s.assign(host_in, host_in + c->n);
+  const size_t rw = ring_words(c);
+  int8_t* d_s = nullptr;
+  u64* tmp = nullptr;
+  if (cudaMalloc(&s->d, sizeof(u64) * rw) != cudaSuccess || cudaMalloc(&d_s, c->n) != cudaSuccess ||
+      cudaMalloc(&tmp, sizeof(u64) * rw) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(d_s);
+    cudaFree(tmp);
+    zn_sk_destroy(s);
+    return ZN_ENOMEM;
+  }
+  int rc = ZN_OK;
+  if (cudaMemcpy(d_s, host_in, c->n, cudaMemcpyHostToDevice) != cudaSuccess ||
+      zn::launch_sk_residues(c->dp, d_s, s->d, 0) != cudaSuccess ||
+      zn::launch_ntt_fwd(c->dp, s->d, 1, tmp, 0) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
+    rc = ZN_ECUDA;
+  cudaFree(d_s);
+  cudaFree(tmp);
+  if (rc) {
+    cudaGetLastError();
+    zn_sk_destroy(s);
+    return rc;
+  }
+  *out = s;
+  return ZN_OK;
+}
+
+// --------------------------------------------------------------- encode
+
+int ckks_encode(zn_ctx* c, const double* slots, uint32_t n_slots, uint32_t batch, int64_t* out, void* stream) {
+  if (!c || !out || n_slots > c->n / 2 || (n_slots && !slots)) return ZN_EINVAL;
+  if (batch == 0) return ZN_OK;
+  DeviceGuard g(c->device);
+  int rc;
+  if (c->prm.log_n > 14 && (rc = ensure_fft(c, batch))) return rc;
+  ZN_CUDA(zn::launch_encode(c->dp, slots, n_slots, batch, (i64*)out, c->d_fft, S(stream)));
+  return ZN_OK;
+}
+
+// -------------------------------------------------------------- encrypt
+
+int ckks_encrypt(zn_ctx* c, const zn_pk* pk, const double* slots, uint32_t n_slots, uint32_t batch, uint64_t seed,
+                 const uint64_t* ct_index, uint64_t* ct, void* stream) {
+  if (!c || !pk || pk->ctx != c) return ZN_EINVAL;
+  return encrypt_common(c, false, pk->d, pk->d + 2 * ring_words(c), slots, n_slots, batch, seed, ct_index, ct,
+                        stream);
+}
+
+int zinc_precompute(zn_ctx* c, const zn_pk* pk, uint64_t seed, zn_zcache** out) {
+  if (!c || !pk || pk->ctx != c || !out) return ZN_EINVAL;
+  *out = nullptr;
+  DeviceGuard g(c->device);
+  zn_zcache* z = new (std::nothrow) zn_zcache();
+  if (!z) return ZN_ENOMEM;
+  z->ctx = c;
+  if (cudaMalloc(&z->d, sizeof(u64) * 2 * ring_words(c)) != cudaSuccess) {
+    cudaGetLastError();
+    delete z;
+    return ZN_ENOMEM;
+  }
+  // vanilla Enc of the zero plaintext, sampling domain 3, ct_index 0
+  zn::EncArgs A;
+  A.key = pk->d;
+  A.keys = pk->d + 2 * ring_words(c);
+  A.m = nullptr;
+  A.ct_index = nullptr;
+  A.ct_index0 = 0;
+  A.seed = seed;
+  A.domain = 3;
+  A.out = z->d;
+  if (zn::launch_encrypt(c->dp, A, false, 1, 0) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+    zn_zcache_destroy(z);
+    return ZN_ECUDA;
+  }
+  *out = z;
+  return ZN_OK;
+}
+
+void zn_zcache_destroy(zn_zcache* z) {
+  if (!z) return;
+  DeviceGuard g(z->ctx->device);
+  cudaFree(z->d);
+  delete z;
+}
+
+int zn_zcache_export(const zn_zcache* z, uint64_t* host_out) {
+  if (!z || !host_out) return ZN_EINVAL;
+  DeviceGuard g(z->ctx->device);
+  ZN_CUDA(cudaMemcpy(host_out, z->d, sizeof(u64) * 2 * ring_words(z->ctx), cudaMemcpyDeviceToHost));
+  return ZN_OK;
+}
+
+int zn_zcache_import(zn_ctx* c, const uint64_t* host_in, zn_zcache** out) {
+  if (!c || !host_in || !out) return ZN_EINVAL;
+  *out = nullptr;
+  const size_t rw = ring_words(c);
+  for (uint32_t i = 0; i < c->L; ++i)
+    for (int p = 0; p < 2; ++p)
+      for (uint32_t j = 0; j < c->n; ++j)
+        if (host_in[(size_t)p * rw + (size_t)i * c->n + j] >= c->q[i]) return ZN_EINVAL;
+  DeviceGuard g(c->device);
+  zn_zcache* z = new (std::nothrow) zn_zcache();
+  if (!z) return ZN_ENOMEM;
+  z->ctx = c;
+  if (cudaMalloc(&z->d, sizeof(u64) * 2 * rw) != cudaSuccess) {
+    cudaGetLastError();
+    delete z;
+    return ZN_ENOMEM;
+  }
+  if (cudaMemcpy(z->d, host_in, sizeof(u64) * 2 * rw, cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    zn_zcache_destroy(z);
+    return ZN_ECUDA;
+  }
+  *out = z;
+  return ZN_OK;
+}
+
+int zinc_encrypt(zn_ctx* c, const zn_zcache* z, const double* slots, uint32_t n_slots, uint32_t batch, uint64_t seed,
+                 const uint64_t* ct_index, uint64_t* ct, void* stream) {
+  if (!c || !z || z->ctx != c) return ZN_EINVAL;
+  return encrypt_common(c, true, z->d, nullptr, slots, n_slots, batch, seed, ct_index, ct, stream);
+}
+
+// -------------------------------------------------------------- decrypt
+
+int ckks_decrypt(zn_ctx* c, const zn_sk* sk, const uint64_t* ct, uint32_t batch, uint64_t* out, void* stream) {
+  if (!c || !sk || sk->ctx != c || !ct || !out) return ZN_EINVAL;
+  if (batch == 0) return ZN_OK;
+  DeviceGuard g(c->device);
+  ZN_CUDA(zn::launch_dec_mul(c->dp, ct, sk->d, batch, out, S(stream)));
+  ZN_CUDA(zn::launch_ntt_inv(c->dp, out, batch, S(stream)));
+  return ZN_OK;
+}
+
+int ckks_decrypt_decode(zn_ctx* c, const zn_sk* sk, const uint64_t* ct, uint32_t batch, uint32_t n_slots, double* out,
+                        void* stream) {
+  if (!c || !sk || sk->ctx != c || !ct || !out || n_slots > c->n / 2) return ZN_EINVAL;
+  if (batch == 0 || n_slots == 0) return ZN_OK;
+  DeviceGuard g(c->device);
+  u64* coeffs = nullptr;
+  double* work = nullptr;
+  if (cudaMalloc(&coeffs, sizeof(u64) * batch * ring_words(c)) != cudaSuccess ||
+      cudaMalloc(&work, sizeof(double) * batch * (size_t)c->n) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(coeffs);
+    cudaFree(work);
+    return ZN_ENOMEM;
+  }
+  int rc = ckks_decrypt(c, sk, ct, batch, coeffs, stream);
+  if (!rc && zn::launch_decode(c->dp, coeffs, batch, n_slots, out, work, S(stream)) != cudaSuccess) rc = ZN_ECUDA;
+  if (!rc && cudaStreamSynchronize(S(stream)) != cudaSuccess) rc = ZN_ECUDA;
+  cudaGetLastError();
+  cudaFree(coeffs);
+  cudaFree(work);
+  return rc;
+}
+
+int ckks_add(zn_ctx* c, const uint64_t* a, const uint64_t* b, uint32_t batch, uint64_t* out, void* stream) {
+  if (!c || !a || !b || !out) return ZN_EINVAL;
+  if (batch == 0) return ZN_OK;
+  DeviceGuard g(c->device);
+  ZN_CUDA(zn::launch_add(c->dp, a, b, batch, out, S(stream)));
+  return ZN_OK;
+}
+
+// ------------------------------------------------------------ building blocks
+
+int zn_ntt_forward(zn_ctx* c, uint64_t* data, uint32_t batch, void* stream) {
+  if (!c || !data) return ZN_EINVAL;
+  if (batch == 0) return ZN_OK;
+  DeviceGuard g(c->device);
+  u64* tmp = nullptr;
+  if (c->prm.log_n > 14) {
+    if (cudaMalloc(&tmp, sizeof(u64) * batch * ring_words(c)) != cudaSuccess) {
+      cudaGetLastError();
+      return ZN_ENOMEM;
+    }
+  }
+  int rc = zn::launch_ntt_fwd(c->dp, data, batch, tmp, S(stream)) == cudaSuccess ? ZN_OK : ZN_ECUDA;
+  if (tmp) {
+    if (cudaStreamSynchronize(S(stream)) != cudaSuccess) rc = ZN_ECUDA;
+    cudaFree(tmp);
+  }
+  cudaGetLastError();
+  return rc;
+}
+
+int zn_ntt_inverse(zn_ctx* c, uint64_t* data, uint32_t batch, void* stream) {
+  if (!c || !data) return ZN_EINVAL;
+  if (batch == 0) return ZN_OK;
+  DeviceGuard g(c->device);
+  ZN_CUDA(zn::launch_ntt_inv(c->dp, data, batch, S(stream)));
+  return ZN_OK;
+}
+
+int zn_sample(zn_ctx* c, int kind, uint64_t seed, uint32_t domain, uint32_t poly, uint32_t prime, uint64_t ct_index0,
+              uint32_t count, int64_t* out, void* stream) {
+  if (!c || !out || kind < 0 || kind > 2 || domain > 255 || poly > 255 || prime >= c->L) return ZN_EINVAL;
+  if (count == 0) return ZN_OK;
+  DeviceGuard g(c->device);
+  ZN_CUDA(zn::launch_sample(c->dp, kind, seed, domain, poly, prime, ct_index0, count, (i64*)out, S(stream)));
+  return ZN_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,265 @@
+// Encoder (FP64 FFT with a fixed operation order), inverse NTT, decryption
+// (Eq. 10), decoding, homomorphic addition and small helpers.
+#include "zn_kernels.h"
+
+namespace zn {
+
+// ------------------------------------------------------------------ encode
+
+// One block per slot vector; (re, im) = n = N/2 doubles each, in shared
+// memory (n <= 8192) or in a global scratch area (larger rings).
+__device__ void encode_one(const DevParams& P, const double* __restrict__ z, uint32_t n_slots, double* re,
+                           double* im, i64* __restrict__ out) {
+  const int log_n = P.log_n, N = 1 << log_n, n = N >> 1;
+  for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    const int t = brv_bits(r, log_n - 1);
+    const int j = __ldg(P.slot_of_t + t);
+    re[r] = (j < (int)n_slots) ? __ldg(z + j) : 0.0;
+    im[r] = 0.0;
+  }
+  __syncthreads();
+  fft_dit(re, im, log_n, P.etw, false);
+  // twist by T[k], exact power-of-two scaling, rint (ties to even)
+  const double scale = ldexp(1.0, P.log2_delta + 1 - log_n);
+  const double* twr = P.etw;
+  const double* twi = P.etw + N;
+  const double lim = 4611686018427387904.0;   // 2^62
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const double xr = re[k], xi = im[k], wr = __ldg(twr + k), wi = __ldg(twi + k);
+    const double sr = __dsub_rn(__dmul_rn(xr, wr), __dmul_rn(xi, wi));
+    const double si = __dadd_rn(__dmul_rn(xr, wi), __dmul_rn(xi, wr));
+    double a = rint(__dmul_rn(sr, scale)), b = rint(__dmul_rn(si, scale));
+    if (!(fabs(a) < lim) || !(fabs(b) < lim)) {
+      atomicOr(P.status, kStatusOverflow);
+      a = 0.0;
+      b = 0.0;
+    }
+    out[k] = (i64)a;
+    out[k + n] = (i64)b;
+  }
+}
+
+__global__ void k_encode_smem(DevParams P, const double* __restrict__ slots, uint32_t n_slots, i64* __restrict__ out) {
+  extern __shared__ double smd[];
+  const int N = 1 << P.log_n, n = N >> 1;
+  const size_t b = blockIdx.x;
+  encode_one(P, slots + b * n_slots, n_slots, smd, smd + n, out + b * N);
+}
+
+__global__ void k_encode_gmem(DevParams P, const double* __restrict__ slots, uint32_t n_slots, i64* __restrict__ out,
+                              double* __restrict__ work) {
+  const int N = 1 << P.log_n, n = N >> 1;
+  const size_t b = blockIdx.x;
+  double* re = work + b * 2 * (size_t)n;
+  encode_one(P, slots + b * n_slots, n_slots, re, re + n, out + b * N);
+}
+
+// ------------------------------------------------------------ inverse NTT
+// Gentleman-Sande, bit-reversed input -> natural order, times N^-1; one
+// block per polynomial, in shared memory or in place in global memory.
+__device__ void intt_block(const DevParams& P, int i, u64* a) {
+  const int log_n = P.log_n, N = 1 << log_n;
+  const u64 q = P.q[i];
+  const u64* itw = P.itw + (size_t)i * N;
+  const u64* itws = P.itws + (size_t)i * N;
+  for (int lt = 0; lt < log_n; ++lt) {
+    const int t = 1 << lt, m = N >> (lt + 1);
+    for (int id = threadIdx.x; id < N / 2; id += blockDim.x) {
+      const int g = id >> lt, j = id & (t - 1);
+      const int j1 = 2 * g * t + j;
+      const u64 w = __ldg(itw + m + g), ws = __ldg(itws + m + g);
+      const u64 U = a[j1], V = a[j1 + t];
+      u64 s = U + V;
+      if (s >= q) s -= q;
+      const u64 d = U >= V ? U - V : U + q - V;
+      u64 r = mul_shoup(d, w, ws, q);
+      if (r >= q) r -= q;
+      a[j1] = s;
+      a[j1 + t] = r;
+    }
+    __syncthreads();
+  }
+  for (int k = threadIdx.x; k < N; k += blockDim.x) {
+    const u64 r = mul_shoup(a[k], P.ninv[i], P.ninvs[i], q);
+    a[k] = r >= q ? r - q : r;
+  }
+  __syncthreads();
+}
+
+__global__ void k_ntt_inv(DevParams P, u64* data, int use_smem) {
+  extern __shared__ u64 sm[];
+  const int i = blockIdx.x, N = 1 << P.log_n;
+  u64* a = data + ((size_t)blockIdx.y * P.L + i) * N;
+  if (use_smem) {
+    for (int k = threadIdx.x; k < N; k += blockDim.x) sm[k] = a[k];
+    __syncthreads();
+    intt_block(P, i, sm);
+    for (int k = threadIdx.x; k < N; k += blockDim.x) a[k] = sm[k];
+  } else {
+    intt_block(P, i, a);
+  }
+}
+
+// -------------------------------------------------------------- decryption
+// d = c0 + c1 * s-hat (NTT domain) per prime -> out [B][L][N]
+__global__ void k_dec_mul(DevParams P, const u64* __restrict__ ct, const u64* __restrict__ sk, uint32_t batch,
+                          u64* __restrict__ out) {
+  const int N = 1 << P.log_n, L = P.L;
+  const size_t total = (size_t)batch * L * N;
+  for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < total; x += (size_t)gridDim.x * blockDim.x) {
+    const size_t b = x / ((size_t)L * N), rem = x % ((size_t)L * N);
+    const int i = (int)(rem / N);
+    const u64 q = P.q[i];
+    const u64 c0 = ct[b * 2 * L * N + rem], c1 = ct[b * 2 * L * N + (size_t)L * N + rem];
+    const u64 p = mulmod_slow(c1, sk[rem], q);
+    u64 s = c0 + p;
+    if (s >= q) s -= q;
+    out[x] = s;
+  }
+}
+
+// CRT over the first two primes (or one), centred, then
+// z_j = Delta^-1 m(zeta^(5^j)); one block per ciphertext.
+__global__ void k_decode(DevParams P, const u64* __restrict__ coeffs, uint32_t n_slots, double* __restrict__ out,
+                         double* __restrict__ work) {
+  const int log_n = P.log_n, N = 1 << log_n, n = N >> 1, L = P.L;
+  const size_t b = blockIdx.x;
+  double* re = work + b * 2 * (size_t)n;
+  double* im = re + n;
+  const u64* r0 = coeffs + b * (size_t)L * N;
+  const u64* r1 = r0 + N;
+  const u64 q0 = P.q[0];
+  const double* twr = P.etw;
+  const double* twi = P.etw + N;
+  auto coef = [&](int k) -> double {
+    if (L == 1) {
+      const u64 x = r0[k];
+      return x > q0 / 2 ? -(double)(q0 - x) : (double)x;
+    }
+    const u64 q1 = P.q[1];
+    const u64 a = r0[k], c = r1[k];
+    const u64 am = a % q1;
+    const u64 d = c >= am ? c - am : c + q1 - am;
+    const u64 y = mulmod_slow(d, P.q0inv_mod_q1, q1);
+    const u128 x = (u128)a + (u128)q0 * y;   // in [0, q0 q1)
+    const u128 Q = (u128)q0 * q1;
+    if (x > Q / 2) return -(double)(Q - x);
+    return (double)x;
+  };
+  // w'_k = (m_k + i m_{k+n}) * conj(T[k]), placed bit-reversed
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const double mr = coef(k), mi = coef(k + n);
+    const double wr = twr[k], wi = -twi[k];
+    const int r = brv_bits(k, log_n - 1);
+    re[r] = mr * wr - mi * wi;
+    im[r] = mr * wi + mi * wr;
+  }
+  __syncthreads();
+  fft_dit(re, im, log_n, P.etw, true);
+  const double inv_delta = ldexp(1.0, -P.log2_delta);
+  // slot j sits at t_j = (5^j mod 2N - 1)/4; slot_of_t is the inverse map
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    const int j = P.slot_of_t[t];
+    if (j < (int)n_slots) out[b * n_slots + j] = re[t] * inv_delta;
+  }
+}
+
+// ----------------------------------------------------------------- helpers
+__global__ void k_add(DevParams P, const u64* a, const u64* b, uint32_t batch, u64* out) {
+  const int N = 1 << P.log_n, L = P.L;
+  const size_t total = (size_t)batch * 2 * L * N;
+  for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < total; x += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)((x / N) % L);
+    const u64 q = P.q[i];
+    const u64 s = a[x] + b[x];
+    out[x] = s >= q ? s - q : s;
+  }
+}
+
+// Shoup companions: ws[x] = floor(w[x] 2^64 / q) for `polys` polynomials [polys][L][N]
+__global__ void k_shoup(DevParams P, const u64* w, u64* ws, uint32_t polys) {
+  const int N = 1 << P.log_n, L = P.L;
+  const size_t total = (size_t)polys * L * N;
+  for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < total; x += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)((x / N) % L);
+    ws[x] = shoup_of(w[x], P.q[i]);
+  }
+}
+
+// secret-key coefficients (int8) -> residues [L][N]
+__global__ void k_sk_residues(DevParams P, const int8_t* s, u64* out) {
+  const int N = 1 << P.log_n, L = P.L;
+  for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < L * N; x += gridDim.x * blockDim.x)
+    out[x] = small_res(s[x % N], P.q[x / N]);
+}
+
+// ================================================================ launchers
+
+static unsigned grid_for(size_t total, int block) {
+  size_t g = (total + block - 1) / block;
+  return (unsigned)(g > 152 * 64 ? 152 * 64 : (g < 1 ? 1 : g));
+}
+
+cudaError_t launch_encode(const DevParams& P, const double* slots, uint32_t n_slots, uint32_t batch, i64* out,
+                          double* work, cudaStream_t st) {
+  if (batch == 0) return cudaSuccess;
+  const int n = 1 << (P.log_n - 1);
+  const int block = n / 2 < 512 ? (n / 2 < 32 ? 32 : n / 2) : 512;
+  if (P.log_n <= 14) {
+    const size_t smem = 2 * sizeof(double) * (size_t)n;
+    cudaError_t e = cudaFuncSetAttribute(k_encode_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_encode_smem<<<batch, block, smem, st>>>(P, slots, n_slots, out);
+  } else {
+    k_encode_gmem<<<batch, block, 0, st>>>(P, slots, n_slots, out, work);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ntt_inv(const DevParams& P, u64* data, uint32_t batch, cudaStream_t st) {
+  if (batch == 0) return cudaSuccess;
+  const int N = 1 << P.log_n;
+  const int use_smem = P.log_n <= 14;
+  const size_t smem = use_smem ? sizeof(u64) * N : 0;
+  cudaError_t e = cudaFuncSetAttribute(k_ntt_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int block = N / 2 < 512 ? (N / 2 < 32 ? 32 : N / 2) : 512;
+  k_ntt_inv<<<dim3(P.L, batch), block, smem, st>>>(P, data, use_smem);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dec_mul(const DevParams& P, const u64* ct, const u64* sk, uint32_t batch, u64* out,
+                           cudaStream_t st) {
+  const size_t total = (size_t)batch * P.L << P.log_n;
+  k_dec_mul<<<grid_for(total, 256), 256, 0, st>>>(P, ct, sk, batch, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_decode(const DevParams& P, const u64* coeffs, uint32_t batch, uint32_t n_slots, double* out,
+                          double* work, cudaStream_t st) {
+  if (batch == 0) return cudaSuccess;
+  const int n = 1 << (P.log_n - 1);
+  const int block = n / 2 < 256 ? (n / 2 < 32 ? 32 : n / 2) : 256;
+  k_decode<<<batch, block, 0, st>>>(P, coeffs, n_slots, out, work);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add(const DevParams& P, const u64* a, const u64* b, uint32_t batch, u64* out, cudaStream_t st) {
+  const size_t total = (size_t)batch * 2 * P.L << P.log_n;
+  k_add<<<grid_for(total, 256), 256, 0, st>>>(P, a, b, batch, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_shoup(const DevParams& P, const u64* w, u64* ws, uint32_t polys, cudaStream_t st) {
+  const size_t total = (size_t)polys * P.L << P.log_n;
+  k_shoup<<<grid_for(total, 256), 256, 0, st>>>(P, w, ws, polys);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sk_residues(const DevParams& P, const int8_t* s, u64* out, cudaStream_t st) {
+  const size_t total = (size_t)P.L << P.log_n;
+  k_sk_residues<<<grid_for(total, 256), 256, 0, st>>>(P, s, out);
+  return cudaGetLastError();
+}
+
+}  // namespace zn

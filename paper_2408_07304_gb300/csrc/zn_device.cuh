@@ -1,0 +1,369 @@
+// Device-side building blocks for the sm_103a encryption path:
+//   * 64-bit modular arithmetic (Shoup multiplication by a precomputed
+//     constant, Barrett reduction of signed integers, Harvey lazy butterflies);
+//   * Philox4x32-10 and the three samplers (R_2, chi, R_q);
+//   * a shared-memory-staged negacyclic NTT with radix-16 register passes;
+//   * the FP64 radix-2 FFT of the CKKS encoder with a fixed operation order.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace zn {
+
+typedef uint64_t u64;
+typedef int64_t i64;
+typedef unsigned __int128 u128;
+
+constexpr int kMaxL = 16;
+constexpr int kCdt = 38;
+constexpr int kBound = 19;
+
+// Everything a kernel needs about one parameter set; passed by value.
+struct DevParams {
+  int log_n, L, log2_delta, pad;
+  u64 q[kMaxL];
+  u64 mu[kMaxL];             // floor(2^64 / q): Barrett reduction
+  u64 ninv[kMaxL];           // N^-1 mod q
+  u64 ninvs[kMaxL];          // its Shoup companion
+  u64 q0inv_mod_q1;          // CRT (decode)
+  u64 cdt[kCdt];             // chi thresholds
+  const u64* tw;             // [L][N] psi^brv(k)
+  const u64* tws;            // [L][N] Shoup companions
+  const u64* itw;            // [L][N] psi^-brv(k)
+  const u64* itws;
+  const double* etw;         // [2][N] encoder twiddles: re, then im
+  const int* slot_of_t;      // [N/2] slot j with (5^j mod 2N - 1)/4 = t
+  unsigned* status;          // device status word (bit 0: encode overflow)
+};
+
+enum : unsigned { kStatusOverflow = 1u, kStatusTimeout = 2u };
+
+// ------------------------------------------------------------ modular math
+
+// x*w mod q up to one q: result in [0, 2q) for any x < 2^64 (w < q, wp = floor(w 2^64 / q)).
+__device__ __forceinline__ u64 mul_shoup(u64 x, u64 w, u64 wp, u64 q) {
+  u64 h = __umul64hi(x, wp);
+  return x * w - h * q;
+}
+
+// [0, 4q) -> [0, q)
+__device__ __forceinline__ u64 reduce4(u64 x, u64 q) {
+  if (x >= 2 * q) x -= 2 * q;
+  if (x >= q) x -= q;
+  return x;
+}
+
+// [0, 8q) -> [0, q)
+__device__ __forceinline__ u64 reduce8(u64 x, u64 q) {
+  if (x >= 4 * q) x -= 4 * q;
+  return reduce4(x, q);
+}
+
+// signed 64-bit integer -> residue in [0, q)
+__device__ __forceinline__ u64 reduce_signed(i64 x, u64 q, u64 mu) {
+  u64 a = x < 0 ? (u64)0 - (u64)x : (u64)x;
+  u64 r = a - __umul64hi(a, mu) * q;       // [0, 2q)
+  if (r >= q) r -= q;
+  return (x < 0 && r) ? q - r : r;
+}
+
+// small signed integer (|v| < q) -> residue
+__device__ __forceinline__ u64 small_res(int v, u64 q) {
+  return v < 0 ? q - (u64)(-(i64)v) : (u64)v;
+}
+
+// general a*b mod q (slow path: keygen and imports only)
+__device__ __forceinline__ u64 mulmod_slow(u64 a, u64 b, u64 q) {
+  return (u64)(((u128)a * b) % q);
+}
+__device__ __forceinline__ u64 shoup_of(u64 w, u64 q) {
+  return (u64)(((u128)w << 64) / q);
+}
+
+// Harvey forward (Cooley-Tukey) butterfly; inputs and outputs in [0, 4q).
+__device__ __forceinline__ void ct_bfly(u64& x, u64& y, u64 w, u64 wp, u64 q) {
+  u64 a = x >= 2 * q ? x - 2 * q : x;
+  u64 t = mul_shoup(y, w, wp, q);
+  x = a + t;
+  y = a - t + 2 * q;
+}
+
+// ------------------------------------------------------------------ Philox
+
+__device__ __forceinline__ uint4 philox10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k.x += 0x9E3779B9u;
+      k.y += 0xBB67AE85u;
+    }
+    unsigned lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    unsigned lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+  }
+  return c;
+}
+
+// counter = (block, domain<<24 | poly<<16 | prime, lo32 ct, hi32 ct), key = seed
+__device__ __forceinline__ uint4 zn_rand(u64 seed, unsigned block, unsigned tag, u64 ct) {
+  return philox10(make_uint4(block, tag, (unsigned)ct, (unsigned)(ct >> 32)),
+                  make_uint2((unsigned)seed, (unsigned)(seed >> 32)));
+}
+__device__ __forceinline__ unsigned rand_tag(unsigned domain, unsigned poly, unsigned prime) {
+  return (domain << 24) | (poly << 16) | prime;
+}
+
+// R_2: floor(3 w / 2^32) - 1
+__device__ __forceinline__ int ternary_of(unsigned w) {
+  return (int)(((u64)w * 3ull) >> 32) - 1;
+}
+
+// chi: -19 + #{j : U >= T_j}
+__device__ __forceinline__ int cdt_of(unsigned lo, unsigned hi, const u64* cdt) {
+  u64 u = ((u64)hi << 32) | lo;
+  int c = 0;
+#pragma unroll
+  for (int j = 0; j < kCdt; ++j) c += (u >= cdt[j]) ? 1 : 0;
+  return c - kBound;
+}
+
+// R_q: floor(W q / 2^128), W = w3:w2:w1:w0
+__device__ __forceinline__ u64 uniform_of(uint4 w, u64 q) {
+  u64 lo = ((u64)w.y << 32) | w.x, hi = ((u64)w.w << 32) | w.z;
+  u64 a = __umul64hi(lo, q);
+  u64 plo = hi * q, phi = __umul64hi(hi, q);
+  u64 s = plo + a;
+  return phi + (s < a ? 1ull : 0ull);
+}
+
+// ------------------------------------------------------------------ NTT
+
+template <int LOGN>
+struct NttShape {
+  static constexpr int N = 1 << LOGN;
+  static constexpr int LOGT = LOGN >= 5 ? LOGN - 5 : 0;
+  static constexpr int T = 1 << LOGT;                 // threads per transform
+  static constexpr int PER = N / T;                   // elements per thread (32)
+  static constexpr int KMAX = 4;                      // butterfly stages per register pass
+  // shared-memory swizzle i ^ ((i >> SA) & 15) ^ ((i >> SB) & 15): a bijection that
+  // keeps every phase's 64-bit accesses (and the generators' consecutive
+  // writes) free of bank conflicts; parameters found by exhaustive check per N
+  static constexpr int SA = LOGN <= 9 ? 2 : LOGN == 10 ? 3 : LOGN == 11 ? 4 : LOGN == 12 ? 2 : LOGN == 13 ? 2
+                          : LOGN == 14 ? 3 : 4;
+  static constexpr int SB = LOGN <= 7 ? SA : LOGN == 8 ? 3 : LOGN == 9 ? 5 : LOGN == 10 ? 4 : LOGN == 11 ? 4
+                          : LOGN == 12 ? 4 : LOGN == 13 ? 5 : 4;
+};
+
+template <int LOGN>
+__device__ __forceinline__ int swz(int i) {
+  using S = NttShape<LOGN>;
+  if constexpr (S::SA == S::SB) return i ^ ((i >> S::SA) & 15);
+  else return i ^ ((i >> S::SA) & 15) ^ ((i >> S::SB) & 15);
+}
+
+// One pass over index bits [LO, LO+K): each thread takes its groups of 2^K
+// elements (one group at a time, in registers), runs K butterfly stages and
+// writes the group back to the same shared-memory slots -- or, in the last
+// pass (LO == 0), hands every output to store(idx, x).  The twiddle of stage
+// bit b for index idx is tw[tmul * 2^(LOGN-1-b) + (idx >> (b+1))]; tmul = 1
+// for a full transform, 2 + h for half h of a transform of twice the size.
+template <int LOGN, int LO, int K, class Store>
+__device__ __forceinline__ void ntt_pass(u64* sm, int t, const u64* __restrict__ tw, const u64* __restrict__ tws,
+                                         int tmul, u64 q, Store& store) {
+  using S = NttShape<LOGN>;
+  constexpr int G = S::PER >> K;
+#pragma unroll 1
+  for (int j = 0; j < G; ++j) {
+    const int g = t + j * S::T;
+    const int ghi = g >> LO;
+    const int base = (g & ((1 << LO) - 1)) | (ghi << (LO + K));
+    u64 v[1 << K];
+#pragma unroll
+    for (int r = 0; r < (1 << K); ++r) v[r] = sm[swz<LOGN>(base | (r << LO))];
+#pragma unroll
+    for (int s = K - 1; s >= 0; --s) {
+      const int m = tmul << (LOGN - 1 - LO - s);
+#pragma unroll
+      for (int r = 0; r < (1 << K); ++r) {
+        if (r & (1 << s)) continue;
+        const int k = m + ((ghi << (K - s - 1)) | (r >> (s + 1)));
+        ct_bfly(v[r], v[r + (1 << s)], __ldg(tw + k), __ldg(tws + k), q);
+      }
+    }
+    if constexpr (LO == 0) {
+#pragma unroll
+      for (int r = 0; r < (1 << K); ++r) store(base | r, v[r]);
+    } else {
+#pragma unroll
+      for (int r = 0; r < (1 << K); ++r) sm[swz<LOGN>(base | (r << LO))] = v[r];
+    }
+  }
+}
+
+template <int LOGN, int HI, class Store>
+__device__ __forceinline__ void ntt_chain(u64* sm, int t, const u64* tw, const u64* tws, int tmul, u64 q,
+                                          Store& store) {
+  constexpr int K = HI < NttShape<LOGN>::KMAX ? HI : NttShape<LOGN>::KMAX;
+  constexpr int LO = HI - K;
+  __syncthreads();
+  ntt_pass<LOGN, LO, K, Store>(sm, t, tw, tws, tmul, q, store);
+  if constexpr (LO > 0) ntt_chain<LOGN, LO, Store>(sm, t, tw, tws, tmul, q, store);
+}
+
+// Forward negacyclic NTT of one length-2^LOGN polynomial by the block's
+// 2^LOGT threads.  On entry sm[swz(k)] holds coefficient k in [0, 4q) (written
+// by one of the generators below; the call begins with a barrier).  store(idx,
+// x) is called once per output index with x in [0, 4q) congruent to ahat[idx].
+// The shared buffer may be reused after a barrier.
+template <int LOGN, class Store>
+__device__ __forceinline__ void ntt_forward(u64* sm, const u64* tw, const u64* tws, int tmul, u64 q, Store& store) {
+  ntt_chain<LOGN, LOGN, Store>(sm, threadIdx.x, tw, tws, tmul, q, store);
+}
+
+// ------------------------------------------------------------- generators
+// Each generator writes one polynomial into the swizzled shared buffer with
+// plain block-strided loops (one Philox call per loop trip).  Callers must
+// place a barrier between the previous transform's last shared-memory read
+// and the generator (ntt_forward's last phase reads shared memory).
+
+// R_2 polynomial: coefficient k comes from block k mod N/4, word k div N/4.
+template <int LOGN>
+__device__ __forceinline__ void gen_ternary(u64* sm, u64 seed, unsigned tag, u64 ct, u64 q) {
+  constexpr int Q4 = (1 << LOGN) / 4;
+  for (int blk = threadIdx.x; blk < Q4; blk += blockDim.x) {
+    const uint4 w = zn_rand(seed, (unsigned)blk, tag, ct);
+    sm[swz<LOGN>(blk)] = small_res(ternary_of(w.x), q);
+    sm[swz<LOGN>(blk + Q4)] = small_res(ternary_of(w.y), q);
+    sm[swz<LOGN>(blk + 2 * Q4)] = small_res(ternary_of(w.z), q);
+    sm[swz<LOGN>(blk + 3 * Q4)] = small_res(ternary_of(w.w), q);
+  }
+}
+
+// chi polynomial (+ optional message m): coefficient k from block k mod N/2,
+// words (0,1) for k < N/2 and (2,3) for k >= N/2.
+template <int LOGN>
+__device__ __forceinline__ void gen_gauss(u64* sm, u64 seed, unsigned tag, u64 ct, const u64* cdt,
+                                          const i64* __restrict__ m, u64 q, u64 mu) {
+  constexpr int H = (1 << LOGN) / 2;
+  for (int blk = threadIdx.x; blk < H; blk += blockDim.x) {
+    const uint4 w = zn_rand(seed, (unsigned)blk, tag, ct);
+    const int e0 = cdt_of(w.x, w.y, cdt), e1 = cdt_of(w.z, w.w, cdt);
+    if (m) {
+      sm[swz<LOGN>(blk)] = reduce_signed(__ldg(m + blk) + e0, q, mu);
+      sm[swz<LOGN>(blk + H)] = reduce_signed(__ldg(m + blk + H) + e1, q, mu);
+    } else {
+      sm[swz<LOGN>(blk)] = small_res(e0, q);
+      sm[swz<LOGN>(blk + H)] = small_res(e1, q);
+    }
+  }
+}
+
+// R_q residues for one prime: coefficient k from block k.
+template <int LOGN>
+__device__ __forceinline__ void gen_uniform(u64* sm, u64 seed, unsigned tag, u64 ct, u64 q) {
+  for (int k = threadIdx.x; k < (1 << LOGN); k += blockDim.x) sm[swz<LOGN>(k)] = uniform_of(zn_rand(seed, k, tag, ct), q);
+}
+
+// Plain residues from global memory.
+template <int LOGN>
+__device__ __forceinline__ void gen_copy(u64* sm, const u64* __restrict__ a) {
+  for (int k = threadIdx.x; k < (1 << LOGN); k += blockDim.x) sm[swz<LOGN>(k)] = a[k];
+}
+
+// ---------------------------------------------- generators, half transforms
+// For N = 2^(LOGH+1) split into two halves handled by separate blocks, block
+// h computes the first butterfly stage (distance N/2, twiddle tw[1]) while
+// generating, and then runs a 2^LOGH transform with tmul = 2 + h.  Slot k of
+// the half holds first_stage(a_k, a_{k+N/2}).
+
+__device__ __forceinline__ u64 first_stage(u64 a, u64 b, int h, u64 w1, u64 w1s, u64 q) {
+  const u64 tt = mul_shoup(b, w1, w1s, q);     // [0, 2q)
+  return h == 0 ? a + tt : a - tt + 2 * q;     // [0, 4q)
+}
+
+// R_2 over N = 2^(LOGH+1): coefficient k from block k mod N/4 = k mod 2^(LOGH-1)
+// and word k div 2^(LOGH-1); the partner k + N/2 is the same block, word + 2.
+template <int LOGH>
+__device__ __forceinline__ void gen_ternary_half(u64* sm, int h, u64 seed, unsigned tag, u64 ct, u64 q, u64 w1,
+                                                 u64 w1s) {
+  constexpr int Q = (1 << LOGH) / 2;
+  for (int blk = threadIdx.x; blk < Q; blk += blockDim.x) {
+    const uint4 w = zn_rand(seed, (unsigned)blk, tag, ct);
+    sm[swz<LOGH>(blk)] = first_stage(small_res(ternary_of(w.x), q), small_res(ternary_of(w.z), q), h, w1, w1s, q);
+    sm[swz<LOGH>(blk + Q)] = first_stage(small_res(ternary_of(w.y), q), small_res(ternary_of(w.w), q), h, w1, w1s, q);
+  }
+}
+
+// chi (+ m) over N = 2^(LOGH+1): coefficient k < N/2 from block k, words
+// (0,1); its partner k + N/2 from the same block, words (2,3).
+template <int LOGH>
+__device__ __forceinline__ void gen_gauss_half(u64* sm, int h, u64 seed, unsigned tag, u64 ct, const u64* cdt,
+                                               const i64* __restrict__ m, u64 q, u64 mu, u64 w1, u64 w1s) {
+  constexpr int HALF = 1 << LOGH;
+  for (int k = threadIdx.x; k < HALF; k += blockDim.x) {
+    const uint4 w = zn_rand(seed, (unsigned)k, tag, ct);
+    const int e0 = cdt_of(w.x, w.y, cdt), e1 = cdt_of(w.z, w.w, cdt);
+    u64 a, b;
+    if (m) {
+      a = reduce_signed(__ldg(m + k) + e0, q, mu);
+      b = reduce_signed(__ldg(m + k + HALF) + e1, q, mu);
+    } else {
+      a = small_res(e0, q);
+      b = small_res(e1, q);
+    }
+    sm[swz<LOGH>(k)] = first_stage(a, b, h, w1, w1s, q);
+  }
+}
+
+template <int LOGH>
+__device__ __forceinline__ void gen_uniform_half(u64* sm, int h, u64 seed, unsigned tag, u64 ct, u64 q, u64 w1,
+                                                 u64 w1s) {
+  constexpr int HALF = 1 << LOGH;
+  for (int k = threadIdx.x; k < HALF; k += blockDim.x) {
+    const u64 a = uniform_of(zn_rand(seed, (unsigned)k, tag, ct), q);
+    const u64 b = uniform_of(zn_rand(seed, (unsigned)(k + HALF), tag, ct), q);
+    sm[swz<LOGH>(k)] = first_stage(a, b, h, w1, w1s, q);
+  }
+}
+
+template <int LOGH>
+__device__ __forceinline__ void gen_copy_half(u64* sm, int h, const u64* __restrict__ a, u64 q, u64 w1, u64 w1s) {
+  constexpr int HALF = 1 << LOGH;
+  for (int k = threadIdx.x; k < HALF; k += blockDim.x) sm[swz<LOGH>(k)] = first_stage(a[k], a[k + HALF], h, w1, w1s, q);
+}
+
+// --------------------------------------------------------- encoder FFT (FP64)
+
+// Radix-2 decimation-in-time FFT of length n = N/2 on (re, im), input already
+// in bit-reversed order; stage with half-size h uses w = T[k N / h].  The
+// butterfly performs, in this order and each separately rounded:
+//   tr = c.re*w.re - c.im*w.im; ti = c.re*w.im + c.im*w.re;
+//   (a.re + tr, a.im + ti), (a.re - tr, a.im - ti).
+// `conj` selects conj(T) (the decoder's inverse transform).
+__device__ __forceinline__ void fft_dit(double* re, double* im, int log_n, const double* etw, bool conj) {
+  const int n = 1 << (log_n - 1), N = 1 << log_n;
+  const double* twr = etw;
+  const double* twi = etw + N;
+  for (int lh = 0; (1 << lh) < n; ++lh) {
+    const int h = 1 << lh;
+    for (int idx = threadIdx.x; idx < n / 2; idx += blockDim.x) {
+      const int k = idx & (h - 1);
+      const int p = ((idx >> lh) << (lh + 1)) + k;
+      const int ti_ = k * (N >> lh);
+      const double wr = __ldg(twr + ti_);
+      const double wi = conj ? -__ldg(twi + ti_) : __ldg(twi + ti_);
+      const double ar = re[p], ai = im[p], cr = re[p + h], ci = im[p + h];
+      const double tr = __dsub_rn(__dmul_rn(cr, wr), __dmul_rn(ci, wi));
+      const double tim = __dadd_rn(__dmul_rn(cr, wi), __dmul_rn(ci, wr));
+      re[p] = __dadd_rn(ar, tr);
+      im[p] = __dadd_rn(ai, tim);
+      re[p + h] = __dsub_rn(ar, tr);
+      im[p + h] = __dsub_rn(ai, tim);
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ int brv_bits(int x, int bits) { return (int)(__brev((unsigned)x) >> (32 - bits)); }
+
+}  // namespace zn

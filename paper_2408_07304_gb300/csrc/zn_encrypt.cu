@@ -1,0 +1,156 @@
+// Hot path: fused per-(prime, ciphertext) encryption kernels for sm_103a.
+//
+// One block owns one RNS limb of one ciphertext.  It samples the small
+// polynomials with Philox4x32-10 straight into shared memory, runs the
+// register-blocked negacyclic NTT (Shoup multiplication, Harvey lazy
+// butterflies), and fuses the epilogue:
+//   vanilla (Eq. 8):      c0 = pk0*u + NTT(m + e0),  c1 = pk1*u + NTT(e1)
+//   Zinc (Algorithm 1):   c0' = z0 + NTT(m + e1'),   c1' = z1 + NTT(e2')
+// The encoded message m is the int64 output of the encoder kernel.
+#include "zn_kernels.h"
+
+namespace zn {
+
+template <int LOGN, bool ZINC>
+__global__ void __launch_bounds__(NttShape<LOGN>::T) k_encrypt(DevParams P, EncArgs A) {
+  using S = NttShape<LOGN>;
+  extern __shared__ u64 sm[];
+  const int i = blockIdx.x, L = P.L;
+  const size_t b = blockIdx.y;
+  const u64 q = P.q[i], mu = P.mu[i];
+  const u64* tw = P.tw + (size_t)i * S::N;
+  const u64* tws = P.tws + (size_t)i * S::N;
+  const u64 ct = A.ct_index ? A.ct_index[b] : A.ct_index0 + b;
+  u64* c0 = A.out + (b * 2 * L + i) * S::N;
+  u64* c1 = c0 + (size_t)L * S::N;
+  const i64* m = A.m ? A.m + b * S::N : nullptr;
+  const u64* k0 = A.key + (size_t)i * S::N;
+  const u64* k1 = k0 + (size_t)L * S::N;
+  if constexpr (!ZINC) {
+    const u64* k0s = A.keys + (size_t)i * S::N;
+    const u64* k1s = k0s + (size_t)L * S::N;
+    // u-hat, then the two key products (kept lazily in [0, 2q) in the output)
+    gen_ternary<LOGN>(sm, A.seed, rand_tag(A.domain, 0, 0), ct, q);
+    auto st_u = [&](int idx, u64 x) {
+      const u64 uh = reduce4(x, q);
+      c0[idx] = mul_shoup(uh, __ldg(k0 + idx), __ldg(k0s + idx), q);
+      c1[idx] = mul_shoup(uh, __ldg(k1 + idx), __ldg(k1s + idx), q);
+    };
+    ntt_forward<LOGN>(sm, tw, tws, 1, q, st_u);
+    // m + e0 -> c0
+    __syncthreads();
+    gen_gauss<LOGN>(sm, A.seed, rand_tag(A.domain, 1, 0), ct, P.cdt, m, q, mu);
+    auto st_0 = [&](int idx, u64 x) { c0[idx] = reduce8(c0[idx] + x, q); };
+    ntt_forward<LOGN>(sm, tw, tws, 1, q, st_0);
+    // e1 -> c1
+    __syncthreads();
+    gen_gauss<LOGN>(sm, A.seed, rand_tag(A.domain, 2, 0), ct, P.cdt, nullptr, q, mu);
+    auto st_1 = [&](int idx, u64 x) { c1[idx] = reduce8(c1[idx] + x, q); };
+    ntt_forward<LOGN>(sm, tw, tws, 1, q, st_1);
+  } else {
+    gen_gauss<LOGN>(sm, A.seed, rand_tag(A.domain, 0, 0), ct, P.cdt, m, q, mu);
+    auto st_0 = [&](int idx, u64 x) { c0[idx] = reduce8(__ldg(k0 + idx) + x, q); };
+    ntt_forward<LOGN>(sm, tw, tws, 1, q, st_0);
+    __syncthreads();
+    gen_gauss<LOGN>(sm, A.seed, rand_tag(A.domain, 1, 0), ct, P.cdt, nullptr, q, mu);
+    auto st_1 = [&](int idx, u64 x) { c1[idx] = reduce8(__ldg(k1 + idx) + x, q); };
+    ntt_forward<LOGN>(sm, tw, tws, 1, q, st_1);
+  }
+}
+
+// N = 2^(LOGH+1) (one limb exceeds shared memory): grid (2L, B); block
+// x = 2i + h produces output half h of prime i.
+template <int LOGH, bool ZINC>
+__global__ void __launch_bounds__(NttShape<LOGH>::T) k_encrypt_half(DevParams P, EncArgs A) {
+  using S = NttShape<LOGH>;
+  constexpr int N = 2 << LOGH, HALF = 1 << LOGH;
+  extern __shared__ u64 sm[];
+  const int i = blockIdx.x >> 1, h = blockIdx.x & 1, L = P.L;
+  const size_t b = blockIdx.y;
+  const u64 q = P.q[i], mu = P.mu[i];
+  const u64* tw = P.tw + (size_t)i * N;
+  const u64* tws = P.tws + (size_t)i * N;
+  const u64 w1 = __ldg(tw + 1), w1s = __ldg(tws + 1);
+  const u64 ct = A.ct_index ? A.ct_index[b] : A.ct_index0 + b;
+  const size_t off = (size_t)h * HALF;
+  u64* c0 = A.out + (b * 2 * L + i) * N + off;
+  u64* c1 = c0 + (size_t)L * N;
+  const i64* m = A.m ? A.m + b * N : nullptr;
+  const u64* k0 = A.key + (size_t)i * N + off;
+  const u64* k1 = k0 + (size_t)L * N;
+  const int tmul = 2 + h;
+  if constexpr (!ZINC) {
+    const u64* k0s = A.keys + (size_t)i * N + off;
+    const u64* k1s = k0s + (size_t)L * N;
+    gen_ternary_half<LOGH>(sm, h, A.seed, rand_tag(A.domain, 0, 0), ct, q, w1, w1s);
+    auto st_u = [&](int idx, u64 x) {
+      const u64 uh = reduce4(x, q);
+      c0[idx] = mul_shoup(uh, __ldg(k0 + idx), __ldg(k0s + idx), q);
+      c1[idx] = mul_shoup(uh, __ldg(k1 + idx), __ldg(k1s + idx), q);
+    };
+    ntt_forward<LOGH>(sm, tw, tws, tmul, q, st_u);
+    __syncthreads();
+    gen_gauss_half<LOGH>(sm, h, A.seed, rand_tag(A.domain, 1, 0), ct, P.cdt, m, q, mu, w1, w1s);
+    auto st_0 = [&](int idx, u64 x) { c0[idx] = reduce8(c0[idx] + x, q); };
+    ntt_forward<LOGH>(sm, tw, tws, tmul, q, st_0);
+    __syncthreads();
+    gen_gauss_half<LOGH>(sm, h, A.seed, rand_tag(A.domain, 2, 0), ct, P.cdt, nullptr, q, mu, w1, w1s);
+    auto st_1 = [&](int idx, u64 x) { c1[idx] = reduce8(c1[idx] + x, q); };
+    ntt_forward<LOGH>(sm, tw, tws, tmul, q, st_1);
+  } else {
+    gen_gauss_half<LOGH>(sm, h, A.seed, rand_tag(A.domain, 0, 0), ct, P.cdt, m, q, mu, w1, w1s);
+    auto st_0 = [&](int idx, u64 x) { c0[idx] = reduce8(__ldg(k0 + idx) + x, q); };
+    ntt_forward<LOGH>(sm, tw, tws, tmul, q, st_0);
+    __syncthreads();
+    gen_gauss_half<LOGH>(sm, h, A.seed, rand_tag(A.domain, 1, 0), ct, P.cdt, nullptr, q, mu, w1, w1s);
+    auto st_1 = [&](int idx, u64 x) { c1[idx] = reduce8(__ldg(k1 + idx) + x, q); };
+    ntt_forward<LOGH>(sm, tw, tws, tmul, q, st_1);
+  }
+}
+
+template <int LOGN, bool ZINC>
+static cudaError_t enc_full(const DevParams& P, const EncArgs& A, uint32_t batch, cudaStream_t st) {
+  using S = NttShape<LOGN>;
+  const size_t smem = sizeof(u64) * S::N;
+  cudaError_t e = cudaFuncSetAttribute(k_encrypt<LOGN, ZINC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_encrypt<LOGN, ZINC><<<dim3(P.L, batch), S::T, smem, st>>>(P, A);
+  return cudaGetLastError();
+}
+
+template <int LOGH, bool ZINC>
+static cudaError_t enc_half(const DevParams& P, const EncArgs& A, uint32_t batch, cudaStream_t st) {
+  using S = NttShape<LOGH>;
+  const size_t smem = sizeof(u64) * S::N;
+  cudaError_t e =
+      cudaFuncSetAttribute(k_encrypt_half<LOGH, ZINC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_encrypt_half<LOGH, ZINC><<<dim3(2 * P.L, batch), S::T, smem, st>>>(P, A);
+  return cudaGetLastError();
+}
+
+template <bool ZINC>
+static cudaError_t enc_dispatch(const DevParams& P, const EncArgs& A, uint32_t batch, cudaStream_t st) {
+  switch (P.log_n) {
+    case 4: return enc_full<4, ZINC>(P, A, batch, st);
+    case 5: return enc_full<5, ZINC>(P, A, batch, st);
+    case 6: return enc_full<6, ZINC>(P, A, batch, st);
+    case 7: return enc_full<7, ZINC>(P, A, batch, st);
+    case 8: return enc_full<8, ZINC>(P, A, batch, st);
+    case 9: return enc_full<9, ZINC>(P, A, batch, st);
+    case 10: return enc_full<10, ZINC>(P, A, batch, st);
+    case 11: return enc_full<11, ZINC>(P, A, batch, st);
+    case 12: return enc_full<12, ZINC>(P, A, batch, st);
+    case 13: return enc_full<13, ZINC>(P, A, batch, st);
+    case 14: return enc_full<14, ZINC>(P, A, batch, st);
+    case 15: return enc_half<14, ZINC>(P, A, batch, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_encrypt(const DevParams& P, const EncArgs& A, bool zinc, uint32_t batch, cudaStream_t st) {
+  if (batch == 0) return cudaSuccess;
+  return zinc ? enc_dispatch<true>(P, A, batch, st) : enc_dispatch<false>(P, A, batch, st);
+}
+
+}  // namespace zn

@@ -1,0 +1,34 @@
+// Launchers of the sm_103a kernels (zn_kernels.cu); used by the C ABI layer.
+#pragma once
+#include "zn_device.cuh"
+
+namespace zn {
+
+struct EncArgs {
+  const u64* key;       // vanilla: pk [2][L][N]; Zinc: cache [2][L][N]
+  const u64* keys;      // vanilla: pk Shoup companions [2][L][N]; Zinc: unused
+  const i64* m;         // [B][N] encoded messages (nullptr: zero plaintext)
+  const u64* ct_index;  // [B] or nullptr (then ct_index0 + b)
+  u64 ct_index0;
+  u64 seed;
+  unsigned domain;
+  u64* out;             // [B][2][L][N]
+};
+
+cudaError_t launch_encode(const DevParams& P, const double* slots, uint32_t n_slots, uint32_t batch, i64* out,
+                          double* work, cudaStream_t st);
+cudaError_t launch_encrypt(const DevParams& P, const EncArgs& A, bool zinc, uint32_t batch, cudaStream_t st);
+cudaError_t launch_keygen(const DevParams& P, u64 seed, u64* sk_ntt, u64* pk, u64* pks, cudaStream_t st);
+cudaError_t launch_ntt_fwd(const DevParams& P, u64* data, uint32_t batch, u64* tmp, cudaStream_t st);
+cudaError_t launch_ntt_inv(const DevParams& P, u64* data, uint32_t batch, cudaStream_t st);
+cudaError_t launch_dec_mul(const DevParams& P, const u64* ct, const u64* sk, uint32_t batch, u64* out,
+                           cudaStream_t st);
+cudaError_t launch_decode(const DevParams& P, const u64* coeffs, uint32_t batch, uint32_t n_slots, double* out,
+                          double* work, cudaStream_t st);
+cudaError_t launch_add(const DevParams& P, const u64* a, const u64* b, uint32_t batch, u64* out, cudaStream_t st);
+cudaError_t launch_sample(const DevParams& P, int kind, u64 seed, unsigned domain, unsigned poly, unsigned prime,
+                          u64 ct_index0, uint32_t count, i64* out, cudaStream_t st);
+cudaError_t launch_shoup(const DevParams& P, const u64* w, u64* ws, uint32_t polys, cudaStream_t st);
+cudaError_t launch_sk_residues(const DevParams& P, const int8_t* s, u64* out, cudaStream_t st);
+
+}  // namespace zn
