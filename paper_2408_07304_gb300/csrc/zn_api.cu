@@ -132,8 +132,9 @@ uint32_t encode_chunk(const zn_ctx* c) {
 
 int encrypt_common(zn_ctx* c, bool zinc, const u64* key, const u64* keys, const double* slots, uint32_t n_slots,
                    uint32_t batch, uint64_t seed, const uint64_t* ct_index, uint64_t* ct, void* stream) {
-  if (!c || !key || !ct || !ct_index || n_slots > c->n / 2 || (n_slots && !slots)) return ZN_EINVAL;
+  if (!c || !key || n_slots > c->n / 2) return ZN_EINVAL;
   if (batch == 0) return ZN_OK;
+  if (!ct || !ct_index || (n_slots && !slots)) return ZN_EINVAL;
   DeviceGuard g(c->device);
   const uint32_t chunk = encode_chunk(c);
   const uint32_t first = batch < chunk ? batch : chunk;
@@ -493,8 +494,9 @@ int zn_sk_import(zn_ctx* c, const int8_t* host_in, zn_sk** out) {
 // --------------------------------------------------------------- encode
 
 int ckks_encode(zn_ctx* c, const double* slots, uint32_t n_slots, uint32_t batch, int64_t* out, void* stream) {
-  if (!c || !out || n_slots > c->n / 2 || (n_slots && !slots)) return ZN_EINVAL;
+  if (!c || n_slots > c->n / 2) return ZN_EINVAL;
   if (batch == 0) return ZN_OK;
+  if (!out || (n_slots && !slots)) return ZN_EINVAL;
   DeviceGuard g(c->device);
   int rc;
   if (c->prm.log_n > 14 && (rc = ensure_fft(c, batch))) return rc;
@@ -591,8 +593,9 @@ int zinc_encrypt(zn_ctx* c, const zn_zcache* z, const double* slots, uint32_t n_
 // -------------------------------------------------------------- decrypt
 
 int ckks_decrypt(zn_ctx* c, const zn_sk* sk, const uint64_t* ct, uint32_t batch, uint64_t* out, void* stream) {
-  if (!c || !sk || sk->ctx != c || !ct || !out) return ZN_EINVAL;
+  if (!c || !sk || sk->ctx != c) return ZN_EINVAL;
   if (batch == 0) return ZN_OK;
+  if (!ct || !out) return ZN_EINVAL;
   DeviceGuard g(c->device);
   ZN_CUDA(zn::launch_dec_mul(c->dp, ct, sk->d, batch, out, S(stream)));
   ZN_CUDA(zn::launch_ntt_inv(c->dp, out, batch, S(stream)));
@@ -601,8 +604,9 @@ int ckks_decrypt(zn_ctx* c, const zn_sk* sk, const uint64_t* ct, uint32_t batch,
 
 int ckks_decrypt_decode(zn_ctx* c, const zn_sk* sk, const uint64_t* ct, uint32_t batch, uint32_t n_slots, double* out,
                         void* stream) {
-  if (!c || !sk || sk->ctx != c || !ct || !out || n_slots > c->n / 2) return ZN_EINVAL;
+  if (!c || !sk || sk->ctx != c || n_slots > c->n / 2) return ZN_EINVAL;
   if (batch == 0 || n_slots == 0) return ZN_OK;
+  if (!ct || !out) return ZN_EINVAL;
   DeviceGuard g(c->device);
   u64* coeffs = nullptr;
   double* work = nullptr;
@@ -623,8 +627,9 @@ int ckks_decrypt_decode(zn_ctx* c, const zn_sk* sk, const uint64_t* ct, uint32_t
 }
 
 int ckks_add(zn_ctx* c, const uint64_t* a, const uint64_t* b, uint32_t batch, uint64_t* out, void* stream) {
-  if (!c || !a || !b || !out) return ZN_EINVAL;
+  if (!c) return ZN_EINVAL;
   if (batch == 0) return ZN_OK;
+  if (!a || !b || !out) return ZN_EINVAL;
   DeviceGuard g(c->device);
   ZN_CUDA(zn::launch_add(c->dp, a, b, batch, out, S(stream)));
   return ZN_OK;
@@ -633,8 +638,9 @@ int ckks_add(zn_ctx* c, const uint64_t* a, const uint64_t* b, uint32_t batch, ui
 // ------------------------------------------------------------ building blocks
 
 int zn_ntt_forward(zn_ctx* c, uint64_t* data, uint32_t batch, void* stream) {
-  if (!c || !data) return ZN_EINVAL;
+  if (!c) return ZN_EINVAL;
   if (batch == 0) return ZN_OK;
+  if (!data) return ZN_EINVAL;
   DeviceGuard g(c->device);
   u64* tmp = nullptr;
   if (c->prm.log_n > 14) {
@@ -653,8 +659,9 @@ int zn_ntt_forward(zn_ctx* c, uint64_t* data, uint32_t batch, void* stream) {
 }
 
 int zn_ntt_inverse(zn_ctx* c, uint64_t* data, uint32_t batch, void* stream) {
-  if (!c || !data) return ZN_EINVAL;
+  if (!c) return ZN_EINVAL;
   if (batch == 0) return ZN_OK;
+  if (!data) return ZN_EINVAL;
   DeviceGuard g(c->device);
   ZN_CUDA(zn::launch_ntt_inv(c->dp, data, batch, S(stream)));
   return ZN_OK;
@@ -662,8 +669,9 @@ int zn_ntt_inverse(zn_ctx* c, uint64_t* data, uint32_t batch, void* stream) {
 
 int zn_sample(zn_ctx* c, int kind, uint64_t seed, uint32_t domain, uint32_t poly, uint32_t prime, uint64_t ct_index0,
               uint32_t count, int64_t* out, void* stream) {
-  if (!c || !out || kind < 0 || kind > 2 || domain > 255 || poly > 255 || prime >= c->L) return ZN_EINVAL;
+  if (!c || kind < 0 || kind > 2 || domain > 255 || poly > 255 || prime >= c->L) return ZN_EINVAL;
   if (count == 0) return ZN_OK;
+  if (!out) return ZN_EINVAL;
   DeviceGuard g(c->device);
   ZN_CUDA(zn::launch_sample(c->dp, kind, seed, domain, poly, prime, ct_index0, count, (i64*)out, S(stream)));
   return ZN_OK;
