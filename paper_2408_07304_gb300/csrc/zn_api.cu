@@ -22,11 +22,12 @@ struct zn_ctx {
   u64 q[ZN_MAX_PRIMES], psi[ZN_MAX_PRIMES];
   DevParams dp;
   // device allocations owned by the context
-  u64* d_tw;          // tw, tws, itw, itws: 4 [L][N] tables, one allocation
+  u64* d_tw;          // (tw, tws) pairs [L][N], itw [L][N], itws [L][N]: one allocation
   double* d_etw;      // [2][N]
   int* d_slot;        // [N/2]
   unsigned* d_status;
-  i64* d_m;           // encode scratch [m_cap][N]
+  i64* d_m;           // prep scratch: message + noise [m_cap][N]
+  int8_t* d_small;    // prep scratch: small polynomials [m_cap][2][N]
   size_t m_cap;
   double* d_fft;      // FFT scratch for large rings [fft_cap][N]
   size_t fft_cap;
@@ -77,11 +78,16 @@ struct DeviceGuard {
 
 int ensure_m(zn_ctx* c, size_t cts) {
   if (cts <= c->m_cap) return ZN_OK;
-  if (c->d_m) cudaFree(c->d_m);
+  cudaFree(c->d_m);
+  cudaFree(c->d_small);
   c->d_m = nullptr;
+  c->d_small = nullptr;
   c->m_cap = 0;
-  if (cudaMalloc(&c->d_m, sizeof(i64) * cts * c->n) != cudaSuccess) {
+  if (cudaMalloc(&c->d_m, sizeof(i64) * cts * c->n) != cudaSuccess ||
+      cudaMalloc(&c->d_small, 2 * cts * (size_t)c->n) != cudaSuccess) {
     cudaGetLastError();
+    cudaFree(c->d_m);
+    c->d_m = nullptr;
     return ZN_ENOMEM;
   }
   c->m_cap = cts;
@@ -143,18 +149,25 @@ int encrypt_common(zn_ctx* c, bool zinc, const u64* key, const u64* keys, const 
   if (c->prm.log_n > 14 && (rc = ensure_fft(c, first))) return rc;
   for (uint32_t b0 = 0; b0 < batch; b0 += chunk) {
     const uint32_t nb = (batch - b0) < chunk ? (batch - b0) : chunk;
+    zn::PrepArgs pa;
+    pa.slots = slots + (size_t)b0 * n_slots;
+    pa.n_slots = n_slots;
+    pa.ct_index = ct_index + b0;
+    pa.ct_index0 = 0;
+    pa.seed = seed;
+    pa.domain = zinc ? 1u : 0u;
+    pa.me = c->d_m;
+    pa.small = c->d_small;
+    pa.work = c->d_fft;
     {
       TimedLaunch t(c, ZN_TIME_ENCODE, S(stream));
-      ZN_CUDA(zn::launch_encode(c->dp, slots + (size_t)b0 * n_slots, n_slots, nb, c->d_m, c->d_fft, S(stream)));
+      ZN_CUDA(zn::launch_prep(c->dp, pa, zinc, nb, S(stream)));
     }
     zn::EncArgs A;
     A.key = key;
     A.keys = keys;
-    A.m = c->d_m;
-    A.ct_index = ct_index + b0;
-    A.ct_index0 = 0;
-    A.seed = seed;
-    A.domain = zinc ? 1u : 0u;
+    A.me = c->d_m;
+    A.small = c->d_small;
     A.out = ct + (size_t)b0 * 2 * ring_words(c);
     TimedLaunch t(c, zinc ? ZN_TIME_ZINC : ZN_TIME_ENCRYPT, S(stream));
     ZN_CUDA(zn::launch_encrypt(c->dp, A, zinc, nb, S(stream)));
@@ -220,14 +233,22 @@ int zn_ctx_create(const zn_params* p, int device, zn_ctx** out) {
   for (uint32_t i = 0; i < L; ++i) c->psi[i] = zn::find_psi(c->q[i], p->log_n);
 
   // host tables
+  // forward twiddles interleaved with their Shoup companions (one 16-byte
+  // load per butterfly), then the inverse tables
   std::vector<u64> tabs(4 * (size_t)L * n);
-  u64* tw = tabs.data();
-  u64* tws = tw + (size_t)L * n;
-  u64* itw = tws + (size_t)L * n;
+  u64* twp = tabs.data();
+  u64* itw = twp + 2 * (size_t)L * n;
   u64* itws = itw + (size_t)L * n;
-  for (uint32_t i = 0; i < L; ++i)
-    zn::ntt_tables(c->q[i], c->psi[i], p->log_n, tw + (size_t)i * n, tws + (size_t)i * n, itw + (size_t)i * n,
-                   itws + (size_t)i * n);
+  {
+    std::vector<u64> tw(n), tws(n);
+    for (uint32_t i = 0; i < L; ++i) {
+      zn::ntt_tables(c->q[i], c->psi[i], p->log_n, tw.data(), tws.data(), itw + (size_t)i * n, itws + (size_t)i * n);
+      for (uint32_t k = 0; k < n; ++k) {
+        twp[2 * ((size_t)i * n + k)] = tw[k];
+        twp[2 * ((size_t)i * n + k) + 1] = tws[k];
+      }
+    }
+  }
   std::vector<double> etw(2 * (size_t)n);
   zn::encoder_twiddles(p->log_n, etw.data(), etw.data() + n);
   std::vector<int> slot(n / 2);
@@ -271,8 +292,7 @@ int zn_ctx_create(const zn_params* p, int device, zn_ctx** out) {
     zn_ctx_destroy(c);
     return rc;
   }
-  dp.tw = c->d_tw;
-  dp.tws = c->d_tw + (size_t)L * n;
+  dp.twp = reinterpret_cast<const ulonglong2*>(c->d_tw);
   dp.itw = c->d_tw + 2 * (size_t)L * n;
   dp.itws = c->d_tw + 3 * (size_t)L * n;
   dp.etw = c->d_etw;
@@ -291,6 +311,7 @@ void zn_ctx_destroy(zn_ctx* c) {
   cudaFree(c->d_slot);
   cudaFree(c->d_status);
   cudaFree(c->d_m);
+  cudaFree(c->d_small);
   cudaFree(c->d_fft);
   delete c;
 }
@@ -526,16 +547,30 @@ int zinc_precompute(zn_ctx* c, const zn_pk* pk, uint64_t seed, zn_zcache** out) 
     return ZN_ENOMEM;
   }
   // vanilla Enc of the zero plaintext, sampling domain 3, ct_index 0
+  int rc = ensure_m(c, 1);
+  if (!rc && c->prm.log_n > 14) rc = ensure_fft(c, 1);
+  if (rc) {
+    zn_zcache_destroy(z);
+    return rc;
+  }
+  zn::PrepArgs pa;
+  pa.slots = nullptr;
+  pa.n_slots = 0;
+  pa.ct_index = nullptr;
+  pa.ct_index0 = 0;
+  pa.seed = seed;
+  pa.domain = 3;
+  pa.me = c->d_m;
+  pa.small = c->d_small;
+  pa.work = c->d_fft;
   zn::EncArgs A;
   A.key = pk->d;
   A.keys = pk->d + 2 * ring_words(c);
-  A.m = nullptr;
-  A.ct_index = nullptr;
-  A.ct_index0 = 0;
-  A.seed = seed;
-  A.domain = 3;
+  A.me = c->d_m;
+  A.small = c->d_small;
   A.out = z->d;
-  if (zn::launch_encrypt(c->dp, A, false, 1, 0) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+  if (zn::launch_prep(c->dp, pa, false, 1, 0) != cudaSuccess || zn::launch_encrypt(c->dp, A, false, 1, 0) != cudaSuccess ||
+      cudaDeviceSynchronize() != cudaSuccess) {
     cudaGetLastError();
     zn_zcache_destroy(z);
     return ZN_ECUDA;

@@ -6,10 +6,12 @@ namespace zn {
 
 // ------------------------------------------------------------------ encode
 
-// One block per slot vector; (re, im) = n = N/2 doubles each, in shared
-// memory (n <= 8192) or in a global scratch area (larger rings).
-__device__ void encode_one(const DevParams& P, const double* __restrict__ z, uint32_t n_slots, double* re,
-                           double* im, i64* __restrict__ out) {
+// Encoder core: one block per slot vector; (re, im) = n = N/2 doubles each,
+// in shared memory (n <= 8192) or in a global scratch area (larger rings).
+// out(k, m_k, m_{k+n}) receives the rounded coefficients, k < n.
+template <class Out>
+__device__ __forceinline__ void encode_core(const DevParams& P, const double* __restrict__ z, uint32_t n_slots,
+                                            double* re, double* im, Out& out) {
   const int log_n = P.log_n, N = 1 << log_n, n = N >> 1;
   for (int r = threadIdx.x; r < n; r += blockDim.x) {
     const int t = brv_bits(r, log_n - 1);
@@ -34,9 +36,18 @@ __device__ void encode_one(const DevParams& P, const double* __restrict__ z, uin
       a = 0.0;
       b = 0.0;
     }
-    out[k] = (i64)a;
-    out[k + n] = (i64)b;
+    out(k, (i64)a, (i64)b);
   }
+}
+
+__device__ __forceinline__ void encode_one(const DevParams& P, const double* __restrict__ z, uint32_t n_slots,
+                                           double* re, double* im, i64* __restrict__ out) {
+  const int n = 1 << (P.log_n - 1);
+  auto st = [&](int k, i64 a, i64 b) {
+    out[k] = a;
+    out[k + n] = b;
+  };
+  encode_core(P, z, n_slots, re, im, st);
 }
 
 __global__ void k_encode_smem(DevParams P, const double* __restrict__ slots, uint32_t n_slots, i64* __restrict__ out) {
@@ -52,6 +63,69 @@ __global__ void k_encode_gmem(DevParams P, const double* __restrict__ slots, uin
   const size_t b = blockIdx.x;
   double* re = work + b * 2 * (size_t)n;
   encode_one(P, slots + b * n_slots, n_slots, re, re + n, out + b * N);
+}
+
+// -------------------------------------------------------------------- prep
+// One block per ciphertext: encode the slots and draw all of the
+// encryption's randomness once, for every prime (the integers are the same
+// for all q_i):
+//   vanilla (Eq. 8):    me = m + e0 (poly 1), small = [u (poly 0), e1 (poly 2)]
+//   Zinc (Algorithm 1): me = m + e1' (poly 0), small = [e2' (poly 1)]
+// chi block k yields coefficients k and k + N/2 -- exactly the pair that the
+// encoder's last loop produces at k.
+template <bool ZINC>
+__device__ __forceinline__ void prep_one(const DevParams& P, const PrepArgs& A, size_t b, double* re, double* im) {
+  const int N = 1 << P.log_n, n = N >> 1;
+  const u64 ct = A.ct_index ? A.ct_index[b] : A.ct_index0 + b;
+  i64* me = A.me + b * N;
+  int8_t* sp = A.small + b * 2 * (size_t)N;
+  const unsigned tag_e = rand_tag(A.domain, ZINC ? 0 : 1, 0);
+  auto st = [&](int k, i64 a, i64 c) {
+    const uint4 w = zn_rand(A.seed, (unsigned)k, tag_e, ct);
+    me[k] = a + cdt_of(w.x, w.y, P.cdt);
+    me[k + n] = c + cdt_of(w.z, w.w, P.cdt);
+  };
+  if (A.n_slots) {
+    encode_core(P, A.slots + b * A.n_slots, A.n_slots, re, im, st);
+  } else {
+    for (int k = threadIdx.x; k < n; k += blockDim.x) st(k, 0, 0);
+  }
+  if constexpr (!ZINC) {
+    const unsigned tag_u = rand_tag(A.domain, 0, 0), tag_1 = rand_tag(A.domain, 2, 0);
+    for (int blk = threadIdx.x; blk < N / 4; blk += blockDim.x) {
+      const uint4 w = zn_rand(A.seed, (unsigned)blk, tag_u, ct);
+      sp[blk] = (int8_t)ternary_of(w.x);
+      sp[blk + N / 4] = (int8_t)ternary_of(w.y);
+      sp[blk + N / 2] = (int8_t)ternary_of(w.z);
+      sp[blk + 3 * N / 4] = (int8_t)ternary_of(w.w);
+    }
+    for (int blk = threadIdx.x; blk < n; blk += blockDim.x) {
+      const uint4 w = zn_rand(A.seed, (unsigned)blk, tag_1, ct);
+      sp[N + blk] = (int8_t)cdt_of(w.x, w.y, P.cdt);
+      sp[N + blk + n] = (int8_t)cdt_of(w.z, w.w, P.cdt);
+    }
+  } else {
+    const unsigned tag_2 = rand_tag(A.domain, 1, 0);
+    for (int blk = threadIdx.x; blk < n; blk += blockDim.x) {
+      const uint4 w = zn_rand(A.seed, (unsigned)blk, tag_2, ct);
+      sp[blk] = (int8_t)cdt_of(w.x, w.y, P.cdt);
+      sp[blk + n] = (int8_t)cdt_of(w.z, w.w, P.cdt);
+    }
+  }
+}
+
+template <bool ZINC>
+__global__ void k_prep_smem(DevParams P, PrepArgs A) {
+  extern __shared__ double smd[];
+  const int n = 1 << (P.log_n - 1);
+  prep_one<ZINC>(P, A, blockIdx.x, smd, smd + n);
+}
+
+template <bool ZINC>
+__global__ void k_prep_gmem(DevParams P, PrepArgs A) {
+  const int N = 1 << P.log_n, n = N >> 1;
+  double* re = A.work + (size_t)blockIdx.x * N;
+  prep_one<ZINC>(P, A, blockIdx.x, re, re + n);
 }
 
 // ------------------------------------------------------------ inverse NTT
@@ -214,6 +288,26 @@ cudaError_t launch_encode(const DevParams& P, const double* slots, uint32_t n_sl
     k_encode_gmem<<<batch, block, 0, st>>>(P, slots, n_slots, out, work);
   }
   return cudaGetLastError();
+}
+
+template <bool ZINC>
+static cudaError_t prep_launch(const DevParams& P, const PrepArgs& A, uint32_t batch, cudaStream_t st) {
+  const int n = 1 << (P.log_n - 1);
+  const int block = n / 2 < 512 ? (n / 2 < 32 ? 32 : n / 2) : 512;
+  if (P.log_n <= 14) {
+    const size_t smem = A.n_slots ? 2 * sizeof(double) * (size_t)n : 0;
+    cudaError_t e = cudaFuncSetAttribute(k_prep_smem<ZINC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_prep_smem<ZINC><<<batch, block, smem, st>>>(P, A);
+  } else {
+    k_prep_gmem<ZINC><<<batch, block, 0, st>>>(P, A);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prep(const DevParams& P, const PrepArgs& A, bool zinc, uint32_t batch, cudaStream_t st) {
+  if (batch == 0) return cudaSuccess;
+  return zinc ? prep_launch<true>(P, A, batch, st) : prep_launch<false>(P, A, batch, st);
 }
 
 cudaError_t launch_ntt_inv(const DevParams& P, u64* data, uint32_t batch, cudaStream_t st) {

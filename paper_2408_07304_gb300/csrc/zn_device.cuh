@@ -27,8 +27,7 @@ struct DevParams {
   u64 ninvs[kMaxL];          // its Shoup companion
   u64 q0inv_mod_q1;          // CRT (decode)
   u64 cdt[kCdt];             // chi thresholds
-  const u64* tw;             // [L][N] psi^brv(k)
-  const u64* tws;            // [L][N] Shoup companions
+  const ulonglong2* twp;     // [L][N] (psi^brv(k), Shoup companion) pairs
   const u64* itw;            // [L][N] psi^-brv(k)
   const u64* itws;
   const double* etw;         // [2][N] encoder twiddles: re, then im
@@ -87,6 +86,7 @@ __device__ __forceinline__ void ct_bfly(u64& x, u64& y, u64 w, u64 wp, u64 q) {
   x = a + t;
   y = a - t + 2 * q;
 }
+__device__ __forceinline__ void ct_bfly(u64& x, u64& y, ulonglong2 w, u64 q) { ct_bfly(x, y, w.x, w.y, q); }
 
 // ------------------------------------------------------------------ Philox
 
@@ -155,11 +155,12 @@ struct NttShape {
 };
 
 template <int LOGN>
-__device__ __forceinline__ int swz(int i) {
+__host__ __device__ constexpr int swz(int i) {
   using S = NttShape<LOGN>;
-  if constexpr (S::SA == S::SB) return i ^ ((i >> S::SA) & 15);
-  else return i ^ ((i >> S::SA) & 15) ^ ((i >> S::SB) & 15);
+  return S::SA == S::SB ? (i ^ ((i >> S::SA) & 15)) : (i ^ ((i >> S::SA) & 15) ^ ((i >> S::SB) & 15));
 }
+// The swizzle is linear over GF(2): swz(a ^ b) = swz(a) ^ swz(b).  A group's
+// slots are swz(base) ^ swz(r << LO), the second term a compile-time constant.
 
 // One pass over index bits [LO, LO+K): each thread takes its groups of 2^K
 // elements (one group at a time, in registers), runs K butterfly stages and
@@ -168,8 +169,8 @@ __device__ __forceinline__ int swz(int i) {
 // bit b for index idx is tw[tmul * 2^(LOGN-1-b) + (idx >> (b+1))]; tmul = 1
 // for a full transform, 2 + h for half h of a transform of twice the size.
 template <int LOGN, int LO, int K, class Store>
-__device__ __forceinline__ void ntt_pass(u64* sm, int t, const u64* __restrict__ tw, const u64* __restrict__ tws,
-                                         int tmul, u64 q, Store& store) {
+__device__ __forceinline__ void ntt_pass(u64* sm, int t, const ulonglong2* __restrict__ twp, int tmul, u64 q,
+                                         Store& store) {
   using S = NttShape<LOGN>;
   constexpr int G = S::PER >> K;
 #pragma unroll 1
@@ -177,17 +178,17 @@ __device__ __forceinline__ void ntt_pass(u64* sm, int t, const u64* __restrict__
     const int g = t + j * S::T;
     const int ghi = g >> LO;
     const int base = (g & ((1 << LO) - 1)) | (ghi << (LO + K));
+    const int sb = swz<LOGN>(base);
     u64 v[1 << K];
 #pragma unroll
-    for (int r = 0; r < (1 << K); ++r) v[r] = sm[swz<LOGN>(base | (r << LO))];
+    for (int r = 0; r < (1 << K); ++r) v[r] = sm[sb ^ swz<LOGN>(r << LO)];
 #pragma unroll
     for (int s = K - 1; s >= 0; --s) {
-      const int m = tmul << (LOGN - 1 - LO - s);
+      const ulonglong2* tws = twp + (tmul << (LOGN - 1 - LO - s)) + (ghi << (K - s - 1));
 #pragma unroll
       for (int r = 0; r < (1 << K); ++r) {
         if (r & (1 << s)) continue;
-        const int k = m + ((ghi << (K - s - 1)) | (r >> (s + 1)));
-        ct_bfly(v[r], v[r + (1 << s)], __ldg(tw + k), __ldg(tws + k), q);
+        ct_bfly(v[r], v[r + (1 << s)], __ldg(tws + (r >> (s + 1))), q);
       }
     }
     if constexpr (LO == 0) {
@@ -195,19 +196,18 @@ __device__ __forceinline__ void ntt_pass(u64* sm, int t, const u64* __restrict__
       for (int r = 0; r < (1 << K); ++r) store(base | r, v[r]);
     } else {
 #pragma unroll
-      for (int r = 0; r < (1 << K); ++r) sm[swz<LOGN>(base | (r << LO))] = v[r];
+      for (int r = 0; r < (1 << K); ++r) sm[sb ^ swz<LOGN>(r << LO)] = v[r];
     }
   }
 }
 
 template <int LOGN, int HI, class Store>
-__device__ __forceinline__ void ntt_chain(u64* sm, int t, const u64* tw, const u64* tws, int tmul, u64 q,
-                                          Store& store) {
+__device__ __forceinline__ void ntt_chain(u64* sm, int t, const ulonglong2* twp, int tmul, u64 q, Store& store) {
   constexpr int K = HI < NttShape<LOGN>::KMAX ? HI : NttShape<LOGN>::KMAX;
   constexpr int LO = HI - K;
   __syncthreads();
-  ntt_pass<LOGN, LO, K, Store>(sm, t, tw, tws, tmul, q, store);
-  if constexpr (LO > 0) ntt_chain<LOGN, LO, Store>(sm, t, tw, tws, tmul, q, store);
+  ntt_pass<LOGN, LO, K, Store>(sm, t, twp, tmul, q, store);
+  if constexpr (LO > 0) ntt_chain<LOGN, LO, Store>(sm, t, twp, tmul, q, store);
 }
 
 // Forward negacyclic NTT of one length-2^LOGN polynomial by the block's
@@ -216,8 +216,8 @@ __device__ __forceinline__ void ntt_chain(u64* sm, int t, const u64* tw, const u
 // x) is called once per output index with x in [0, 4q) congruent to ahat[idx].
 // The shared buffer may be reused after a barrier.
 template <int LOGN, class Store>
-__device__ __forceinline__ void ntt_forward(u64* sm, const u64* tw, const u64* tws, int tmul, u64 q, Store& store) {
-  ntt_chain<LOGN, LOGN, Store>(sm, threadIdx.x, tw, tws, tmul, q, store);
+__device__ __forceinline__ void ntt_forward(u64* sm, const ulonglong2* twp, int tmul, u64 q, Store& store) {
+  ntt_chain<LOGN, LOGN, Store>(sm, threadIdx.x, twp, tmul, q, store);
 }
 
 // ------------------------------------------------------------- generators
@@ -268,6 +268,18 @@ __device__ __forceinline__ void gen_uniform(u64* sm, u64 seed, unsigned tag, u64
 template <int LOGN>
 __device__ __forceinline__ void gen_copy(u64* sm, const u64* __restrict__ a) {
   for (int k = threadIdx.x; k < (1 << LOGN); k += blockDim.x) sm[swz<LOGN>(k)] = a[k];
+}
+
+// Encoded message plus noise (int64) from the per-ciphertext scratch.
+template <int LOGN>
+__device__ __forceinline__ void gen_i64(u64* sm, const i64* __restrict__ a, u64 q, u64 mu) {
+  for (int k = threadIdx.x; k < (1 << LOGN); k += blockDim.x) sm[swz<LOGN>(k)] = reduce_signed(__ldg(a + k), q, mu);
+}
+
+// Small signed polynomial (int8) from the per-ciphertext scratch.
+template <int LOGN>
+__device__ __forceinline__ void gen_i8(u64* sm, const int8_t* __restrict__ a, u64 q) {
+  for (int k = threadIdx.x; k < (1 << LOGN); k += blockDim.x) sm[swz<LOGN>(k)] = small_res(__ldg(a + k), q);
 }
 
 // ---------------------------------------------- generators, half transforms
@@ -324,6 +336,22 @@ __device__ __forceinline__ void gen_uniform_half(u64* sm, int h, u64 seed, unsig
     const u64 b = uniform_of(zn_rand(seed, (unsigned)(k + HALF), tag, ct), q);
     sm[swz<LOGH>(k)] = first_stage(a, b, h, w1, w1s, q);
   }
+}
+
+template <int LOGH>
+__device__ __forceinline__ void gen_i64_half(u64* sm, int h, const i64* __restrict__ a, u64 q, u64 mu, u64 w1,
+                                             u64 w1s) {
+  constexpr int HALF = 1 << LOGH;
+  for (int k = threadIdx.x; k < HALF; k += blockDim.x)
+    sm[swz<LOGH>(k)] = first_stage(reduce_signed(__ldg(a + k), q, mu), reduce_signed(__ldg(a + k + HALF), q, mu), h,
+                                   w1, w1s, q);
+}
+
+template <int LOGH>
+__device__ __forceinline__ void gen_i8_half(u64* sm, int h, const int8_t* __restrict__ a, u64 q, u64 w1, u64 w1s) {
+  constexpr int HALF = 1 << LOGH;
+  for (int k = threadIdx.x; k < HALF; k += blockDim.x)
+    sm[swz<LOGH>(k)] = first_stage(small_res(__ldg(a + k), q), small_res(__ldg(a + k + HALF), q), h, w1, w1s, q);
 }
 
 template <int LOGH>

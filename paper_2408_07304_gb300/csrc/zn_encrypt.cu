@@ -1,12 +1,12 @@
 // Hot path: fused per-(prime, ciphertext) encryption kernels for sm_103a.
 //
-// One block owns one RNS limb of one ciphertext.  It samples the small
-// polynomials with Philox4x32-10 straight into shared memory, runs the
-// register-blocked negacyclic NTT (Shoup multiplication, Harvey lazy
-// butterflies), and fuses the epilogue:
+// One block owns one RNS limb of one ciphertext.  It reduces the prepared
+// integer polynomials (sampled and encoded once per ciphertext by the prep
+// kernel) mod its prime into shared memory, runs the negacyclic NTT (Shoup
+// multiplication, Harvey lazy butterflies, radix-16 register passes), and
+// fuses the epilogue:
 //   vanilla (Eq. 8):      c0 = pk0*u + NTT(m + e0),  c1 = pk1*u + NTT(e1)
 //   Zinc (Algorithm 1):   c0' = z0 + NTT(m + e1'),   c1' = z1 + NTT(e2')
-// The encoded message m is the int64 output of the encoder kernel.
 #include "zn_kernels.h"
 
 namespace zn {
@@ -18,43 +18,42 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T) k_encrypt(DevParams P, EncA
   const int i = blockIdx.x, L = P.L;
   const size_t b = blockIdx.y;
   const u64 q = P.q[i], mu = P.mu[i];
-  const u64* tw = P.tw + (size_t)i * S::N;
-  const u64* tws = P.tws + (size_t)i * S::N;
-  const u64 ct = A.ct_index ? A.ct_index[b] : A.ct_index0 + b;
+  const ulonglong2* tw = P.twp + (size_t)i * S::N;
   u64* c0 = A.out + (b * 2 * L + i) * S::N;
   u64* c1 = c0 + (size_t)L * S::N;
-  const i64* m = A.m ? A.m + b * S::N : nullptr;
+  const i64* me = A.me + b * S::N;
+  const int8_t* sp = A.small + b * 2 * S::N;
   const u64* k0 = A.key + (size_t)i * S::N;
   const u64* k1 = k0 + (size_t)L * S::N;
   if constexpr (!ZINC) {
     const u64* k0s = A.keys + (size_t)i * S::N;
     const u64* k1s = k0s + (size_t)L * S::N;
     // u-hat, then the two key products (kept lazily in [0, 2q) in the output)
-    gen_ternary<LOGN>(sm, A.seed, rand_tag(A.domain, 0, 0), ct, q);
+    gen_i8<LOGN>(sm, sp, q);
     auto st_u = [&](int idx, u64 x) {
       const u64 uh = reduce4(x, q);
       c0[idx] = mul_shoup(uh, __ldg(k0 + idx), __ldg(k0s + idx), q);
       c1[idx] = mul_shoup(uh, __ldg(k1 + idx), __ldg(k1s + idx), q);
     };
-    ntt_forward<LOGN>(sm, tw, tws, 1, q, st_u);
+    ntt_forward<LOGN>(sm, tw, 1, q, st_u);
     // m + e0 -> c0
     __syncthreads();
-    gen_gauss<LOGN>(sm, A.seed, rand_tag(A.domain, 1, 0), ct, P.cdt, m, q, mu);
+    gen_i64<LOGN>(sm, me, q, mu);
     auto st_0 = [&](int idx, u64 x) { c0[idx] = reduce8(c0[idx] + x, q); };
-    ntt_forward<LOGN>(sm, tw, tws, 1, q, st_0);
+    ntt_forward<LOGN>(sm, tw, 1, q, st_0);
     // e1 -> c1
     __syncthreads();
-    gen_gauss<LOGN>(sm, A.seed, rand_tag(A.domain, 2, 0), ct, P.cdt, nullptr, q, mu);
+    gen_i8<LOGN>(sm, sp + S::N, q);
     auto st_1 = [&](int idx, u64 x) { c1[idx] = reduce8(c1[idx] + x, q); };
-    ntt_forward<LOGN>(sm, tw, tws, 1, q, st_1);
+    ntt_forward<LOGN>(sm, tw, 1, q, st_1);
   } else {
-    gen_gauss<LOGN>(sm, A.seed, rand_tag(A.domain, 0, 0), ct, P.cdt, m, q, mu);
+    gen_i64<LOGN>(sm, me, q, mu);
     auto st_0 = [&](int idx, u64 x) { c0[idx] = reduce8(__ldg(k0 + idx) + x, q); };
-    ntt_forward<LOGN>(sm, tw, tws, 1, q, st_0);
+    ntt_forward<LOGN>(sm, tw, 1, q, st_0);
     __syncthreads();
-    gen_gauss<LOGN>(sm, A.seed, rand_tag(A.domain, 1, 0), ct, P.cdt, nullptr, q, mu);
+    gen_i8<LOGN>(sm, sp, q);
     auto st_1 = [&](int idx, u64 x) { c1[idx] = reduce8(__ldg(k1 + idx) + x, q); };
-    ntt_forward<LOGN>(sm, tw, tws, 1, q, st_1);
+    ntt_forward<LOGN>(sm, tw, 1, q, st_1);
   }
 }
 
@@ -68,43 +67,43 @@ __global__ void __launch_bounds__(NttShape<LOGH>::T) k_encrypt_half(DevParams P,
   const int i = blockIdx.x >> 1, h = blockIdx.x & 1, L = P.L;
   const size_t b = blockIdx.y;
   const u64 q = P.q[i], mu = P.mu[i];
-  const u64* tw = P.tw + (size_t)i * N;
-  const u64* tws = P.tws + (size_t)i * N;
-  const u64 w1 = __ldg(tw + 1), w1s = __ldg(tws + 1);
-  const u64 ct = A.ct_index ? A.ct_index[b] : A.ct_index0 + b;
+  const ulonglong2* tw = P.twp + (size_t)i * N;
+  const ulonglong2 w1p = __ldg(tw + 1);
+  const u64 w1 = w1p.x, w1s = w1p.y;
   const size_t off = (size_t)h * HALF;
   u64* c0 = A.out + (b * 2 * L + i) * N + off;
   u64* c1 = c0 + (size_t)L * N;
-  const i64* m = A.m ? A.m + b * N : nullptr;
+  const i64* me = A.me + b * N;
+  const int8_t* sp = A.small + b * 2 * N;
   const u64* k0 = A.key + (size_t)i * N + off;
   const u64* k1 = k0 + (size_t)L * N;
   const int tmul = 2 + h;
   if constexpr (!ZINC) {
     const u64* k0s = A.keys + (size_t)i * N + off;
     const u64* k1s = k0s + (size_t)L * N;
-    gen_ternary_half<LOGH>(sm, h, A.seed, rand_tag(A.domain, 0, 0), ct, q, w1, w1s);
+    gen_i8_half<LOGH>(sm, h, sp, q, w1, w1s);
     auto st_u = [&](int idx, u64 x) {
       const u64 uh = reduce4(x, q);
       c0[idx] = mul_shoup(uh, __ldg(k0 + idx), __ldg(k0s + idx), q);
       c1[idx] = mul_shoup(uh, __ldg(k1 + idx), __ldg(k1s + idx), q);
     };
-    ntt_forward<LOGH>(sm, tw, tws, tmul, q, st_u);
+    ntt_forward<LOGH>(sm, tw, tmul, q, st_u);
     __syncthreads();
-    gen_gauss_half<LOGH>(sm, h, A.seed, rand_tag(A.domain, 1, 0), ct, P.cdt, m, q, mu, w1, w1s);
+    gen_i64_half<LOGH>(sm, h, me, q, mu, w1, w1s);
     auto st_0 = [&](int idx, u64 x) { c0[idx] = reduce8(c0[idx] + x, q); };
-    ntt_forward<LOGH>(sm, tw, tws, tmul, q, st_0);
+    ntt_forward<LOGH>(sm, tw, tmul, q, st_0);
     __syncthreads();
-    gen_gauss_half<LOGH>(sm, h, A.seed, rand_tag(A.domain, 2, 0), ct, P.cdt, nullptr, q, mu, w1, w1s);
+    gen_i8_half<LOGH>(sm, h, sp + N, q, w1, w1s);
     auto st_1 = [&](int idx, u64 x) { c1[idx] = reduce8(c1[idx] + x, q); };
-    ntt_forward<LOGH>(sm, tw, tws, tmul, q, st_1);
+    ntt_forward<LOGH>(sm, tw, tmul, q, st_1);
   } else {
-    gen_gauss_half<LOGH>(sm, h, A.seed, rand_tag(A.domain, 0, 0), ct, P.cdt, m, q, mu, w1, w1s);
+    gen_i64_half<LOGH>(sm, h, me, q, mu, w1, w1s);
     auto st_0 = [&](int idx, u64 x) { c0[idx] = reduce8(__ldg(k0 + idx) + x, q); };
-    ntt_forward<LOGH>(sm, tw, tws, tmul, q, st_0);
+    ntt_forward<LOGH>(sm, tw, tmul, q, st_0);
     __syncthreads();
-    gen_gauss_half<LOGH>(sm, h, A.seed, rand_tag(A.domain, 1, 0), ct, P.cdt, nullptr, q, mu, w1, w1s);
+    gen_i8_half<LOGH>(sm, h, sp, q, w1, w1s);
     auto st_1 = [&](int idx, u64 x) { c1[idx] = reduce8(__ldg(k1 + idx) + x, q); };
-    ntt_forward<LOGH>(sm, tw, tws, tmul, q, st_1);
+    ntt_forward<LOGH>(sm, tw, tmul, q, st_1);
   }
 }
 

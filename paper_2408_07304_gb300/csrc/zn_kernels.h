@@ -4,19 +4,30 @@
 
 namespace zn {
 
-struct EncArgs {
-  const u64* key;       // vanilla: pk [2][L][N]; Zinc: cache [2][L][N]
-  const u64* keys;      // vanilla: pk Shoup companions [2][L][N]; Zinc: unused
-  const i64* m;         // [B][N] encoded messages (nullptr: zero plaintext)
+// Per-ciphertext inputs prepared once for all primes by the prep kernel.
+struct PrepArgs {
+  const double* slots;  // [B][n_slots]
+  uint32_t n_slots;     // 0: zero plaintext
   const u64* ct_index;  // [B] or nullptr (then ct_index0 + b)
   u64 ct_index0;
   u64 seed;
-  unsigned domain;
+  unsigned domain;      // sampling domain (0 vanilla, 1 Zinc, 3 Zinc cache)
+  i64* me;              // [B][N] encoded message plus its noise polynomial
+  int8_t* small;        // [B][2][N] small polynomials (vanilla: u, e1; Zinc: e2')
+  double* work;         // FFT scratch for rings above 2^14: [B][N] doubles
+};
+
+struct EncArgs {
+  const u64* key;       // vanilla: pk [2][L][N]; Zinc: cache [2][L][N]
+  const u64* keys;      // vanilla: pk Shoup companions [2][L][N]; Zinc: unused
+  const i64* me;        // [B][N] from the prep kernel
+  const int8_t* small;  // [B][2][N] from the prep kernel
   u64* out;             // [B][2][L][N]
 };
 
 cudaError_t launch_encode(const DevParams& P, const double* slots, uint32_t n_slots, uint32_t batch, i64* out,
                           double* work, cudaStream_t st);
+cudaError_t launch_prep(const DevParams& P, const PrepArgs& A, bool zinc, uint32_t batch, cudaStream_t st);
 cudaError_t launch_encrypt(const DevParams& P, const EncArgs& A, bool zinc, uint32_t batch, cudaStream_t st);
 cudaError_t launch_keygen(const DevParams& P, u64 seed, u64* sk_ntt, u64* pk, u64* pks, cudaStream_t st);
 cudaError_t launch_ntt_fwd(const DevParams& P, u64* data, uint32_t batch, u64* tmp, cudaStream_t st);

@@ -18,8 +18,7 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T) k_keygen(DevParams P, KeyAr
   extern __shared__ u64 sm[];
   const int i = blockIdx.x, L = P.L;
   const u64 q = P.q[i];
-  const u64* tw = P.tw + (size_t)i * S::N;
-  const u64* tws = P.tws + (size_t)i * S::N;
+  const ulonglong2* tw = P.twp + (size_t)i * S::N;
   u64* sh = A.sk_ntt + (size_t)i * S::N;
   u64* p0 = A.pk + (size_t)i * S::N;
   u64* p1 = p0 + (size_t)L * S::N;
@@ -27,7 +26,7 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T) k_keygen(DevParams P, KeyAr
   u64* p1s = p0s + (size_t)L * S::N;
   gen_ternary<LOGN>(sm, A.seed, rand_tag(2, 0, 0), 0, q);
   auto st_s = [&](int idx, u64 x) { sh[idx] = reduce4(x, q); };
-  ntt_forward<LOGN>(sm, tw, tws, 1, q, st_s);
+  ntt_forward<LOGN>(sm, tw, 1, q, st_s);
   __syncthreads();
   gen_uniform<LOGN>(sm, A.seed, rand_tag(2, 1, (unsigned)i), 0, q);
   auto st_a = [&](int idx, u64 x) {
@@ -35,7 +34,7 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T) k_keygen(DevParams P, KeyAr
     p1[idx] = a;
     p1s[idx] = shoup_of(a, q);
   };
-  ntt_forward<LOGN>(sm, tw, tws, 1, q, st_a);
+  ntt_forward<LOGN>(sm, tw, 1, q, st_a);
   __syncthreads();
   gen_gauss<LOGN>(sm, A.seed, rand_tag(2, 2, 0), 0, P.cdt, nullptr, q, P.mu[i]);
   auto st_e = [&](int idx, u64 x) {
@@ -45,7 +44,7 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T) k_keygen(DevParams P, KeyAr
     p0[idx] = pk0;
     p0s[idx] = shoup_of(pk0, q);
   };
-  ntt_forward<LOGN>(sm, tw, tws, 1, q, st_e);
+  ntt_forward<LOGN>(sm, tw, 1, q, st_e);
 }
 
 template <int LOGH>
@@ -54,9 +53,9 @@ __global__ void __launch_bounds__(NttShape<LOGH>::T) k_keygen_half(DevParams P, 
   extern __shared__ u64 sm[];
   const int i = blockIdx.x >> 1, h = blockIdx.x & 1, L = P.L;
   const u64 q = P.q[i];
-  const u64* tw = P.tw + (size_t)i * N;
-  const u64* tws = P.tws + (size_t)i * N;
-  const u64 w1 = __ldg(tw + 1), w1s = __ldg(tws + 1);
+  const ulonglong2* tw = P.twp + (size_t)i * N;
+  const ulonglong2 w1p = __ldg(tw + 1);
+  const u64 w1 = w1p.x, w1s = w1p.y;
   const size_t off = (size_t)h * HALF;
   u64* sh = A.sk_ntt + (size_t)i * N + off;
   u64* p0 = A.pk + (size_t)i * N + off;
@@ -66,7 +65,7 @@ __global__ void __launch_bounds__(NttShape<LOGH>::T) k_keygen_half(DevParams P, 
   const int tmul = 2 + h;
   gen_ternary_half<LOGH>(sm, h, A.seed, rand_tag(2, 0, 0), 0, q, w1, w1s);
   auto st_s = [&](int idx, u64 x) { sh[idx] = reduce4(x, q); };
-  ntt_forward<LOGH>(sm, tw, tws, tmul, q, st_s);
+  ntt_forward<LOGH>(sm, tw, tmul, q, st_s);
   __syncthreads();
   gen_uniform_half<LOGH>(sm, h, A.seed, rand_tag(2, 1, (unsigned)i), 0, q, w1, w1s);
   auto st_a = [&](int idx, u64 x) {
@@ -74,7 +73,7 @@ __global__ void __launch_bounds__(NttShape<LOGH>::T) k_keygen_half(DevParams P, 
     p1[idx] = a;
     p1s[idx] = shoup_of(a, q);
   };
-  ntt_forward<LOGH>(sm, tw, tws, tmul, q, st_a);
+  ntt_forward<LOGH>(sm, tw, tmul, q, st_a);
   __syncthreads();
   gen_gauss_half<LOGH>(sm, h, A.seed, rand_tag(2, 2, 0), 0, P.cdt, nullptr, q, P.mu[i], w1, w1s);
   auto st_e = [&](int idx, u64 x) {
@@ -84,7 +83,7 @@ __global__ void __launch_bounds__(NttShape<LOGH>::T) k_keygen_half(DevParams P, 
     p0[idx] = pk0;
     p0s[idx] = shoup_of(pk0, q);
   };
-  ntt_forward<LOGH>(sm, tw, tws, tmul, q, st_e);
+  ntt_forward<LOGH>(sm, tw, tmul, q, st_e);
 }
 
 // Out-of-place forward NTT of src [B][L][N] into dst (may alias for N <= 2^14).
@@ -98,7 +97,7 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T) k_ntt_fwd(DevParams P, cons
   gen_copy<LOGN>(sm, src + off);
   u64* o = dst + off;
   auto st = [&](int idx, u64 x) { o[idx] = reduce4(x, q); };
-  ntt_forward<LOGN>(sm, P.tw + (size_t)i * S::N, P.tws + (size_t)i * S::N, 1, q, st);
+  ntt_forward<LOGN>(sm, P.twp + (size_t)i * S::N, 1, q, st);
 }
 
 template <int LOGH>
@@ -107,13 +106,13 @@ __global__ void __launch_bounds__(NttShape<LOGH>::T) k_ntt_fwd_half(DevParams P,
   extern __shared__ u64 sm[];
   const int i = blockIdx.x >> 1, h = blockIdx.x & 1;
   const u64 q = P.q[i];
-  const u64* tw = P.tw + (size_t)i * N;
-  const u64* tws = P.tws + (size_t)i * N;
+  const ulonglong2* tw = P.twp + (size_t)i * N;
+  const ulonglong2 w1p = __ldg(tw + 1);
   const size_t off = ((size_t)blockIdx.y * P.L + i) * N;
-  gen_copy_half<LOGH>(sm, h, src + off, q, __ldg(tw + 1), __ldg(tws + 1));
+  gen_copy_half<LOGH>(sm, h, src + off, q, w1p.x, w1p.y);
   u64* o = dst + off + (size_t)h * HALF;
   auto st = [&](int idx, u64 x) { o[idx] = reduce4(x, q); };
-  ntt_forward<LOGH>(sm, tw, tws, 2 + h, q, st);
+  ntt_forward<LOGH>(sm, tw, 2 + h, q, st);
 }
 
 // Samples of one polynomial kind for `count` ciphertext indices.
