@@ -168,6 +168,7 @@ def run_ours(args, w):
     out_v = torch.empty((B, 2, w.L, w.n), dtype=torch.int64, device=dev)
     out_z = torch.empty_like(out_v)
     stream = torch.cuda.current_stream(dev)
+    tune = api.zn_autotune(ctx, pk, zc, min(B, 512))
 
     def step():
         api.ckks_encrypt(ctx, pk, slots, w.seed, idx, out=out_v, stream=stream)
@@ -282,8 +283,9 @@ def run_ours(args, w):
             "vanilla_enc_s": van_rate, "zinc_enc_s": zin_rate, "zinc_speedup": zin_rate / van_rate,
             "hbm_roofline_frac": value * per_ct_bytes / (hbm_peak * 1e9),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-            "kernel_ms_per_launch": {"encode": enc_ms / max(enc_n, 1), "encrypt_vanilla": kv_avg,
+            "kernel_ms_per_launch": {"prep": enc_ms / max(enc_n, 1), "encrypt_vanilla": kv_avg,
                                      "encrypt_zinc": kz_avg},
+            "autotune": {"variant": tune[0], "ms_per_variant": tune[1]},
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)

@@ -174,6 +174,22 @@ int zn_ntt_inverse(zn_ctx* ctx, uint64_t* data, uint32_t batch, void* stream);
 int zn_sample(zn_ctx* ctx, int kind, uint64_t seed, uint32_t domain, uint32_t poly,
               uint32_t prime, uint64_t ct_index0, uint32_t count, int64_t* out, void* stream);
 
+/* -------------------------------------------------------------- autotuning */
+
+/* Launch shapes of the encryption kernels.  Variant 0: each thread owns 32
+ * NTT elements (2^(log_n-5) threads per block); variant 1: 16 elements, twice
+ * the threads (rings of 2^12 and above; smaller rings always use 0). */
+#define ZN_VARIANTS 2
+int zn_set_variant(zn_ctx* ctx, int variant);
+int zn_get_variant(const zn_ctx* ctx);
+
+/* Time every variant on `batch` vanilla and Zinc encryptions of the zero
+ * message under pk / zc (device scratch allocated and freed inside;
+ * synchronous), keep the fastest in the context, and report per-variant
+ * milliseconds in ms[ZN_VARIANTS] and the choice in *chosen (either may be
+ * NULL).  Results of the encryptions do not depend on the variant. */
+int zn_autotune(zn_ctx* ctx, const zn_pk* pk, const zn_zcache* zc, uint32_t batch, float* ms, int* chosen);
+
 /* ---------------------------------------------------- launch timing (bench) */
 
 /* Kernel kinds that can be timed. */

@@ -67,6 +67,9 @@ _SIGS = {
     "zn_ntt_forward": (_i32, [_vp, _vp, _u32, _vp]),
     "zn_ntt_inverse": (_i32, [_vp, _vp, _u32, _vp]),
     "zn_sample": (_i32, [_vp, _i32, _u64, _u32, _u32, _u32, _u64, _u32, _vp, _vp]),
+    "zn_set_variant": (_i32, [_vp, _i32]),
+    "zn_get_variant": (_i32, [_vp]),
+    "zn_autotune": (_i32, [_vp, _vp, _vp, _u32, _vp, _vp]),
     "zn_timing_enable": (_i32, [_vp, _i32]),
     "zn_timing_read": (_i32, [_vp, _i32, _vp, _vp]),
     "zn_host_primes": (_i32, [_u32, _vp, _u32, _vp]),
@@ -362,6 +365,26 @@ def zn_sample(ctx, kind, seed, domain, poly, prime, ct_index0, count, out=None, 
     _check(lib().zn_sample(ctx.handle, kind, seed, domain, poly, prime, ct_index0, count, out.data_ptr(),
                            _stream(stream)), "zn_sample")
     return out
+
+
+VARIANTS = 2
+
+
+def zn_set_variant(ctx, variant):
+    _check(lib().zn_set_variant(ctx.handle, variant), "zn_set_variant")
+
+
+def zn_get_variant(ctx):
+    return int(lib().zn_get_variant(ctx.handle))
+
+
+def zn_autotune(ctx, pk, zc, batch):
+    """Time each encryption launch shape on `batch` ciphertexts; keep the fastest.
+    Returns (chosen variant, [milliseconds per variant])."""
+    ms = (ctypes.c_float * VARIANTS)()
+    chosen = ctypes.c_int()
+    _check(lib().zn_autotune(ctx.handle, pk.handle, zc.handle, batch, ms, ctypes.byref(chosen)), "zn_autotune")
+    return chosen.value, [float(x) for x in ms]
 
 
 TIME_ENCODE, TIME_ENCRYPT, TIME_ZINC = 0, 1, 2

@@ -31,6 +31,7 @@ struct zn_ctx {
   size_t m_cap;
   double* d_fft;      // FFT scratch for large rings [fft_cap][N]
   size_t fft_cap;
+  int variant;        // encryption launch shape (zn_autotune)
   // launch timing (benchmark instrumentation)
   bool timing;
   std::vector<cudaEvent_t> ev[ZN_TIME_KINDS];   // start/stop pairs
@@ -170,7 +171,7 @@ int encrypt_common(zn_ctx* c, bool zinc, const u64* key, const u64* keys, const 
     A.small = c->d_small;
     A.out = ct + (size_t)b0 * 2 * ring_words(c);
     TimedLaunch t(c, zinc ? ZN_TIME_ZINC : ZN_TIME_ENCRYPT, S(stream));
-    ZN_CUDA(zn::launch_encrypt(c->dp, A, zinc, nb, S(stream)));
+    ZN_CUDA(zn::launch_encrypt(c->dp, A, zinc, nb, c->variant, S(stream)));
   }
   return ZN_OK;
 }
@@ -569,7 +570,7 @@ int zinc_precompute(zn_ctx* c, const zn_pk* pk, uint64_t seed, zn_zcache** out) 
   A.me = c->d_m;
   A.small = c->d_small;
   A.out = z->d;
-  if (zn::launch_prep(c->dp, pa, false, 1, 0) != cudaSuccess || zn::launch_encrypt(c->dp, A, false, 1, 0) != cudaSuccess ||
+  if (zn::launch_prep(c->dp, pa, false, 1, 0) != cudaSuccess || zn::launch_encrypt(c->dp, A, false, 1, c->variant, 0) != cudaSuccess ||
       cudaDeviceSynchronize() != cudaSuccess) {
     cudaGetLastError();
     zn_zcache_destroy(z);
@@ -668,6 +669,64 @@ int ckks_add(zn_ctx* c, const uint64_t* a, const uint64_t* b, uint32_t batch, ui
   DeviceGuard g(c->device);
   ZN_CUDA(zn::launch_add(c->dp, a, b, batch, out, S(stream)));
   return ZN_OK;
+}
+
+// ------------------------------------------------------------- autotuning
+
+int zn_set_variant(zn_ctx* c, int variant) {
+  if (!c || variant < 0 || variant >= ZN_VARIANTS) return ZN_EINVAL;
+  c->variant = variant;
+  return ZN_OK;
+}
+
+int zn_get_variant(const zn_ctx* c) { return c ? c->variant : ZN_EINVAL; }
+
+int zn_autotune(zn_ctx* c, const zn_pk* pk, const zn_zcache* zc, uint32_t batch, float* ms, int* chosen) {
+  if (!c || !pk || !zc || pk->ctx != c || zc->ctx != c || batch == 0) return ZN_EINVAL;
+  DeviceGuard g(c->device);
+  u64* ct = nullptr;
+  u64* idx = nullptr;
+  if (cudaMalloc(&ct, sizeof(u64) * 2 * ring_words(c) * batch) != cudaSuccess ||
+      cudaMalloc(&idx, sizeof(u64) * batch) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(ct);
+    return ZN_ENOMEM;
+  }
+  int rc = cudaMemset(idx, 0, sizeof(u64) * batch) == cudaSuccess ? ZN_OK : ZN_ECUDA;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (!rc && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) rc = ZN_ECUDA;
+  const int saved = c->variant;
+  const bool saved_timing = c->timing;
+  c->timing = false;
+  int best = saved;
+  float best_ms = 0.f;
+  for (int v = 0; v < ZN_VARIANTS && !rc; ++v) {
+    c->variant = v;
+    float t = 0.f;
+    for (int rep = 0; rep < 3 && !rc; ++rep) {   // first repetition warms up
+      if (cudaEventRecord(e0, 0) != cudaSuccess) rc = ZN_ECUDA;
+      if (!rc) rc = encrypt_common(c, false, pk->d, pk->d + 2 * ring_words(c), nullptr, 0, batch, 1, idx, ct, 0);
+      if (!rc) rc = encrypt_common(c, true, zc->d, nullptr, nullptr, 0, batch, 1, idx, ct, 0);
+      if (!rc && (cudaEventRecord(e1, 0) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                  cudaEventElapsedTime(&t, e0, e1) != cudaSuccess))
+        rc = ZN_ECUDA;
+    }
+    if (rc) break;
+    if (ms) ms[v] = t;
+    if (v == 0 || t < best_ms) {
+      best = v;
+      best_ms = t;
+    }
+  }
+  c->variant = rc ? saved : best;
+  c->timing = saved_timing;
+  if (chosen) *chosen = c->variant;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(ct);
+  cudaFree(idx);
+  cudaGetLastError();
+  return rc;
 }
 
 // ------------------------------------------------------------ building blocks

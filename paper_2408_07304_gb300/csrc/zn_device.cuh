@@ -138,12 +138,14 @@ __device__ __forceinline__ u64 uniform_of(uint4 w, u64 q) {
 
 // ------------------------------------------------------------------ NTT
 
-template <int LOGN>
+// LOGPER: log2 of the elements each thread owns (5: 32 elements, 2^(LOGN-5)
+// threads; 4: 16 elements, twice the threads, half the registers each).
+template <int LOGN, int LOGPER = 5>
 struct NttShape {
   static constexpr int N = 1 << LOGN;
-  static constexpr int LOGT = LOGN >= 5 ? LOGN - 5 : 0;
+  static constexpr int LOGT = LOGN >= LOGPER ? LOGN - LOGPER : 0;
   static constexpr int T = 1 << LOGT;                 // threads per transform
-  static constexpr int PER = N / T;                   // elements per thread (32)
+  static constexpr int PER = N / T;                   // elements per thread
   static constexpr int KMAX = 4;                      // butterfly stages per register pass
   // shared-memory swizzle i ^ ((i >> SA) & 15) ^ ((i >> SB) & 15): a bijection that
   // keeps every phase's 64-bit accesses (and the generators' consecutive
@@ -168,10 +170,10 @@ __host__ __device__ constexpr int swz(int i) {
 // pass (LO == 0), hands every output to store(idx, x).  The twiddle of stage
 // bit b for index idx is tw[tmul * 2^(LOGN-1-b) + (idx >> (b+1))]; tmul = 1
 // for a full transform, 2 + h for half h of a transform of twice the size.
-template <int LOGN, int LO, int K, class Store>
+template <int LOGN, int LOGPER, int LO, int K, class Store>
 __device__ __forceinline__ void ntt_pass(u64* sm, int t, const ulonglong2* __restrict__ twp, int tmul, u64 q,
                                          Store& store) {
-  using S = NttShape<LOGN>;
+  using S = NttShape<LOGN, LOGPER>;
   constexpr int G = S::PER >> K;
 #pragma unroll 1
   for (int j = 0; j < G; ++j) {
@@ -201,13 +203,13 @@ __device__ __forceinline__ void ntt_pass(u64* sm, int t, const ulonglong2* __res
   }
 }
 
-template <int LOGN, int HI, class Store>
+template <int LOGN, int LOGPER, int HI, class Store>
 __device__ __forceinline__ void ntt_chain(u64* sm, int t, const ulonglong2* twp, int tmul, u64 q, Store& store) {
   constexpr int K = HI < NttShape<LOGN>::KMAX ? HI : NttShape<LOGN>::KMAX;
   constexpr int LO = HI - K;
   __syncthreads();
-  ntt_pass<LOGN, LO, K, Store>(sm, t, twp, tmul, q, store);
-  if constexpr (LO > 0) ntt_chain<LOGN, LO, Store>(sm, t, twp, tmul, q, store);
+  ntt_pass<LOGN, LOGPER, LO, K, Store>(sm, t, twp, tmul, q, store);
+  if constexpr (LO > 0) ntt_chain<LOGN, LOGPER, LO, Store>(sm, t, twp, tmul, q, store);
 }
 
 // Forward negacyclic NTT of one length-2^LOGN polynomial by the block's
@@ -215,9 +217,9 @@ __device__ __forceinline__ void ntt_chain(u64* sm, int t, const ulonglong2* twp,
 // by one of the generators below; the call begins with a barrier).  store(idx,
 // x) is called once per output index with x in [0, 4q) congruent to ahat[idx].
 // The shared buffer may be reused after a barrier.
-template <int LOGN, class Store>
+template <int LOGN, class Store, int LOGPER = 5>
 __device__ __forceinline__ void ntt_forward(u64* sm, const ulonglong2* twp, int tmul, u64 q, Store& store) {
-  ntt_chain<LOGN, LOGN, Store>(sm, threadIdx.x, twp, tmul, q, store);
+  ntt_chain<LOGN, LOGPER, LOGN, Store>(sm, threadIdx.x, twp, tmul, q, store);
 }
 
 // ------------------------------------------------------------- generators

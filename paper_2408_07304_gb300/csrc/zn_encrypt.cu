@@ -11,9 +11,9 @@
 
 namespace zn {
 
-template <int LOGN, bool ZINC>
-__global__ void __launch_bounds__(NttShape<LOGN>::T) k_encrypt(DevParams P, EncArgs A) {
-  using S = NttShape<LOGN>;
+template <int LOGN, bool ZINC, int LOGPER>
+__global__ void __launch_bounds__(NttShape<LOGN, LOGPER>::T) k_encrypt(DevParams P, EncArgs A) {
+  using S = NttShape<LOGN, LOGPER>;
   extern __shared__ u64 sm[];
   const int i = blockIdx.x, L = P.L;
   const size_t b = blockIdx.y;
@@ -35,33 +35,33 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T) k_encrypt(DevParams P, EncA
       c0[idx] = mul_shoup(uh, __ldg(k0 + idx), __ldg(k0s + idx), q);
       c1[idx] = mul_shoup(uh, __ldg(k1 + idx), __ldg(k1s + idx), q);
     };
-    ntt_forward<LOGN>(sm, tw, 1, q, st_u);
+    ntt_forward<LOGN, decltype(st_u), LOGPER>(sm, tw, 1, q, st_u);
     // m + e0 -> c0
     __syncthreads();
     gen_i64<LOGN>(sm, me, q, mu);
     auto st_0 = [&](int idx, u64 x) { c0[idx] = reduce8(c0[idx] + x, q); };
-    ntt_forward<LOGN>(sm, tw, 1, q, st_0);
+    ntt_forward<LOGN, decltype(st_0), LOGPER>(sm, tw, 1, q, st_0);
     // e1 -> c1
     __syncthreads();
     gen_i8<LOGN>(sm, sp + S::N, q);
     auto st_1 = [&](int idx, u64 x) { c1[idx] = reduce8(c1[idx] + x, q); };
-    ntt_forward<LOGN>(sm, tw, 1, q, st_1);
+    ntt_forward<LOGN, decltype(st_1), LOGPER>(sm, tw, 1, q, st_1);
   } else {
     gen_i64<LOGN>(sm, me, q, mu);
     auto st_0 = [&](int idx, u64 x) { c0[idx] = reduce8(__ldg(k0 + idx) + x, q); };
-    ntt_forward<LOGN>(sm, tw, 1, q, st_0);
+    ntt_forward<LOGN, decltype(st_0), LOGPER>(sm, tw, 1, q, st_0);
     __syncthreads();
     gen_i8<LOGN>(sm, sp, q);
     auto st_1 = [&](int idx, u64 x) { c1[idx] = reduce8(__ldg(k1 + idx) + x, q); };
-    ntt_forward<LOGN>(sm, tw, 1, q, st_1);
+    ntt_forward<LOGN, decltype(st_1), LOGPER>(sm, tw, 1, q, st_1);
   }
 }
 
 // N = 2^(LOGH+1) (one limb exceeds shared memory): grid (2L, B); block
 // x = 2i + h produces output half h of prime i.
-template <int LOGH, bool ZINC>
-__global__ void __launch_bounds__(NttShape<LOGH>::T) k_encrypt_half(DevParams P, EncArgs A) {
-  using S = NttShape<LOGH>;
+template <int LOGH, bool ZINC, int LOGPER>
+__global__ void __launch_bounds__(NttShape<LOGH, LOGPER>::T) k_encrypt_half(DevParams P, EncArgs A) {
+  using S = NttShape<LOGH, LOGPER>;
   constexpr int N = 2 << LOGH, HALF = 1 << LOGH;
   extern __shared__ u64 sm[];
   const int i = blockIdx.x >> 1, h = blockIdx.x & 1, L = P.L;
@@ -87,69 +87,73 @@ __global__ void __launch_bounds__(NttShape<LOGH>::T) k_encrypt_half(DevParams P,
       c0[idx] = mul_shoup(uh, __ldg(k0 + idx), __ldg(k0s + idx), q);
       c1[idx] = mul_shoup(uh, __ldg(k1 + idx), __ldg(k1s + idx), q);
     };
-    ntt_forward<LOGH>(sm, tw, tmul, q, st_u);
+    ntt_forward<LOGH, decltype(st_u), LOGPER>(sm, tw, tmul, q, st_u);
     __syncthreads();
     gen_i64_half<LOGH>(sm, h, me, q, mu, w1, w1s);
     auto st_0 = [&](int idx, u64 x) { c0[idx] = reduce8(c0[idx] + x, q); };
-    ntt_forward<LOGH>(sm, tw, tmul, q, st_0);
+    ntt_forward<LOGH, decltype(st_0), LOGPER>(sm, tw, tmul, q, st_0);
     __syncthreads();
     gen_i8_half<LOGH>(sm, h, sp + N, q, w1, w1s);
     auto st_1 = [&](int idx, u64 x) { c1[idx] = reduce8(c1[idx] + x, q); };
-    ntt_forward<LOGH>(sm, tw, tmul, q, st_1);
+    ntt_forward<LOGH, decltype(st_1), LOGPER>(sm, tw, tmul, q, st_1);
   } else {
     gen_i64_half<LOGH>(sm, h, me, q, mu, w1, w1s);
     auto st_0 = [&](int idx, u64 x) { c0[idx] = reduce8(__ldg(k0 + idx) + x, q); };
-    ntt_forward<LOGH>(sm, tw, tmul, q, st_0);
+    ntt_forward<LOGH, decltype(st_0), LOGPER>(sm, tw, tmul, q, st_0);
     __syncthreads();
     gen_i8_half<LOGH>(sm, h, sp, q, w1, w1s);
     auto st_1 = [&](int idx, u64 x) { c1[idx] = reduce8(__ldg(k1 + idx) + x, q); };
-    ntt_forward<LOGH>(sm, tw, tmul, q, st_1);
+    ntt_forward<LOGH, decltype(st_1), LOGPER>(sm, tw, tmul, q, st_1);
   }
 }
 
-template <int LOGN, bool ZINC>
+template <int LOGN, bool ZINC, int LOGPER>
 static cudaError_t enc_full(const DevParams& P, const EncArgs& A, uint32_t batch, cudaStream_t st) {
-  using S = NttShape<LOGN>;
+  using S = NttShape<LOGN, LOGPER>;
   const size_t smem = sizeof(u64) * S::N;
-  cudaError_t e = cudaFuncSetAttribute(k_encrypt<LOGN, ZINC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = k_encrypt<LOGN, ZINC, LOGPER>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_encrypt<LOGN, ZINC><<<dim3(P.L, batch), S::T, smem, st>>>(P, A);
+  kern<<<dim3(P.L, batch), S::T, smem, st>>>(P, A);
   return cudaGetLastError();
 }
 
-template <int LOGH, bool ZINC>
+template <int LOGH, bool ZINC, int LOGPER>
 static cudaError_t enc_half(const DevParams& P, const EncArgs& A, uint32_t batch, cudaStream_t st) {
-  using S = NttShape<LOGH>;
+  using S = NttShape<LOGH, LOGPER>;
   const size_t smem = sizeof(u64) * S::N;
-  cudaError_t e =
-      cudaFuncSetAttribute(k_encrypt_half<LOGH, ZINC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = k_encrypt_half<LOGH, ZINC, LOGPER>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_encrypt_half<LOGH, ZINC><<<dim3(2 * P.L, batch), S::T, smem, st>>>(P, A);
+  kern<<<dim3(2 * P.L, batch), S::T, smem, st>>>(P, A);
   return cudaGetLastError();
 }
 
+// variant 0: 32 elements per thread; variant 1: 16 elements per thread (rings >= 2^12)
 template <bool ZINC>
-static cudaError_t enc_dispatch(const DevParams& P, const EncArgs& A, uint32_t batch, cudaStream_t st) {
+static cudaError_t enc_dispatch(const DevParams& P, const EncArgs& A, uint32_t batch, int variant, cudaStream_t st) {
+  const bool v1 = variant == 1;
   switch (P.log_n) {
-    case 4: return enc_full<4, ZINC>(P, A, batch, st);
-    case 5: return enc_full<5, ZINC>(P, A, batch, st);
-    case 6: return enc_full<6, ZINC>(P, A, batch, st);
-    case 7: return enc_full<7, ZINC>(P, A, batch, st);
-    case 8: return enc_full<8, ZINC>(P, A, batch, st);
-    case 9: return enc_full<9, ZINC>(P, A, batch, st);
-    case 10: return enc_full<10, ZINC>(P, A, batch, st);
-    case 11: return enc_full<11, ZINC>(P, A, batch, st);
-    case 12: return enc_full<12, ZINC>(P, A, batch, st);
-    case 13: return enc_full<13, ZINC>(P, A, batch, st);
-    case 14: return enc_full<14, ZINC>(P, A, batch, st);
-    case 15: return enc_half<14, ZINC>(P, A, batch, st);
+    case 4: return enc_full<4, ZINC, 5>(P, A, batch, st);
+    case 5: return enc_full<5, ZINC, 5>(P, A, batch, st);
+    case 6: return enc_full<6, ZINC, 5>(P, A, batch, st);
+    case 7: return enc_full<7, ZINC, 5>(P, A, batch, st);
+    case 8: return enc_full<8, ZINC, 5>(P, A, batch, st);
+    case 9: return enc_full<9, ZINC, 5>(P, A, batch, st);
+    case 10: return enc_full<10, ZINC, 5>(P, A, batch, st);
+    case 11: return enc_full<11, ZINC, 5>(P, A, batch, st);
+    case 12: return v1 ? enc_full<12, ZINC, 4>(P, A, batch, st) : enc_full<12, ZINC, 5>(P, A, batch, st);
+    case 13: return v1 ? enc_full<13, ZINC, 4>(P, A, batch, st) : enc_full<13, ZINC, 5>(P, A, batch, st);
+    case 14: return v1 ? enc_full<14, ZINC, 4>(P, A, batch, st) : enc_full<14, ZINC, 5>(P, A, batch, st);
+    case 15: return v1 ? enc_half<14, ZINC, 4>(P, A, batch, st) : enc_half<14, ZINC, 5>(P, A, batch, st);
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t launch_encrypt(const DevParams& P, const EncArgs& A, bool zinc, uint32_t batch, cudaStream_t st) {
+cudaError_t launch_encrypt(const DevParams& P, const EncArgs& A, bool zinc, uint32_t batch, int variant,
+                           cudaStream_t st) {
   if (batch == 0) return cudaSuccess;
-  return zinc ? enc_dispatch<true>(P, A, batch, st) : enc_dispatch<false>(P, A, batch, st);
+  return zinc ? enc_dispatch<true>(P, A, batch, variant, st) : enc_dispatch<false>(P, A, batch, variant, st);
 }
 
 }  // namespace zn

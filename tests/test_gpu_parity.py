@@ -309,3 +309,26 @@ def test_invalid_arguments():
     out = torch.empty((0, 2, 2, 1024), dtype=torch.int64, device="cuda:0")
     api.ckks_encrypt(ctx, pk, dev(np.zeros((0, 4)), torch.float64), 0,
                      torch.empty((0,), dtype=torch.int64, device="cuda:0"), out=out)
+
+
+@pytest.mark.parametrize("log_n,bits,ld", [(12, (36, 36, 36), 30), (13, (60, 40), 40), (14, (60, 50, 60), 50),
+                                           (15, (55, 60), 55)])
+def test_launch_variants_bit_identical(log_n, bits, ld):
+    """Every launch shape the autotuner may choose gives the same ciphertexts."""
+    ctx = gpu_ctx(log_n, bits, ld)
+    _, pk = gpu_keys(log_n, bits, ld, 1)
+    zc = gpu_cache(log_n, bits, ld, 1, 2)
+    w = workloads.small(log_n, bits, ld, 3, (1 << log_n) // 2 - 5, seed=8)
+    z = dev(workloads.slots(w), torch.float64)
+    idx = dev(np.array([4, 0, 2 ** 34]), torch.int64)
+    outs = []
+    for v in range(api.VARIANTS):
+        api.zn_set_variant(ctx, v)
+        assert api.zn_get_variant(ctx) == v
+        outs.append((api.ckks_encrypt(ctx, pk, z, 5, idx), api.zinc_encrypt(ctx, zc, z, 5, idx)))
+    for o in outs[1:]:
+        assert torch.equal(o[0], outs[0][0]) and torch.equal(o[1], outs[0][1])
+    chosen, ms = api.zn_autotune(ctx, pk, zc, 8)
+    assert chosen in range(api.VARIANTS) and all(m > 0 for m in ms)
+    assert api.zn_get_variant(ctx) == chosen
+    api.zn_set_variant(ctx, 0)
