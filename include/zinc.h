@@ -174,6 +174,44 @@ int zn_ntt_inverse(zn_ctx* ctx, uint64_t* data, uint32_t batch, void* stream);
 int zn_sample(zn_ctx* ctx, int kind, uint64_t seed, uint32_t domain, uint32_t poly,
               uint32_t prime, uint64_t ct_index0, uint32_t count, int64_t* out, void* stream);
 
+/* ------------------------------------------------ mixed-ring batched launch */
+
+/* One job of a batch: `count` encryptions under one parameter set and mode.
+ * All pointers are device pointers owned by the caller and must stay valid
+ * (and keep their addresses) for the life of the batch; their contents may
+ * change between runs. */
+typedef struct {
+  zn_ctx* ctx;                /* parameter set (ring degree 2^10 .. 2^15)       */
+  int zinc;                   /* 0: vanilla (Eq. 8) under pk; 1: Zinc (Alg. 1)  */
+  const zn_pk* pk;            /* vanilla key (zinc = 0)                          */
+  const zn_zcache* zc;        /* cached Enc(0) (zinc = 1)                        */
+  const double* slots;        /* [count][n_slots]                                */
+  uint32_t n_slots;           /* <= N/2                                          */
+  uint32_t count;
+  uint64_t seed;
+  const uint64_t* ct_index;   /* [count]                                         */
+  uint64_t* ct;               /* [count][2][L][N]                                */
+} zn_job;
+
+typedef struct zn_batch zn_batch;
+
+/* Plan a batch over jobs of mixed ring degree, chain and mode (all contexts
+ * on `device`): builds the work lists (one prep unit per ciphertext; encrypt
+ * packets of same-ring units that fill a 512-thread block, largest rings
+ * first) and allocates the scratch for every ciphertext.  Synchronous. */
+int zn_batch_create(const zn_job* jobs, uint32_t n_jobs, int device, zn_batch** out);
+void zn_batch_destroy(zn_batch* b);
+
+/* Enqueue the batch on `stream`: two persistent launches (prep, encrypt),
+ * one block per SM, blocks taking work from a device counter.  graph != 0:
+ * the first call captures the launches into a CUDA graph on `stream` and
+ * every call replays it (one graph launch per run).  Results are identical to
+ * ckks_encrypt / zinc_encrypt of each job. */
+int zn_batch_run(zn_batch* b, void* stream, int graph);
+
+/* Number of prep units and encrypt packets in the plan (either may be NULL). */
+int zn_batch_info(const zn_batch* b, uint32_t* prep_units, uint32_t* packets);
+
 /* -------------------------------------------------------------- autotuning */
 
 /* Launch shapes of the encryption kernels.  Variant 0: each thread owns 32
@@ -204,6 +242,12 @@ int zn_timing_enable(zn_ctx* ctx, int on);
 /* Synchronise the recorded events of `kind`, return their summed duration
  * (milliseconds) and launch count, and clear them. */
 int zn_timing_read(zn_ctx* ctx, int kind, double* ms, uint64_t* launches);
+
+/* Diagnostic (no counterpart in the paper): butterflies per second that the
+ * NTT's Harvey/Shoup butterfly reaches on `device` when it runs from
+ * registers alone (no memory traffic) -- the practical ALU ceiling of every
+ * transform in this library.  Synchronous; ~30 ms. */
+int zn_probe_butterfly(int device, double* butterflies_per_s);
 
 /* ------------------------------------------------ host-side tables (no GPU) */
 

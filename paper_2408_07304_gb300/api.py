@@ -67,9 +67,14 @@ _SIGS = {
     "zn_ntt_forward": (_i32, [_vp, _vp, _u32, _vp]),
     "zn_ntt_inverse": (_i32, [_vp, _vp, _u32, _vp]),
     "zn_sample": (_i32, [_vp, _i32, _u64, _u32, _u32, _u32, _u64, _u32, _vp, _vp]),
+    "zn_batch_create": (_i32, [_vp, _u32, _i32, _pp]),
+    "zn_batch_destroy": (None, [_vp]),
+    "zn_batch_run": (_i32, [_vp, _vp, _i32]),
+    "zn_batch_info": (_i32, [_vp, _vp, _vp]),
     "zn_set_variant": (_i32, [_vp, _i32]),
     "zn_get_variant": (_i32, [_vp]),
     "zn_autotune": (_i32, [_vp, _vp, _vp, _u32, _vp, _vp]),
+    "zn_probe_butterfly": (_i32, [_i32, _vp]),
     "zn_timing_enable": (_i32, [_vp, _i32]),
     "zn_timing_read": (_i32, [_vp, _i32, _vp, _vp]),
     "zn_host_primes": (_i32, [_u32, _vp, _u32, _vp]),
@@ -367,6 +372,71 @@ def zn_sample(ctx, kind, seed, domain, poly, prime, ct_index0, count, out=None, 
     return out
 
 
+class _Job(ctypes.Structure):
+    _fields_ = [("ctx", ctypes.c_void_p), ("zinc", ctypes.c_int), ("pk", ctypes.c_void_p), ("zc", ctypes.c_void_p),
+                ("slots", ctypes.c_void_p), ("n_slots", ctypes.c_uint32), ("count", ctypes.c_uint32),
+                ("seed", ctypes.c_uint64), ("ct_index", ctypes.c_void_p), ("ct", ctypes.c_void_p)]
+
+
+class Batch:
+    """A planned mixed-ring batch (zn_batch); keeps its jobs' tensors alive."""
+
+    def __init__(self, h, keep, device):
+        self._h = h
+        self._keep = keep
+        self.device = device
+        pu, pk = ctypes.c_uint32(), ctypes.c_uint32()
+        _check(lib().zn_batch_info(h, ctypes.byref(pu), ctypes.byref(pk)), "zn_batch_info")
+        self.prep_units, self.packets = pu.value, pk.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            lib().zn_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def zn_batch_create(jobs, device=0):
+    """jobs: list of dicts {ctx, zinc (bool), key (PublicKey or ZincCache), slots (CUDA f64 [B, n_slots]),
+    seed, ct_index (CUDA int64 [B]), out (CUDA int64 [B, 2, L, N])}."""
+    import torch
+    arr = (_Job * len(jobs))()
+    keep = []
+    for k, j in enumerate(jobs):
+        ctx, slots, idx, out = j["ctx"], j["slots"], j["ct_index"], j["out"]
+        B = slots.shape[0]
+        _dev(slots, torch.float64, None, "slots")
+        _dev(idx, torch.int64, (B,), "ct_index")
+        _dev(out, torch.int64, (B, 2, ctx.L, ctx.n), "out")
+        arr[k].ctx = ctx.handle.value
+        arr[k].zinc = 1 if j["zinc"] else 0
+        arr[k].pk = None if j["zinc"] else j["key"].handle.value
+        arr[k].zc = j["key"].handle.value if j["zinc"] else None
+        arr[k].slots = slots.data_ptr()
+        arr[k].n_slots = slots.shape[1]
+        arr[k].count = B
+        arr[k].seed = j["seed"]
+        arr[k].ct_index = idx.data_ptr()
+        arr[k].ct = out.data_ptr()
+        keep.append((ctx, j["key"], slots, idx, out))
+    h = ctypes.c_void_p()
+    _check(lib().zn_batch_create(arr, len(jobs), device, ctypes.byref(h)), "zn_batch_create")
+    return Batch(h, keep, device)
+
+
+def zn_batch_run(batch, stream=None, graph=True):
+    _check(lib().zn_batch_run(batch.handle, _stream(stream), 1 if graph else 0), "zn_batch_run")
+
+
 VARIANTS = 2
 
 
@@ -385,6 +455,13 @@ def zn_autotune(ctx, pk, zc, batch):
     chosen = ctypes.c_int()
     _check(lib().zn_autotune(ctx.handle, pk.handle, zc.handle, batch, ms, ctypes.byref(chosen)), "zn_autotune")
     return chosen.value, [float(x) for x in ms]
+
+
+def zn_probe_butterfly(device=0):
+    """Register-only butterflies/s of the NTT butterfly on `device` (ALU ceiling)."""
+    r = ctypes.c_double()
+    _check(lib().zn_probe_butterfly(device, ctypes.byref(r)), "zn_probe_butterfly")
+    return r.value
 
 
 TIME_ENCODE, TIME_ENCRYPT, TIME_ZINC = 0, 1, 2

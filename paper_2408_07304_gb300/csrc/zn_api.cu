@@ -2,6 +2,7 @@
 // argument checking, scratch management and kernel launches.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -671,6 +672,181 @@ int ckks_add(zn_ctx* c, const uint64_t* a, const uint64_t* b, uint32_t batch, ui
   return ZN_OK;
 }
 
+// ------------------------------------------------------------ batches
+
+struct zn_batch {
+  int device;
+  int sms;
+  uint32_t n_prep, n_packets;
+  zn::JobDesc* d_jobs;
+  zn::PrepUnit* d_units;
+  zn::EncPacket* d_packets;
+  int* d_counters;        // [2]: prep, encrypt
+  i64* d_me;
+  int8_t* d_small;
+  double* d_work;         // [sms][2^15] FFT scratch for 2^15 rings
+  cudaGraphExec_t exec;
+};
+
+void zn_batch_destroy(zn_batch* b) {
+  if (!b) return;
+  DeviceGuard g(b->device);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  cudaFree(b->d_jobs);
+  cudaFree(b->d_units);
+  cudaFree(b->d_packets);
+  cudaFree(b->d_counters);
+  cudaFree(b->d_me);
+  cudaFree(b->d_small);
+  cudaFree(b->d_work);
+  delete b;
+}
+
+int zn_batch_create(const zn_job* jobs, uint32_t n_jobs, int device, zn_batch** out) {
+  if (!jobs || !out || n_jobs == 0) return ZN_EINVAL;
+  *out = nullptr;
+  size_t me_words = 0, small_bytes = 0;
+  bool big = false;
+  for (uint32_t j = 0; j < n_jobs; ++j) {
+    const zn_job& J = jobs[j];
+    zn_ctx* c = J.ctx;
+    if (!c || c->device != device || c->prm.log_n < 10 || c->prm.log_n > 15) return ZN_EINVAL;
+    if (J.zinc ? (!J.zc || J.zc->ctx != c) : (!J.pk || J.pk->ctx != c)) return ZN_EINVAL;
+    if (J.n_slots > c->n / 2) return ZN_EINVAL;
+    if (J.count && (!J.ct || !J.ct_index || (J.n_slots && !J.slots))) return ZN_EINVAL;
+    me_words += (size_t)J.count * c->n;
+    small_bytes += 2 * (size_t)J.count * c->n;
+    big |= c->prm.log_n == 15;
+  }
+  DeviceGuard g(device);
+  zn_batch* b = new (std::nothrow) zn_batch();
+  if (!b) return ZN_ENOMEM;
+  b->device = device;
+  if (cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    cudaGetLastError();
+    delete b;
+    return ZN_ECUDA;
+  }
+  // descriptors, scratch offsets and work lists (largest rings first)
+  std::vector<zn::JobDesc> desc(n_jobs);
+  std::vector<uint32_t> order(n_jobs);
+  for (uint32_t j = 0; j < n_jobs; ++j) order[j] = j;
+  std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t c) {
+    return jobs[a].ctx->prm.log_n > jobs[c].ctx->prm.log_n;
+  });
+  int rc = ZN_OK;
+  if ((me_words && cudaMalloc(&b->d_me, sizeof(i64) * me_words) != cudaSuccess) ||
+      (small_bytes && cudaMalloc(&b->d_small, small_bytes) != cudaSuccess) ||
+      (big && cudaMalloc(&b->d_work, sizeof(double) * (size_t)b->sms * (1u << 15)) != cudaSuccess) ||
+      cudaMalloc(&b->d_counters, 2 * sizeof(int)) != cudaSuccess)
+    rc = ZN_ENOMEM;
+  std::vector<zn::PrepUnit> units;
+  std::vector<zn::EncPacket> packets;
+  size_t me_off = 0, sm_off = 0;
+  for (uint32_t j = 0; j < n_jobs && !rc; ++j) {
+    const zn_job& J = jobs[j];
+    zn_ctx* c = J.ctx;
+    zn::JobDesc& D = desc[j];
+    std::memset(&D, 0, sizeof(D));
+    D.P = c->dp;
+    D.zinc = J.zinc ? 1 : 0;
+    D.E.key = J.zinc ? J.zc->d : J.pk->d;
+    D.E.keys = J.zinc ? nullptr : J.pk->d + 2 * ring_words(c);
+    D.E.me = b->d_me + me_off;
+    D.E.small = b->d_small + sm_off;
+    D.E.out = J.ct;
+    D.Pr.slots = J.slots;
+    D.Pr.n_slots = J.n_slots;
+    D.Pr.ct_index = J.ct_index;
+    D.Pr.ct_index0 = 0;
+    D.Pr.seed = J.seed;
+    D.Pr.domain = J.zinc ? 1u : 0u;
+    D.Pr.me = b->d_me + me_off;
+    D.Pr.small = b->d_small + sm_off;
+    D.Pr.work = nullptr;
+    me_off += (size_t)J.count * c->n;
+    sm_off += 2 * (size_t)J.count * c->n;
+  }
+  for (uint32_t oj = 0; oj < n_jobs && !rc; ++oj) {
+    const uint32_t j = order[oj];
+    const zn_job& J = jobs[j];
+    const uint32_t log_n = J.ctx->prm.log_n, L = J.ctx->L;
+    for (uint32_t k = 0; k < J.count; ++k) units.push_back({j, k});
+    if (log_n == 15) {
+      for (uint32_t i = 0; i < L; ++i)
+        for (uint32_t k = 0; k < J.count; ++k)
+          for (uint8_t h = 0; h < 2; ++h) packets.push_back({j, k, (uint16_t)i, 1, h});
+    } else {
+      const uint32_t per = 1u << (14 - log_n);
+      for (uint32_t i = 0; i < L; ++i)
+        for (uint32_t k = 0; k < J.count; k += per)
+          packets.push_back({j, k, (uint16_t)i, (uint8_t)std::min(per, J.count - k), 0});
+    }
+  }
+  b->n_prep = (uint32_t)units.size();
+  b->n_packets = (uint32_t)packets.size();
+  if (!rc && (cudaMalloc(&b->d_jobs, sizeof(zn::JobDesc) * n_jobs) != cudaSuccess ||
+              (b->n_prep && cudaMalloc(&b->d_units, sizeof(zn::PrepUnit) * b->n_prep) != cudaSuccess) ||
+              (b->n_packets && cudaMalloc(&b->d_packets, sizeof(zn::EncPacket) * b->n_packets) != cudaSuccess)))
+    rc = ZN_ENOMEM;
+  if (!rc && (cudaMemcpy(b->d_jobs, desc.data(), sizeof(zn::JobDesc) * n_jobs, cudaMemcpyHostToDevice) != cudaSuccess ||
+              (b->n_prep && cudaMemcpy(b->d_units, units.data(), sizeof(zn::PrepUnit) * b->n_prep,
+                                       cudaMemcpyHostToDevice) != cudaSuccess) ||
+              (b->n_packets && cudaMemcpy(b->d_packets, packets.data(), sizeof(zn::EncPacket) * b->n_packets,
+                                          cudaMemcpyHostToDevice) != cudaSuccess) ||
+              zn::batch_set_attributes() != cudaSuccess))
+    rc = ZN_ECUDA;
+  if (rc) {
+    cudaGetLastError();
+    zn_batch_destroy(b);
+    return rc;
+  }
+  *out = b;
+  return ZN_OK;
+}
+
+static int batch_enqueue(zn_batch* b, cudaStream_t st) {
+  ZN_CUDA(cudaMemsetAsync(b->d_counters, 0, 2 * sizeof(int), st));
+  if (b->n_prep)
+    ZN_CUDA(zn::launch_batch_prep(b->d_jobs, b->d_units, (int)b->n_prep, b->d_counters, b->d_work, b->sms, st));
+  if (b->n_packets)
+    ZN_CUDA(zn::launch_batch_encrypt(b->d_jobs, b->d_packets, (int)b->n_packets, b->d_counters + 1, b->sms, st));
+  return ZN_OK;
+}
+
+int zn_batch_run(zn_batch* b, void* stream, int graph) {
+  if (!b) return ZN_EINVAL;
+  DeviceGuard g(b->device);
+  cudaStream_t st = S(stream);
+  if (!graph) return batch_enqueue(b, st);
+  if (!b->exec) {
+    if (st == 0) return ZN_EINVAL;   // capture needs a non-default stream
+    cudaGraph_t gr = nullptr;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      return ZN_ECUDA;
+    }
+    const int rc = batch_enqueue(b, st);
+    const cudaError_t e = cudaStreamEndCapture(st, &gr);
+    if (rc || e != cudaSuccess || cudaGraphInstantiate(&b->exec, gr, 0) != cudaSuccess) {
+      if (gr) cudaGraphDestroy(gr);
+      b->exec = nullptr;
+      cudaGetLastError();
+      return rc ? rc : ZN_ECUDA;
+    }
+    cudaGraphDestroy(gr);
+  }
+  ZN_CUDA(cudaGraphLaunch(b->exec, st));
+  return ZN_OK;
+}
+
+int zn_batch_info(const zn_batch* b, uint32_t* prep_units, uint32_t* packets) {
+  if (!b) return ZN_EINVAL;
+  if (prep_units) *prep_units = b->n_prep;
+  if (packets) *packets = b->n_packets;
+  return ZN_OK;
+}
+
 // ------------------------------------------------------------- autotuning
 
 int zn_set_variant(zn_ctx* c, int variant) {
@@ -727,6 +903,17 @@ int zn_autotune(zn_ctx* c, const zn_pk* pk, const zn_zcache* zc, uint32_t batch,
   cudaFree(idx);
   cudaGetLastError();
   return rc;
+}
+
+int zn_probe_butterfly(int device, double* per_s) {
+  if (!per_s) return ZN_EINVAL;
+  DeviceGuard g(device);
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    cudaGetLastError();
+    return ZN_ECUDA;
+  }
+  return zn::probe_butterfly(sms, per_s) == cudaSuccess ? ZN_OK : ZN_ECUDA;
 }
 
 // ------------------------------------------------------------ building blocks

@@ -128,6 +128,31 @@ __global__ void k_prep_gmem(DevParams P, PrepArgs A) {
   prep_one<ZINC>(P, A, blockIdx.x, re, re + n);
 }
 
+// Persistent prep over a mixed work list: one 512-thread block per SM takes
+// the next ciphertext from a global counter (zero at launch).  Rings up to
+// 2^14 transform in shared memory, 2^15 in this block's slice of `work`
+// (2^15 doubles per block).
+__global__ void __launch_bounds__(512, 1) k_batch_prep(const JobDesc* __restrict__ jobs,
+                                                       const PrepUnit* __restrict__ units, int n_units, int* counter,
+                                                       double* work) {
+  extern __shared__ double smd[];
+  __shared__ int s_next;
+  for (;;) {
+    if (threadIdx.x == 0) s_next = atomicAdd(counter, 1);
+    __syncthreads();
+    const int p = s_next;
+    __syncthreads();
+    if (p >= n_units) break;
+    const PrepUnit u = units[p];
+    const JobDesc& J = jobs[u.job];
+    const int n = 1 << (J.P.log_n - 1);
+    double* re = J.P.log_n <= 14 ? smd : work + (size_t)blockIdx.x * (2 * (size_t)n);
+    if (J.zinc) prep_one<true>(J.P, J.Pr, u.b, re, re + n);
+    else prep_one<false>(J.P, J.Pr, u.b, re, re + n);
+    __syncthreads();
+  }
+}
+
 // ------------------------------------------------------------ inverse NTT
 // Gentleman-Sande, bit-reversed input -> natural order, times N^-1; one
 // block per polynomial, in shared memory or in place in global memory.
@@ -308,6 +333,19 @@ static cudaError_t prep_launch(const DevParams& P, const PrepArgs& A, uint32_t b
 cudaError_t launch_prep(const DevParams& P, const PrepArgs& A, bool zinc, uint32_t batch, cudaStream_t st) {
   if (batch == 0) return cudaSuccess;
   return zinc ? prep_launch<true>(P, A, batch, st) : prep_launch<false>(P, A, batch, st);
+}
+
+cudaError_t launch_batch_prep(const JobDesc* jobs, const PrepUnit* units, int n_units, int* counter, double* work,
+                              int grid, cudaStream_t st) {
+  k_batch_prep<<<grid, 512, sizeof(double) << 14, st>>>(jobs, units, n_units, counter, work);
+  return cudaGetLastError();
+}
+
+cudaError_t batch_set_attributes() {
+  cudaError_t e = cudaFuncSetAttribute(k_batch_prep, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(sizeof(double) << 14));
+  if (e != cudaSuccess) return e;
+  return batch_encrypt_attributes();
 }
 
 cudaError_t launch_ntt_inv(const DevParams& P, u64* data, uint32_t batch, cudaStream_t st) {

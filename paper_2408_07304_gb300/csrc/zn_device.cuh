@@ -222,6 +222,16 @@ __device__ __forceinline__ void ntt_forward(u64* sm, const ulonglong2* twp, int 
   ntt_chain<LOGN, LOGPER, LOGN, Store>(sm, threadIdx.x, twp, tmul, q, store);
 }
 
+// The same transform run by a sub-group of the block: thread t of the 2^LOGT
+// threads that own this polynomial (several sub-groups may share one block;
+// all of them must execute the same sequence of transforms, because the
+// passes are separated by block-wide barriers).
+template <int LOGN, class Store, int LOGPER = 5>
+__device__ __forceinline__ void ntt_forward_sub(u64* sm, int t, const ulonglong2* twp, int tmul, u64 q,
+                                                Store& store) {
+  ntt_chain<LOGN, LOGPER, LOGN, Store>(sm, t, twp, tmul, q, store);
+}
+
 // ------------------------------------------------------------- generators
 // Each generator writes one polynomial into the swizzled shared buffer with
 // plain block-strided loops (one Philox call per loop trip).  Callers must
@@ -272,16 +282,17 @@ __device__ __forceinline__ void gen_copy(u64* sm, const u64* __restrict__ a) {
   for (int k = threadIdx.x; k < (1 << LOGN); k += blockDim.x) sm[swz<LOGN>(k)] = a[k];
 }
 
-// Encoded message plus noise (int64) from the per-ciphertext scratch.
+// Encoded message plus noise (int64) from the per-ciphertext scratch; thread t
+// of nt.
 template <int LOGN>
-__device__ __forceinline__ void gen_i64(u64* sm, const i64* __restrict__ a, u64 q, u64 mu) {
-  for (int k = threadIdx.x; k < (1 << LOGN); k += blockDim.x) sm[swz<LOGN>(k)] = reduce_signed(__ldg(a + k), q, mu);
+__device__ __forceinline__ void gen_i64(u64* sm, int t, int nt, const i64* __restrict__ a, u64 q, u64 mu) {
+  for (int k = t; k < (1 << LOGN); k += nt) sm[swz<LOGN>(k)] = reduce_signed(__ldg(a + k), q, mu);
 }
 
 // Small signed polynomial (int8) from the per-ciphertext scratch.
 template <int LOGN>
-__device__ __forceinline__ void gen_i8(u64* sm, const int8_t* __restrict__ a, u64 q) {
-  for (int k = threadIdx.x; k < (1 << LOGN); k += blockDim.x) sm[swz<LOGN>(k)] = small_res(__ldg(a + k), q);
+__device__ __forceinline__ void gen_i8(u64* sm, int t, int nt, const int8_t* __restrict__ a, u64 q) {
+  for (int k = t; k < (1 << LOGN); k += nt) sm[swz<LOGN>(k)] = small_res(__ldg(a + k), q);
 }
 
 // ---------------------------------------------- generators, half transforms
@@ -341,18 +352,19 @@ __device__ __forceinline__ void gen_uniform_half(u64* sm, int h, u64 seed, unsig
 }
 
 template <int LOGH>
-__device__ __forceinline__ void gen_i64_half(u64* sm, int h, const i64* __restrict__ a, u64 q, u64 mu, u64 w1,
-                                             u64 w1s) {
+__device__ __forceinline__ void gen_i64_half(u64* sm, int t, int nt, int h, const i64* __restrict__ a, u64 q, u64 mu,
+                                             u64 w1, u64 w1s) {
   constexpr int HALF = 1 << LOGH;
-  for (int k = threadIdx.x; k < HALF; k += blockDim.x)
+  for (int k = t; k < HALF; k += nt)
     sm[swz<LOGH>(k)] = first_stage(reduce_signed(__ldg(a + k), q, mu), reduce_signed(__ldg(a + k + HALF), q, mu), h,
                                    w1, w1s, q);
 }
 
 template <int LOGH>
-__device__ __forceinline__ void gen_i8_half(u64* sm, int h, const int8_t* __restrict__ a, u64 q, u64 w1, u64 w1s) {
+__device__ __forceinline__ void gen_i8_half(u64* sm, int t, int nt, int h, const int8_t* __restrict__ a, u64 q, u64 w1,
+                                            u64 w1s) {
   constexpr int HALF = 1 << LOGH;
-  for (int k = threadIdx.x; k < HALF; k += blockDim.x)
+  for (int k = t; k < HALF; k += nt)
     sm[swz<LOGH>(k)] = first_stage(small_res(__ldg(a + k), q), small_res(__ldg(a + k + HALF), q), h, w1, w1s, q);
 }
 

@@ -28,6 +28,34 @@ struct EncArgs {
 cudaError_t launch_encode(const DevParams& P, const double* slots, uint32_t n_slots, uint32_t batch, i64* out,
                           double* work, cudaStream_t st);
 cudaError_t launch_prep(const DevParams& P, const PrepArgs& A, bool zinc, uint32_t batch, cudaStream_t st);
+// Mixed-ring batches (persistent kernels): one descriptor per job (a ring,
+// a mode, a key or cache, buffers), a work list of encrypt packets and one of
+// prep units.
+struct JobDesc {
+  DevParams P;
+  EncArgs E;      // me / small point into this job's scratch
+  PrepArgs Pr;    // idem; Pr.work unused (large rings use the per-block area)
+  int zinc;
+  int pad;
+};
+struct EncPacket {
+  uint32_t job;
+  uint32_t b0;      // first ciphertext of the packet (within the job)
+  uint16_t prime;
+  uint8_t count;    // ciphertexts in the packet (units sharing one block)
+  uint8_t half;     // N = 2^15: which output half
+};
+struct PrepUnit {
+  uint32_t job;
+  uint32_t b;
+};
+cudaError_t batch_set_attributes();
+cudaError_t batch_encrypt_attributes();
+cudaError_t launch_batch_prep(const JobDesc* jobs, const PrepUnit* units, int n_units, int* counter, double* work,
+                              int grid, cudaStream_t st);
+cudaError_t launch_batch_encrypt(const JobDesc* jobs, const EncPacket* packets, int n_packets, int* counter, int grid,
+                                 cudaStream_t st);
+
 // variant: 0 = 32 NTT elements per thread, 1 = 16 (selected by the autotuner)
 cudaError_t launch_encrypt(const DevParams& P, const EncArgs& A, bool zinc, uint32_t batch, int variant,
                            cudaStream_t st);
@@ -42,6 +70,8 @@ cudaError_t launch_add(const DevParams& P, const u64* a, const u64* b, uint32_t 
 cudaError_t launch_sample(const DevParams& P, int kind, u64 seed, unsigned domain, unsigned poly, unsigned prime,
                           u64 ct_index0, uint32_t count, i64* out, cudaStream_t st);
 cudaError_t launch_shoup(const DevParams& P, const u64* w, u64* ws, uint32_t polys, cudaStream_t st);
+// Butterflies per second of k_probe_butterfly (register-only ceiling).
+cudaError_t probe_butterfly(int sms, double* per_s);
 cudaError_t launch_sk_residues(const DevParams& P, const int8_t* s, u64* out, cudaStream_t st);
 
 }  // namespace zn

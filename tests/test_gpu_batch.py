@@ -1,0 +1,103 @@
+"""Mixed-ring batches (persistent launches, CUDA-graph replay): every job's
+ciphertexts equal, bit for bit, those of the single-ring entry points, which
+test_gpu_parity checks against the oracle.  Ragged job sizes exercise
+partially filled packets (idle sub-groups) and both halves of 2^15 rings."""
+import functools
+
+import numpy as np
+import pytest
+
+from paper_2408_07304_gb300 import api, workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@functools.lru_cache(maxsize=None)
+def ring(log_n, bits, ld):
+    from paper_2408_07304_gb300 import build
+    build.build()
+    ctx = api.Context(log_n, bits, ld, device=0)
+    sk, pk = api.ckks_keygen(ctx, 1)
+    zc = api.zinc_precompute(ctx, pk, 2)
+    return ctx, sk, pk, zc
+
+
+JOBS = [  # (log_n, bits, log2_delta, zinc, count, n_slots)
+    (12, (36, 36, 36), 30, False, 5, 2048),
+    (12, (36, 36, 36), 30, True, 3, 100),
+    (13, (60, 40, 40, 60), 40, True, 7, 4096),
+    (14, (60, 50, 50, 60), 50, False, 2, 8192),
+    (15, (55, 55, 60), 55, False, 1, 16384),
+    (15, (55, 55, 60), 55, True, 2, 3000),
+    (10, (40, 41), 30, True, 17, 512),
+    (11, (45, 45), 35, False, 9, 0),
+]
+
+
+def _make(seed_shift=0):
+    jobs, refs = [], []
+    for k, (log_n, bits, ld, zinc, count, ns) in enumerate(JOBS):
+        ctx, sk, pk, zc = ring(log_n, bits, ld)
+        w = workloads.small(log_n, bits, ld, count, ns, seed=100 + k + seed_shift)
+        z = torch.tensor(workloads.slots(w), dtype=torch.float64, device="cuda:0")
+        idx = torch.tensor(np.arange(count) * 3 + k * 1000, dtype=torch.int64, device="cuda:0")
+        out = torch.full((count, 2, ctx.L, ctx.n), -1, dtype=torch.int64, device="cuda:0")
+        jobs.append({"ctx": ctx, "zinc": zinc, "key": zc if zinc else pk, "slots": z, "seed": 7 + k,
+                     "ct_index": idx, "out": out})
+    return jobs
+
+
+def _reference(j):
+    fn = api.zinc_encrypt if j["zinc"] else api.ckks_encrypt
+    return fn(j["ctx"], j["key"], j["slots"], j["seed"], j["ct_index"])
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_batch_matches_single_ring(graph):
+    jobs = _make()
+    b = api.zn_batch_create(jobs)
+    expect_packets = 0
+    for log_n, bits, _, _, count, _ in JOBS:
+        per = 1 << (14 - log_n) if log_n <= 14 else 1
+        expect_packets += len(bits) * (-(-count // per) if log_n <= 14 else 2 * count)
+    assert b.prep_units == sum(j[4] for j in JOBS) and b.packets == expect_packets
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        api.zn_batch_run(b, s, graph=graph)
+        api.zn_batch_run(b, s, graph=graph)          # a replay gives the same result
+    s.synchronize()
+    for j in jobs:
+        api.zn_sync_status(j["ctx"])
+        assert torch.equal(j["out"], _reference(j)), (j["ctx"].log_n, j["zinc"])
+
+
+def test_batch_graph_sees_new_inputs():
+    jobs = _make()
+    b = api.zn_batch_create(jobs)
+    s = torch.cuda.Stream()
+    api.zn_batch_run(b, s, graph=True)
+    s.synchronize()
+    fresh = _make(seed_shift=50)
+    for j, f in zip(jobs, fresh):          # same buffers, new contents
+        j["slots"].copy_(f["slots"])
+        j["ct_index"].add_(1)
+    api.zn_batch_run(b, s, graph=True)
+    s.synchronize()
+    for j in jobs:
+        assert torch.equal(j["out"], _reference(j))
+
+
+def test_batch_rejects_bad_jobs():
+    ctx, _, pk, zc = ring(12, (36, 36, 36), 30)
+    z = torch.zeros((1, 8), dtype=torch.float64, device="cuda:0")
+    idx = torch.zeros((1,), dtype=torch.int64, device="cuda:0")
+    out = torch.empty((1, 2, ctx.L, ctx.n), dtype=torch.int64, device="cuda:0")
+    with pytest.raises(api.ZincError):       # a vanilla job carrying a cache instead of a key
+        api.zn_batch_create([{"ctx": ctx, "zinc": False, "key": zc, "slots": z, "seed": 0,
+                              "ct_index": idx, "out": out}])
+    tiny = api.Context(9, (40,), 20)          # below the batch kernel's smallest ring
+    tpk = api.ckks_keygen(tiny, 1)[1]
+    with pytest.raises(api.ZincError):
+        api.zn_batch_create([{"ctx": tiny, "zinc": False, "key": tpk, "slots": z, "seed": 0, "ct_index": idx,
+                              "out": torch.empty((1, 2, 1, 512), dtype=torch.int64, device="cuda:0")}])
