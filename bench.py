@@ -278,6 +278,14 @@ def run_ours(args, w):
                "steps": e2e_steps}
         del host_v, host_z
 
+    # ---- serving: Poisson stream of mixed-ring requests, continuous batching
+    serving = None
+    if rank == 0 and world == 1 and not args.no_serve:
+        from paper_2408_07304_gb300 import serve
+        del out_v, out_z
+        torch.cuda.empty_cache()
+        serving = serve.serve_benchmark(args.serve_requests, 0.7, device=local)
+
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, one GPU only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -296,6 +304,7 @@ def run_ours(args, w):
             "vanilla_enc_s": van_rate, "zinc_enc_s": zin_rate, "zinc_speedup": zin_rate / van_rate,
             "hbm_roofline_frac": value * per_ct_bytes / (hbm_peak * 1e9),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "serving": serving,
             "kernel_ms_per_launch": {"prep": enc_ms / max(enc_n, 1), "encrypt_vanilla": kv_avg,
                                      "encrypt_zinc": kz_avg},
             "autotune": {"variant": tune[0], "ms_per_variant": tune[1]},
@@ -316,6 +325,8 @@ def main():
     ap.add_argument("--batch", type=int, default=None, help="override the workload's batch (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving (p50/p99) run")
+    ap.add_argument("--serve-requests", type=int, default=20000)
     args = ap.parse_args()
     w = workloads.WORKLOADS[args.workload]
     if args.batch:

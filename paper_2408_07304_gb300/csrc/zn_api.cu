@@ -27,30 +27,36 @@ struct zn_ctx {
   double* d_etw;      // [2][N]
   int* d_slot;        // [N/2]
   unsigned* d_status;
-  i64* d_m;           // prep scratch: message + noise [m_cap][N]
-  int8_t* d_small;    // prep scratch: small polynomials [m_cap][2][N]
-  size_t m_cap;
-  double* d_fft;      // FFT scratch for large rings [fft_cap][N]
-  size_t fft_cap;
+  cudaMemPool_t pool; // stream-ordered scratch (prep outputs, FFT work areas)
   int variant;        // encryption launch shape (zn_autotune)
   // launch timing (benchmark instrumentation)
   bool timing;
   std::vector<cudaEvent_t> ev[ZN_TIME_KINDS];   // start/stop pairs
 };
 
+// Handle type tags: an opaque pointer of the wrong kind is rejected (ZN_EINVAL).
+enum : uint32_t { kTagPk = 0x6b70u, kTagSk = 0x6b73u, kTagZc = 0x637au, kTagDead = 0u };
+
 struct zn_pk {
+  uint32_t tag = kTagPk;
   zn_ctx* ctx;
   u64* d;    // [2][L][N] then Shoup companions [2][L][N]
 };
 struct zn_sk {
+  uint32_t tag = kTagSk;
   zn_ctx* ctx;
   u64* d;                    // [L][N] NTT form
   std::vector<int8_t> s;     // coefficients
 };
 struct zn_zcache {
+  uint32_t tag = kTagZc;
   zn_ctx* ctx;
   u64* d;    // [2][L][N]
 };
+
+static inline bool pk_of(const zn_pk* k, const zn_ctx* c) { return k && k->tag == kTagPk && k->ctx == c; }
+static inline bool sk_of(const zn_sk* k, const zn_ctx* c) { return k && k->tag == kTagSk && k->ctx == c; }
+static inline bool zc_of(const zn_zcache* z, const zn_ctx* c) { return z && z->tag == kTagZc && z->ctx == c; }
 
 namespace {
 
@@ -78,36 +84,26 @@ struct DeviceGuard {
     }                                      \
   } while (0)
 
-int ensure_m(zn_ctx* c, size_t cts) {
-  if (cts <= c->m_cap) return ZN_OK;
-  cudaFree(c->d_m);
-  cudaFree(c->d_small);
-  c->d_m = nullptr;
-  c->d_small = nullptr;
-  c->m_cap = 0;
-  if (cudaMalloc(&c->d_m, sizeof(i64) * cts * c->n) != cudaSuccess ||
-      cudaMalloc(&c->d_small, 2 * cts * (size_t)c->n) != cudaSuccess) {
-    cudaGetLastError();
-    cudaFree(c->d_m);
-    c->d_m = nullptr;
-    return ZN_ENOMEM;
+// Stream-ordered scratch from the context's memory pool: concurrent calls on
+// different streams never share scratch, and the allocations are legal
+// inside a CUDA-graph capture.
+struct Scratch {
+  zn_ctx* c;
+  cudaStream_t st;
+  void* p = nullptr;
+  Scratch(zn_ctx* c_, cudaStream_t st_) : c(c_), st(st_) {}
+  bool alloc(size_t bytes) {
+    if (cudaMallocFromPoolAsync(&p, bytes, c->pool, st) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+      return false;
+    }
+    return true;
   }
-  c->m_cap = cts;
-  return ZN_OK;
-}
-
-int ensure_fft(zn_ctx* c, size_t cts) {
-  if (cts <= c->fft_cap) return ZN_OK;
-  if (c->d_fft) cudaFree(c->d_fft);
-  c->d_fft = nullptr;
-  c->fft_cap = 0;
-  if (cudaMalloc(&c->d_fft, sizeof(double) * cts * c->n) != cudaSuccess) {
-    cudaGetLastError();
-    return ZN_ENOMEM;
+  ~Scratch() {
+    if (p) cudaFreeAsync(p, st);
   }
-  c->fft_cap = cts;
-  return ZN_OK;
-}
+};
 
 // Event pair around one launch (no-op unless timing is on).
 struct TimedLaunch {
@@ -146,9 +142,16 @@ int encrypt_common(zn_ctx* c, bool zinc, const u64* key, const u64* keys, const 
   DeviceGuard g(c->device);
   const uint32_t chunk = encode_chunk(c);
   const uint32_t first = batch < chunk ? batch : chunk;
-  int rc = ensure_m(c, first);
-  if (rc) return rc;
-  if (c->prm.log_n > 14 && (rc = ensure_fft(c, first))) return rc;
+  // per chunk: message + noise (int64 [N]), small polynomials (int8 [2][N]),
+  // and for 2^15 rings an FFT work area (double [N])
+  const size_t me_b = sizeof(i64) * first * c->n, sm_b = 2 * (size_t)first * c->n;
+  const size_t fft_b = c->prm.log_n > 14 ? sizeof(double) * first * c->n : 0;
+  const size_t sm_pad = (sm_b + 255) / 256 * 256;
+  Scratch scratch(c, S(stream));
+  if (!scratch.alloc(me_b + sm_pad + fft_b)) return ZN_ENOMEM;
+  i64* me = (i64*)scratch.p;
+  int8_t* small = (int8_t*)scratch.p + me_b;
+  double* fft = fft_b ? (double*)((char*)scratch.p + me_b + sm_pad) : nullptr;
   for (uint32_t b0 = 0; b0 < batch; b0 += chunk) {
     const uint32_t nb = (batch - b0) < chunk ? (batch - b0) : chunk;
     zn::PrepArgs pa;
@@ -158,9 +161,9 @@ int encrypt_common(zn_ctx* c, bool zinc, const u64* key, const u64* keys, const 
     pa.ct_index0 = 0;
     pa.seed = seed;
     pa.domain = zinc ? 1u : 0u;
-    pa.me = c->d_m;
-    pa.small = c->d_small;
-    pa.work = c->d_fft;
+    pa.me = me;
+    pa.small = small;
+    pa.work = fft;
     {
       TimedLaunch t(c, ZN_TIME_ENCODE, S(stream));
       ZN_CUDA(zn::launch_prep(c->dp, pa, zinc, nb, S(stream)));
@@ -168,8 +171,8 @@ int encrypt_common(zn_ctx* c, bool zinc, const u64* key, const u64* keys, const 
     zn::EncArgs A;
     A.key = key;
     A.keys = keys;
-    A.me = c->d_m;
-    A.small = c->d_small;
+    A.me = me;
+    A.small = small;
     A.out = ct + (size_t)b0 * 2 * ring_words(c);
     TimedLaunch t(c, zinc ? ZN_TIME_ZINC : ZN_TIME_ENCRYPT, S(stream));
     ZN_CUDA(zn::launch_encrypt(c->dp, A, zinc, nb, c->variant, S(stream)));
@@ -294,6 +297,21 @@ int zn_ctx_create(const zn_params* p, int device, zn_ctx** out) {
     zn_ctx_destroy(c);
     return rc;
   }
+  {
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    if (cudaMemPoolCreate(&c->pool, &props) != cudaSuccess) {
+      cudaGetLastError();
+      c->pool = nullptr;
+      zn_ctx_destroy(c);
+      return ZN_ECUDA;
+    }
+    uint64_t keep = ~0ull;   // keep freed scratch in the pool between calls
+    cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
   dp.twp = reinterpret_cast<const ulonglong2*>(c->d_tw);
   dp.itw = c->d_tw + 2 * (size_t)L * n;
   dp.itws = c->d_tw + 3 * (size_t)L * n;
@@ -312,9 +330,10 @@ void zn_ctx_destroy(zn_ctx* c) {
   cudaFree(c->d_etw);
   cudaFree(c->d_slot);
   cudaFree(c->d_status);
-  cudaFree(c->d_m);
-  cudaFree(c->d_small);
-  cudaFree(c->d_fft);
+  if (c->pool) {
+    cudaDeviceSynchronize();   // pending stream-ordered frees
+    cudaMemPoolDestroy(c->pool);
+  }
   delete c;
 }
 
@@ -424,21 +443,23 @@ int ckks_keygen(zn_ctx* c, uint64_t seed, zn_sk** sk, zn_pk** pk) {
 }
 
 void zn_sk_destroy(zn_sk* s) {
-  if (!s) return;
+  if (!s || s->tag != kTagSk) return;
+  s->tag = kTagDead;
   DeviceGuard g(s->ctx->device);
   cudaFree(s->d);
   delete s;
 }
 
 void zn_pk_destroy(zn_pk* k) {
-  if (!k) return;
+  if (!k || k->tag != kTagPk) return;
+  k->tag = kTagDead;
   DeviceGuard g(k->ctx->device);
   cudaFree(k->d);
   delete k;
 }
 
 int zn_pk_export(const zn_pk* k, uint64_t* host_out) {
-  if (!k || !host_out) return ZN_EINVAL;
+  if (!k || k->tag != kTagPk || !host_out) return ZN_EINVAL;
   DeviceGuard g(k->ctx->device);
   ZN_CUDA(cudaMemcpy(host_out, k->d, sizeof(u64) * 2 * ring_words(k->ctx), cudaMemcpyDeviceToHost));
   return ZN_OK;
@@ -472,7 +493,7 @@ int zn_pk_import(zn_ctx* c, const uint64_t* host_in, zn_pk** out) {
 }
 
 int zn_sk_export(const zn_sk* s, int8_t* host_out) {
-  if (!s || !host_out) return ZN_EINVAL;
+  if (!s || s->tag != kTagSk || !host_out) return ZN_EINVAL;
   std::memcpy(host_out, s->s.data(), s->s.size());
   return ZN_OK;
 }
@@ -521,9 +542,9 @@ int ckks_encode(zn_ctx* c, const double* slots, uint32_t n_slots, uint32_t batch
   if (batch == 0) return ZN_OK;
   if (!out || (n_slots && !slots)) return ZN_EINVAL;
   DeviceGuard g(c->device);
-  int rc;
-  if (c->prm.log_n > 14 && (rc = ensure_fft(c, batch))) return rc;
-  ZN_CUDA(zn::launch_encode(c->dp, slots, n_slots, batch, (i64*)out, c->d_fft, S(stream)));
+  Scratch fft(c, S(stream));
+  if (c->prm.log_n > 14 && !fft.alloc(sizeof(double) * batch * (size_t)c->n)) return ZN_ENOMEM;
+  ZN_CUDA(zn::launch_encode(c->dp, slots, n_slots, batch, (i64*)out, (double*)fft.p, S(stream)));
   return ZN_OK;
 }
 
@@ -531,13 +552,13 @@ int ckks_encode(zn_ctx* c, const double* slots, uint32_t n_slots, uint32_t batch
 
 int ckks_encrypt(zn_ctx* c, const zn_pk* pk, const double* slots, uint32_t n_slots, uint32_t batch, uint64_t seed,
                  const uint64_t* ct_index, uint64_t* ct, void* stream) {
-  if (!c || !pk || pk->ctx != c) return ZN_EINVAL;
+  if (!c || !pk_of(pk, c)) return ZN_EINVAL;
   return encrypt_common(c, false, pk->d, pk->d + 2 * ring_words(c), slots, n_slots, batch, seed, ct_index, ct,
                         stream);
 }
 
 int zinc_precompute(zn_ctx* c, const zn_pk* pk, uint64_t seed, zn_zcache** out) {
-  if (!c || !pk || pk->ctx != c || !out) return ZN_EINVAL;
+  if (!c || !pk_of(pk, c) || !out) return ZN_EINVAL;
   *out = nullptr;
   DeviceGuard g(c->device);
   zn_zcache* z = new (std::nothrow) zn_zcache();
@@ -549,47 +570,55 @@ int zinc_precompute(zn_ctx* c, const zn_pk* pk, uint64_t seed, zn_zcache** out) 
     return ZN_ENOMEM;
   }
   // vanilla Enc of the zero plaintext, sampling domain 3, ct_index 0
-  int rc = ensure_m(c, 1);
-  if (!rc && c->prm.log_n > 14) rc = ensure_fft(c, 1);
-  if (rc) {
-    zn_zcache_destroy(z);
-    return rc;
+  const size_t me_b = sizeof(i64) * c->n, sm_b = 2 * (size_t)c->n;
+  const size_t fft_b = c->prm.log_n > 14 ? sizeof(double) * c->n : 0;
+  int rc = ZN_OK;
+  {
+    Scratch scratch(c, 0);
+    if (!scratch.alloc(me_b + sm_b + fft_b)) {
+      rc = ZN_ENOMEM;
+    } else {
+      zn::PrepArgs pa;
+      pa.slots = nullptr;
+      pa.n_slots = 0;
+      pa.ct_index = nullptr;
+      pa.ct_index0 = 0;
+      pa.seed = seed;
+      pa.domain = 3;
+      pa.me = (i64*)scratch.p;
+      pa.small = (int8_t*)scratch.p + me_b;
+      pa.work = fft_b ? (double*)((char*)scratch.p + me_b + sm_b) : nullptr;
+      zn::EncArgs A;
+      A.key = pk->d;
+      A.keys = pk->d + 2 * ring_words(c);
+      A.me = pa.me;
+      A.small = pa.small;
+      A.out = z->d;
+      if (zn::launch_prep(c->dp, pa, false, 1, 0) != cudaSuccess ||
+          zn::launch_encrypt(c->dp, A, false, 1, c->variant, 0) != cudaSuccess)
+        rc = ZN_ECUDA;
+    }
   }
-  zn::PrepArgs pa;
-  pa.slots = nullptr;
-  pa.n_slots = 0;
-  pa.ct_index = nullptr;
-  pa.ct_index0 = 0;
-  pa.seed = seed;
-  pa.domain = 3;
-  pa.me = c->d_m;
-  pa.small = c->d_small;
-  pa.work = c->d_fft;
-  zn::EncArgs A;
-  A.key = pk->d;
-  A.keys = pk->d + 2 * ring_words(c);
-  A.me = c->d_m;
-  A.small = c->d_small;
-  A.out = z->d;
-  if (zn::launch_prep(c->dp, pa, false, 1, 0) != cudaSuccess || zn::launch_encrypt(c->dp, A, false, 1, c->variant, 0) != cudaSuccess ||
-      cudaDeviceSynchronize() != cudaSuccess) {
+  if (!rc && cudaDeviceSynchronize() != cudaSuccess) rc = ZN_ECUDA;
+  if (rc) {
     cudaGetLastError();
     zn_zcache_destroy(z);
-    return ZN_ECUDA;
+    return rc;
   }
   *out = z;
   return ZN_OK;
 }
 
 void zn_zcache_destroy(zn_zcache* z) {
-  if (!z) return;
+  if (!z || z->tag != kTagZc) return;
+  z->tag = kTagDead;
   DeviceGuard g(z->ctx->device);
   cudaFree(z->d);
   delete z;
 }
 
 int zn_zcache_export(const zn_zcache* z, uint64_t* host_out) {
-  if (!z || !host_out) return ZN_EINVAL;
+  if (!z || z->tag != kTagZc || !host_out) return ZN_EINVAL;
   DeviceGuard g(z->ctx->device);
   ZN_CUDA(cudaMemcpy(host_out, z->d, sizeof(u64) * 2 * ring_words(z->ctx), cudaMemcpyDeviceToHost));
   return ZN_OK;
@@ -623,14 +652,14 @@ int zn_zcache_import(zn_ctx* c, const uint64_t* host_in, zn_zcache** out) {
 
 int zinc_encrypt(zn_ctx* c, const zn_zcache* z, const double* slots, uint32_t n_slots, uint32_t batch, uint64_t seed,
                  const uint64_t* ct_index, uint64_t* ct, void* stream) {
-  if (!c || !z || z->ctx != c) return ZN_EINVAL;
+  if (!c || !zc_of(z, c)) return ZN_EINVAL;
   return encrypt_common(c, true, z->d, nullptr, slots, n_slots, batch, seed, ct_index, ct, stream);
 }
 
 // -------------------------------------------------------------- decrypt
 
 int ckks_decrypt(zn_ctx* c, const zn_sk* sk, const uint64_t* ct, uint32_t batch, uint64_t* out, void* stream) {
-  if (!c || !sk || sk->ctx != c) return ZN_EINVAL;
+  if (!c || !sk_of(sk, c)) return ZN_EINVAL;
   if (batch == 0) return ZN_OK;
   if (!ct || !out) return ZN_EINVAL;
   DeviceGuard g(c->device);
@@ -641,7 +670,7 @@ int ckks_decrypt(zn_ctx* c, const zn_sk* sk, const uint64_t* ct, uint32_t batch,
 
 int ckks_decrypt_decode(zn_ctx* c, const zn_sk* sk, const uint64_t* ct, uint32_t batch, uint32_t n_slots, double* out,
                         void* stream) {
-  if (!c || !sk || sk->ctx != c || n_slots > c->n / 2) return ZN_EINVAL;
+  if (!c || !sk_of(sk, c) || n_slots > c->n / 2) return ZN_EINVAL;
   if (batch == 0 || n_slots == 0) return ZN_OK;
   if (!ct || !out) return ZN_EINVAL;
   DeviceGuard g(c->device);
@@ -711,7 +740,7 @@ int zn_batch_create(const zn_job* jobs, uint32_t n_jobs, int device, zn_batch** 
     const zn_job& J = jobs[j];
     zn_ctx* c = J.ctx;
     if (!c || c->device != device || c->prm.log_n < 10 || c->prm.log_n > 15) return ZN_EINVAL;
-    if (J.zinc ? (!J.zc || J.zc->ctx != c) : (!J.pk || J.pk->ctx != c)) return ZN_EINVAL;
+    if (J.zinc ? !zc_of(J.zc, c) : !pk_of(J.pk, c)) return ZN_EINVAL;
     if (J.n_slots > c->n / 2) return ZN_EINVAL;
     if (J.count && (!J.ct || !J.ct_index || (J.n_slots && !J.slots))) return ZN_EINVAL;
     me_words += (size_t)J.count * c->n;
@@ -858,7 +887,7 @@ int zn_set_variant(zn_ctx* c, int variant) {
 int zn_get_variant(const zn_ctx* c) { return c ? c->variant : ZN_EINVAL; }
 
 int zn_autotune(zn_ctx* c, const zn_pk* pk, const zn_zcache* zc, uint32_t batch, float* ms, int* chosen) {
-  if (!c || !pk || !zc || pk->ctx != c || zc->ctx != c || batch == 0) return ZN_EINVAL;
+  if (!c || !pk_of(pk, c) || !zc_of(zc, c) || batch == 0) return ZN_EINVAL;
   DeviceGuard g(c->device);
   u64* ct = nullptr;
   u64* idx = nullptr;
