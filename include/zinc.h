@@ -46,7 +46,8 @@ enum {
   ZN_EOVERFLOW = -3,  /* an encoded coefficient reached |m_k| >= 2^62 (or was not finite) */
   ZN_ECUDA = -4,      /* a CUDA runtime call failed */
   ZN_ETIMEOUT = -5,   /* a bounded device wait gave up */
-  ZN_ENOPRIME = -6    /* no prime q < 2^b with q = 1 mod 2N is left for a chain entry */
+  ZN_ENOPRIME = -6,   /* no prime q < 2^b with q = 1 mod 2N is left for a chain entry */
+  ZN_ELIMIT = -7      /* request larger than the fixed scratch of zinc_encrypt_noalloc */
 };
 
 typedef struct zn_ctx zn_ctx;
@@ -140,6 +141,30 @@ int zn_zcache_import(zn_ctx* ctx, const uint64_t* host_in, zn_zcache** out);
 int zinc_encrypt(zn_ctx* ctx, const zn_zcache* zc, const double* slots, uint32_t n_slots,
                  uint32_t batch, uint64_t seed, const uint64_t* ct_index, uint64_t* ct,
                  void* stream);
+
+/* Allocation-free Zinc encryption (no counterpart in the paper).  For callers
+ * that must not allocate device memory during a call: code running where
+ * the allocator is off limits or too slow (a real-time loop with a fixed
+ * memory footprint, an embedding host that owns every allocation, a process
+ * whose device memory is already fully reserved).  Same arguments and
+ * results as zinc_encrypt, but the per-call scratch (encoded message plus
+ * noise and the small polynomials; an FFT area for 2^15 rings) lives in one
+ * static 16 MiB device array of the library instead of the context's memory
+ * pool, and nothing is allocated or freed by the call.
+ *  - Limit: batch * (10 N bytes, 18 N for N = 2^15, each part rounded up to
+ *    256 bytes) must fit in ZN_NOALLOC_SCRATCH_BYTES; larger requests return
+ *    ZN_ELIMIT without launching anything (split them into smaller calls).
+ *  - The first call on a device looks up the array's device address (once
+ *    per device); make that first call before any stream capture.
+ *  - Every call on a device shares the one array: calls whose work overlaps
+ *    on the GPU (different streams, or host threads) race and corrupt each
+ *    other's results; serialise them.  The array keeps the last call's
+ *    contents; nothing in it needs to start at zero (every byte a call reads
+ *    is first written by the same call). */
+#define ZN_NOALLOC_SCRATCH_BYTES (16u << 20)
+int zinc_encrypt_noalloc(zn_ctx* ctx, const zn_zcache* zc, const double* slots, uint32_t n_slots,
+                         uint32_t batch, uint64_t seed, const uint64_t* ct_index, uint64_t* ct,
+                         void* stream);
 
 /* -------------------------------------------------------------- decrypt */
 

@@ -15,7 +15,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libzinc.so")
 MAX_PRIMES = 16
 
-ZN_OK, ZN_EINVAL, ZN_ENOMEM, ZN_EOVERFLOW, ZN_ECUDA, ZN_ETIMEOUT, ZN_ENOPRIME = 0, -1, -2, -3, -4, -5, -6
+ZN_OK, ZN_EINVAL, ZN_ENOMEM, ZN_EOVERFLOW, ZN_ECUDA, ZN_ETIMEOUT, ZN_ENOPRIME, ZN_ELIMIT = 0, -1, -2, -3, -4, -5, -6, -7
+NOALLOC_SCRATCH_BYTES = 16 << 20
 
 # sampler kinds for zn_sample
 KIND_TERNARY, KIND_GAUSSIAN, KIND_UNIFORM = 0, 1, 2
@@ -61,6 +62,7 @@ _SIGS = {
     "zn_zcache_export": (_i32, [_vp, _vp]),
     "zn_zcache_import": (_i32, [_vp, _vp, _pp]),
     "zinc_encrypt": (_i32, [_vp, _vp, _vp, _u32, _u32, _u64, _vp, _vp, _vp]),
+    "zinc_encrypt_noalloc": (_i32, [_vp, _vp, _vp, _u32, _u32, _u64, _vp, _vp, _vp]),
     "ckks_decrypt": (_i32, [_vp, _vp, _vp, _u32, _vp, _vp]),
     "ckks_decrypt_decode": (_i32, [_vp, _vp, _vp, _u32, _u32, _vp, _vp]),
     "ckks_add": (_i32, [_vp, _vp, _vp, _u32, _vp, _vp]),
@@ -312,6 +314,21 @@ def zn_zcache_import(ctx, arr):
 def zinc_encrypt(ctx, zc, slots, seed, ct_index, out=None, stream=None):
     """Zinc encryption (Algorithm 1): same shapes as ckks_encrypt."""
     return _enc(lib().zinc_encrypt, ctx, zc, slots, seed, ct_index, out, stream, "zinc_encrypt")
+
+
+def zinc_encrypt_noalloc(ctx, zc, slots, seed, ct_index, out, stream=None):
+    """Zinc encryption that allocates nothing: the caller supplies `out`
+    (int64 [B, 2, L, N]); the library's fixed scratch array holds the
+    intermediates (see include/zinc.h for the size limit and the rule that
+    overlapping calls race)."""
+    import torch
+    B, ns = slots.shape
+    _dev(slots, torch.float64, None, "slots")
+    _dev(ct_index, torch.int64, (B,), "ct_index")
+    _dev(out, torch.int64, (B, 2, ctx.L, ctx.n), "out")
+    _check(lib().zinc_encrypt_noalloc(ctx.handle, zc.handle, slots.data_ptr(), ns, B, seed, ct_index.data_ptr(),
+                                      out.data_ptr(), _stream(stream)), "zinc_encrypt_noalloc")
+    return out
 
 
 def ckks_decrypt(ctx, sk, ct, out=None, stream=None):

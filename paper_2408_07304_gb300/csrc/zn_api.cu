@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -193,6 +194,7 @@ const char* zn_strerror(int status) {
     case ZN_ECUDA: return "CUDA runtime error";
     case ZN_ETIMEOUT: return "device wait timed out";
     case ZN_ENOPRIME: return "no NTT-friendly prime left for a chain entry";
+    case ZN_ELIMIT: return "batch exceeds the fixed scratch of the allocation-free entry point";
     default: return "unknown status";
   }
 }
@@ -987,4 +989,69 @@ int zn_sample(zn_ctx* c, int kind, uint64_t seed, uint32_t domain, uint32_t poly
   return ZN_OK;
 }
 
+// ------------------------------------------- allocation-free Zinc encryption
+
 }  // extern "C"
+
+// The fixed scratch of zinc_encrypt_noalloc.  In host code this name is only
+// a stand-in for the device array: kernels receive the address returned by
+// cudaGetSymbolAddress for the current device.
+static __device__ __align__(256) unsigned char zn_noalloc_scratch[ZN_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices];   // device address of the array, per device (set up once)
+
+// With `device` current: the array's device address, looked up on first use.
+int noalloc_scratch(int device, void** out) {
+  if (device < 0 || device >= kMaxDevices) return ZN_EINVAL;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[device]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, zn_noalloc_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return ZN_ECUDA;
+    }
+    g_noalloc_ptr[device] = p;
+  }
+  *out = g_noalloc_ptr[device];
+  return ZN_OK;
+}
+}  // namespace
+
+extern "C" int zinc_encrypt_noalloc(zn_ctx* c, const zn_zcache* z, const double* slots, uint32_t n_slots,
+                                    uint32_t batch, uint64_t seed, const uint64_t* ct_index, uint64_t* ct,
+                                    void* stream) {
+  if (!c || !zc_of(z, c) || n_slots > c->n / 2) return ZN_EINVAL;
+  if (batch == 0) return ZN_OK;
+  if (!ct || !ct_index || (n_slots && !slots)) return ZN_EINVAL;
+  const size_t n = c->n;
+  const size_t me_b = ((size_t)batch * 8 * n + 255) / 256 * 256;
+  const size_t sm_b = ((size_t)batch * 2 * n + 255) / 256 * 256;
+  const size_t fft_b = c->prm.log_n > 14 ? (size_t)batch * 8 * n : 0;
+  if (me_b + sm_b + fft_b > ZN_NOALLOC_SCRATCH_BYTES) return ZN_ELIMIT;
+  DeviceGuard g(c->device);
+  unsigned char* base = nullptr;
+  int rc = noalloc_scratch(c->device, (void**)&base);
+  if (rc) return rc;
+  zn::PrepArgs pa;
+  pa.slots = slots;
+  pa.n_slots = n_slots;
+  pa.ct_index = ct_index;
+  pa.ct_index0 = 0;
+  pa.seed = seed;
+  pa.domain = 1;                                   // Zinc randomiser
+  pa.me = (i64*)base;
+  pa.small = (int8_t*)(base + me_b);
+  pa.work = fft_b ? (double*)(base + me_b + sm_b) : nullptr;
+  zn::EncArgs A;
+  A.key = z->d;
+  A.keys = nullptr;
+  A.me = pa.me;
+  A.small = pa.small;
+  A.out = ct;
+  ZN_CUDA(zn::launch_prep(c->dp, pa, true, batch, S(stream)));
+  ZN_CUDA(zn::launch_encrypt(c->dp, A, true, batch, c->variant, S(stream)));
+  return ZN_OK;
+}
