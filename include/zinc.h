@@ -148,12 +148,12 @@ int zinc_encrypt(zn_ctx* ctx, const zn_zcache* zc, const double* slots, uint32_t
  * memory footprint, an embedding host that owns every allocation, a process
  * whose device memory is already fully reserved).  Same arguments and
  * results as zinc_encrypt, but the per-call scratch (encoded message plus
- * noise and the small polynomials; an FFT area for 2^15 rings) lives in one
- * static 16 MiB device array of the library instead of the context's memory
- * pool, and nothing is allocated or freed by the call.
- *  - Limit: batch * (10 N bytes, 18 N for N = 2^15, each part rounded up to
- *    256 bytes) must fit in ZN_NOALLOC_SCRATCH_BYTES; larger requests return
- *    ZN_ELIMIT without launching anything (split them into smaller calls).
+ * noise and the small polynomials) lives in one static 16 MiB device array
+ * of the library instead of the context's memory pool, and nothing is
+ * allocated or freed by the call.
+ *  - Limit: batch * 10 N bytes (8 N + 2 N, each part rounded up to 256 bytes)
+ *    must fit in ZN_NOALLOC_SCRATCH_BYTES; larger requests return ZN_ELIMIT
+ *    without launching anything (split them into smaller calls).
  *  - The first call on a device looks up the array's device address (once
  *    per device); make that first call before any stream capture.
  *  - Every call on a device shares the one array: calls whose work overlaps
@@ -239,10 +239,12 @@ int zn_batch_info(const zn_batch* b, uint32_t* prep_units, uint32_t* packets);
 
 /* -------------------------------------------------------------- autotuning */
 
-/* Launch shapes of the encryption kernels.  Variant 0: each thread owns 32
- * NTT elements (2^(log_n-5) threads per block); variant 1: 16 elements, twice
- * the threads (rings of 2^12 and above; smaller rings always use 0). */
-#define ZN_VARIANTS 2
+/* Launch shapes of the encryption kernels.  Bit 0 of the variant: each thread
+ * owns 16 NTT elements (twice the threads) instead of 32 (rings of 2^12 and
+ * above; smaller rings always use 32).  Bit 1: ciphertext-major grid (the
+ * blocks of a wave share one prime's twiddles and keys) instead of
+ * prime-major. */
+#define ZN_VARIANTS 4
 int zn_set_variant(zn_ctx* ctx, int variant);
 int zn_get_variant(const zn_ctx* ctx);
 

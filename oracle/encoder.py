@@ -16,14 +16,23 @@ m_{k+n} = scale Im S_k (because zeta^(-5^j n) = -i).
 Two forms:
 * ``encode_direct``: the defining sum, evaluated term by term (pin only).
 * ``encode``: the FP64 procedure whose every IEEE operation is specified, so
-  that an independent implementation can reproduce the integers bit for bit:
-    1. y[t_j] = z_j; X = y in bit-reversed order (log2 n bits);
-    2. radix-2 decimation-in-time: for h = 1, 2, .., n/2, every block of 2h and
-       k < h: w = T[k N / h]; (a, c) = (X[b+k], X[b+k+h]);
+  that an independent implementation can reproduce the integers bit for bit.
+  y is real, so its length-n DFT is taken through a complex DFT of half the
+  length (the standard real-input split):
+    1. y[t_j] = z_j (other entries 0); g_s = y[2s] + i y[2s+1], s < h = n/2;
+    2. G = DFT_h(g) by radix-2 decimation in time: g in bit-reversed order
+       (log2 h bits); for hh = 1, 2, .., h/2, every block of 2hh and k < hh:
+       w = T[k N / hh]; (a, c) = (X[b+k], X[b+k+hh]);
        tr = c.re*w.re - c.im*w.im; ti = c.re*w.im + c.im*w.re;
-       X[b+k] = (a.re + tr, a.im + ti); X[b+k+h] = (a.re - tr, a.im - ti);
-    3. twist: S[k] = X[k] * T[k] with the same complex product formula;
-    4. m_k = rint(2^s Re S[k]), m_{k+n} = rint(2^s Im S[k]), s = log2 Delta + 1 - log2 N
+       X[b+k] = (a.re + tr, a.im + ti); X[b+k+hh] = (a.re - tr, a.im - ti);
+    3. split, for k = 0..h with G[h] = G[0]: a = G[k], b = G[h-k];
+       sr = a.re + b.re; si = a.im - b.im; dr = a.re - b.re; di = a.im + b.im;
+       E = (0.5*sr, 0.5*si); O = (0.5*di, -(0.5*dr));
+       W = T[4k] for k < h, W = (-1, 0) for k = h;
+       t = (O.re*W.re - O.im*W.im, O.re*W.im + O.im*W.re);
+       X[k] = (E.re + t.re, E.im + t.im); X[n-k] = conj(X[k]) for 0 < k < h;
+    4. twist: S[k] = X[k] * T[k] (the same complex product formula), k < n;
+    5. m_k = rint(2^s Re S[k]), m_{k+n} = rint(2^s Im S[k]), s = log2 Delta + 1 - log2 N
        (an exact power-of-two scaling), ties to even.
   Each product and sum is a separate correctly rounded FP64 operation (no
   fused multiply-add).  T[k] = cos(pi k / N) - i sin(pi k / N), k < N, each
@@ -131,35 +140,70 @@ def _brv_perm(bits):
     return r
 
 
-def encode_real(z, log_n: int, log2_delta: int):
-    """Steps 1-3 of the specified FFT procedure and the power-of-two scaling
-    (exact); returns the N unrounded coefficients as float64."""
-    n = 1 << log_n
-    half = n // 2
-    z = np.asarray(z, dtype=np.float64)
-    assert z.ndim == 1 and z.shape[0] <= half
-    y = np.zeros(half)
-    y[slot_index(log_n)[: z.shape[0]]] = z
-    lg = half.bit_length() - 1
-    xr = y[_brv_perm(lg)].copy()
-    xi = np.zeros(half)
-    tr_, ti_ = twiddles(log_n)
-    h = 1
-    while h < half:
-        k = np.arange(h)
-        wr = tr_[k * (n // h)]
-        wi = ti_[k * (n // h)]
-        xr = xr.reshape(-1, 2 * h)
-        xi = xi.reshape(-1, 2 * h)
-        ar, ai = xr[:, :h].copy(), xi[:, :h].copy()
-        cr, ci = xr[:, h:].copy(), xi[:, h:].copy()
+def _dit(xr, xi, log_n, tr_, ti_):
+    """Radix-2 DIT butterflies (step 2) on bit-reversed input, in place order."""
+    n_ring = 1 << log_n
+    size = xr.shape[0]
+    hh = 1
+    while hh < size:
+        k = np.arange(hh)
+        wr = tr_[k * (n_ring // hh)]
+        wi = ti_[k * (n_ring // hh)]
+        xr = xr.reshape(-1, 2 * hh)
+        xi = xi.reshape(-1, 2 * hh)
+        ar, ai = xr[:, :hh].copy(), xi[:, :hh].copy()
+        cr, ci = xr[:, hh:].copy(), xi[:, hh:].copy()
         tr = cr * wr - ci * wi
         ti = cr * wi + ci * wr
         xr = np.concatenate([ar + tr, ar - tr], axis=1).reshape(-1)
         xi = np.concatenate([ai + ti, ai - ti], axis=1).reshape(-1)
-        h *= 2
-    wr = tr_[:half]
-    wi = ti_[:half]
+        hh *= 2
+    return xr, xi
+
+
+def encode_real(z, log_n: int, log2_delta: int):
+    """Steps 1-4 of the specified procedure and the power-of-two scaling
+    (exact); returns the N unrounded coefficients as float64."""
+    n_ring = 1 << log_n
+    n = n_ring // 2
+    h = n // 2
+    z = np.asarray(z, dtype=np.float64)
+    assert z.ndim == 1 and z.shape[0] <= n
+    y = np.zeros(n)
+    y[slot_index(log_n)[: z.shape[0]]] = z
+    lg = h.bit_length() - 1
+    perm = _brv_perm(lg)
+    tr_, ti_ = twiddles(log_n)
+    gr, gi = _dit(y[0::2][perm].copy(), y[1::2][perm].copy(), log_n, tr_, ti_)   # steps 1, 2
+    # step 3: split the half-length transform into X[0..n)
+    k = np.arange(h + 1)
+    Gr = np.concatenate([gr, gr[:1]])
+    Gi = np.concatenate([gi, gi[:1]])
+    ar, ai = Gr[k], Gi[k]
+    br, bi = Gr[h - k], Gi[h - k]
+    sr = ar + br
+    si = ai - bi
+    dr = ar - br
+    di = ai + bi
+    er = 0.5 * sr
+    ei = 0.5 * si
+    o_r = 0.5 * di
+    o_i = -(0.5 * dr)
+    wr = np.where(k < h, tr_[(4 * k) % n_ring], -1.0)
+    wi = np.where(k < h, ti_[(4 * k) % n_ring], 0.0)
+    t_r = o_r * wr - o_i * wi
+    t_i = o_r * wi + o_i * wr
+    xk_r = er + t_r
+    xk_i = ei + t_i
+    xr = np.empty(n)
+    xi = np.empty(n)
+    xr[: h + 1] = xk_r
+    xi[: h + 1] = xk_i
+    xr[h + 1:] = xk_r[1:h][::-1]
+    xi[h + 1:] = -xk_i[1:h][::-1]
+    # step 4: twist
+    wr = tr_[:n]
+    wi = ti_[:n]
     sr = xr * wr - xi * wi
     si = xr * wi + xi * wr
     scale = 2.0 ** (log2_delta + 1 - log_n)

@@ -28,7 +28,7 @@ struct zn_ctx {
   double* d_etw;      // [2][N]
   int* d_slot;        // [N/2]
   unsigned* d_status;
-  cudaMemPool_t pool; // stream-ordered scratch (prep outputs, FFT work areas)
+  cudaMemPool_t pool; // stream-ordered scratch (prep outputs)
   int variant;        // encryption launch shape (zn_autotune)
   // launch timing (benchmark instrumentation)
   bool timing;
@@ -143,16 +143,12 @@ int encrypt_common(zn_ctx* c, bool zinc, const u64* key, const u64* keys, const 
   DeviceGuard g(c->device);
   const uint32_t chunk = encode_chunk(c);
   const uint32_t first = batch < chunk ? batch : chunk;
-  // per chunk: message + noise (int64 [N]), small polynomials (int8 [2][N]),
-  // and for 2^15 rings an FFT work area (double [N])
+  // per chunk: message + noise (int64 [N]) and small polynomials (int8 [2][N])
   const size_t me_b = sizeof(i64) * first * c->n, sm_b = 2 * (size_t)first * c->n;
-  const size_t fft_b = c->prm.log_n > 14 ? sizeof(double) * first * c->n : 0;
-  const size_t sm_pad = (sm_b + 255) / 256 * 256;
   Scratch scratch(c, S(stream));
-  if (!scratch.alloc(me_b + sm_pad + fft_b)) return ZN_ENOMEM;
+  if (!scratch.alloc(me_b + sm_b)) return ZN_ENOMEM;
   i64* me = (i64*)scratch.p;
   int8_t* small = (int8_t*)scratch.p + me_b;
-  double* fft = fft_b ? (double*)((char*)scratch.p + me_b + sm_pad) : nullptr;
   for (uint32_t b0 = 0; b0 < batch; b0 += chunk) {
     const uint32_t nb = (batch - b0) < chunk ? (batch - b0) : chunk;
     zn::PrepArgs pa;
@@ -164,12 +160,12 @@ int encrypt_common(zn_ctx* c, bool zinc, const u64* key, const u64* keys, const 
     pa.domain = zinc ? 1u : 0u;
     pa.me = me;
     pa.small = small;
-    pa.work = fft;
     {
       TimedLaunch t(c, ZN_TIME_ENCODE, S(stream));
       ZN_CUDA(zn::launch_prep(c->dp, pa, zinc, nb, S(stream)));
     }
     zn::EncArgs A;
+    A.swap = 0;
     A.key = key;
     A.keys = keys;
     A.me = me;
@@ -544,9 +540,7 @@ int ckks_encode(zn_ctx* c, const double* slots, uint32_t n_slots, uint32_t batch
   if (batch == 0) return ZN_OK;
   if (!out || (n_slots && !slots)) return ZN_EINVAL;
   DeviceGuard g(c->device);
-  Scratch fft(c, S(stream));
-  if (c->prm.log_n > 14 && !fft.alloc(sizeof(double) * batch * (size_t)c->n)) return ZN_ENOMEM;
-  ZN_CUDA(zn::launch_encode(c->dp, slots, n_slots, batch, (i64*)out, (double*)fft.p, S(stream)));
+  ZN_CUDA(zn::launch_encode(c->dp, slots, n_slots, batch, (i64*)out, S(stream)));
   return ZN_OK;
 }
 
@@ -573,11 +567,10 @@ int zinc_precompute(zn_ctx* c, const zn_pk* pk, uint64_t seed, zn_zcache** out) 
   }
   // vanilla Enc of the zero plaintext, sampling domain 3, ct_index 0
   const size_t me_b = sizeof(i64) * c->n, sm_b = 2 * (size_t)c->n;
-  const size_t fft_b = c->prm.log_n > 14 ? sizeof(double) * c->n : 0;
   int rc = ZN_OK;
   {
     Scratch scratch(c, 0);
-    if (!scratch.alloc(me_b + sm_b + fft_b)) {
+    if (!scratch.alloc(me_b + sm_b)) {
       rc = ZN_ENOMEM;
     } else {
       zn::PrepArgs pa;
@@ -589,8 +582,8 @@ int zinc_precompute(zn_ctx* c, const zn_pk* pk, uint64_t seed, zn_zcache** out) 
       pa.domain = 3;
       pa.me = (i64*)scratch.p;
       pa.small = (int8_t*)scratch.p + me_b;
-      pa.work = fft_b ? (double*)((char*)scratch.p + me_b + sm_b) : nullptr;
       zn::EncArgs A;
+      A.swap = 0;
       A.key = pk->d;
       A.keys = pk->d + 2 * ring_words(c);
       A.me = pa.me;
@@ -715,7 +708,6 @@ struct zn_batch {
   int* d_counters;        // [2]: prep, encrypt
   i64* d_me;
   int8_t* d_small;
-  double* d_work;         // [sms][2^15] FFT scratch for 2^15 rings
   cudaGraphExec_t exec;
 };
 
@@ -729,7 +721,6 @@ void zn_batch_destroy(zn_batch* b) {
   cudaFree(b->d_counters);
   cudaFree(b->d_me);
   cudaFree(b->d_small);
-  cudaFree(b->d_work);
   delete b;
 }
 
@@ -737,7 +728,6 @@ int zn_batch_create(const zn_job* jobs, uint32_t n_jobs, int device, zn_batch** 
   if (!jobs || !out || n_jobs == 0) return ZN_EINVAL;
   *out = nullptr;
   size_t me_words = 0, small_bytes = 0;
-  bool big = false;
   for (uint32_t j = 0; j < n_jobs; ++j) {
     const zn_job& J = jobs[j];
     zn_ctx* c = J.ctx;
@@ -747,7 +737,6 @@ int zn_batch_create(const zn_job* jobs, uint32_t n_jobs, int device, zn_batch** 
     if (J.count && (!J.ct || !J.ct_index || (J.n_slots && !J.slots))) return ZN_EINVAL;
     me_words += (size_t)J.count * c->n;
     small_bytes += 2 * (size_t)J.count * c->n;
-    big |= c->prm.log_n == 15;
   }
   DeviceGuard g(device);
   zn_batch* b = new (std::nothrow) zn_batch();
@@ -768,7 +757,6 @@ int zn_batch_create(const zn_job* jobs, uint32_t n_jobs, int device, zn_batch** 
   int rc = ZN_OK;
   if ((me_words && cudaMalloc(&b->d_me, sizeof(i64) * me_words) != cudaSuccess) ||
       (small_bytes && cudaMalloc(&b->d_small, small_bytes) != cudaSuccess) ||
-      (big && cudaMalloc(&b->d_work, sizeof(double) * (size_t)b->sms * (1u << 15)) != cudaSuccess) ||
       cudaMalloc(&b->d_counters, 2 * sizeof(int)) != cudaSuccess)
     rc = ZN_ENOMEM;
   std::vector<zn::PrepUnit> units;
@@ -794,7 +782,6 @@ int zn_batch_create(const zn_job* jobs, uint32_t n_jobs, int device, zn_batch** 
     D.Pr.domain = J.zinc ? 1u : 0u;
     D.Pr.me = b->d_me + me_off;
     D.Pr.small = b->d_small + sm_off;
-    D.Pr.work = nullptr;
     me_off += (size_t)J.count * c->n;
     sm_off += 2 * (size_t)J.count * c->n;
   }
@@ -839,7 +826,7 @@ int zn_batch_create(const zn_job* jobs, uint32_t n_jobs, int device, zn_batch** 
 static int batch_enqueue(zn_batch* b, cudaStream_t st) {
   ZN_CUDA(cudaMemsetAsync(b->d_counters, 0, 2 * sizeof(int), st));
   if (b->n_prep)
-    ZN_CUDA(zn::launch_batch_prep(b->d_jobs, b->d_units, (int)b->n_prep, b->d_counters, b->d_work, b->sms, st));
+    ZN_CUDA(zn::launch_batch_prep(b->d_jobs, b->d_units, (int)b->n_prep, b->d_counters, b->sms, st));
   if (b->n_packets)
     ZN_CUDA(zn::launch_batch_encrypt(b->d_jobs, b->d_packets, (int)b->n_packets, b->d_counters + 1, b->sms, st));
   return ZN_OK;
@@ -1029,8 +1016,7 @@ extern "C" int zinc_encrypt_noalloc(zn_ctx* c, const zn_zcache* z, const double*
   const size_t n = c->n;
   const size_t me_b = ((size_t)batch * 8 * n + 255) / 256 * 256;
   const size_t sm_b = ((size_t)batch * 2 * n + 255) / 256 * 256;
-  const size_t fft_b = c->prm.log_n > 14 ? (size_t)batch * 8 * n : 0;
-  if (me_b + sm_b + fft_b > ZN_NOALLOC_SCRATCH_BYTES) return ZN_ELIMIT;
+  if (me_b + sm_b > ZN_NOALLOC_SCRATCH_BYTES) return ZN_ELIMIT;
   DeviceGuard g(c->device);
   unsigned char* base = nullptr;
   int rc = noalloc_scratch(c->device, (void**)&base);
@@ -1044,8 +1030,8 @@ extern "C" int zinc_encrypt_noalloc(zn_ctx* c, const zn_zcache* z, const double*
   pa.domain = 1;                                   // Zinc randomiser
   pa.me = (i64*)base;
   pa.small = (int8_t*)(base + me_b);
-  pa.work = fft_b ? (double*)(base + me_b + sm_b) : nullptr;
   zn::EncArgs A;
+  A.swap = 0;
   A.key = z->d;
   A.keys = nullptr;
   A.me = pa.me;

@@ -6,28 +6,31 @@ namespace zn {
 
 // ------------------------------------------------------------------ encode
 
-// Encoder core: one block per slot vector; (re, im) = n = N/2 doubles each,
-// in shared memory (n <= 8192) or in a global scratch area (larger rings).
-// out(k, m_k, m_{k+n}) receives the rounded coefficients, k < n.
+// Encoder core: one block per slot vector.  (re, im) hold h = N/4 doubles
+// each, in shared memory.  The real length-n DFT (n = N/2) is taken through a
+// complex DFT of length h and a split step; every FP64 operation follows the
+// specified order (see fft_dit and the split below).  out(k, m_k, m_{k+n})
+// receives the rounded coefficients, once for every k < n.
 template <class Out>
 __device__ __forceinline__ void encode_core(const DevParams& P, const double* __restrict__ z, uint32_t n_slots,
                                             double* re, double* im, Out& out) {
-  const int log_n = P.log_n, N = 1 << log_n, n = N >> 1;
-  for (int r = threadIdx.x; r < n; r += blockDim.x) {
-    const int t = brv_bits(r, log_n - 1);
-    const int j = __ldg(P.slot_of_t + t);
-    re[r] = (j < (int)n_slots) ? __ldg(z + j) : 0.0;
-    im[r] = 0.0;
+  const int log_n = P.log_n, N = 1 << log_n, n = N >> 1, h = n >> 1, lh = log_n - 2;
+  // g_s = y[2s] + i y[2s+1] with y[t_j] = z_j, in bit-reversed order
+  for (int r = threadIdx.x; r < h; r += blockDim.x) {
+    const int s2 = 2 * brv_bits(r, lh);
+    const int j0 = __ldg(P.slot_of_t + s2), j1 = __ldg(P.slot_of_t + s2 + 1);
+    re[r] = (j0 < (int)n_slots) ? __ldg(z + j0) : 0.0;
+    im[r] = (j1 < (int)n_slots) ? __ldg(z + j1) : 0.0;
   }
   __syncthreads();
-  fft_dit(re, im, log_n, P.etw, false);
-  // twist by T[k], exact power-of-two scaling, rint (ties to even)
+  fft_dit(re, im, lh, log_n, P.etw, false);
   const double scale = ldexp(1.0, P.log2_delta + 1 - log_n);
   const double* twr = P.etw;
   const double* twi = P.etw + N;
   const double lim = 4611686018427387904.0;   // 2^62
-  for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    const double xr = re[k], xi = im[k], wr = __ldg(twr + k), wi = __ldg(twi + k);
+  // twist by T[k], exact power-of-two scaling, rint (ties to even)
+  auto emit = [&](int k, double xr, double xi) {
+    const double wr = __ldg(twr + k), wi = __ldg(twi + k);
     const double sr = __dsub_rn(__dmul_rn(xr, wr), __dmul_rn(xi, wi));
     const double si = __dadd_rn(__dmul_rn(xr, wi), __dmul_rn(xi, wr));
     double a = rint(__dmul_rn(sr, scale)), b = rint(__dmul_rn(si, scale));
@@ -37,6 +40,22 @@ __device__ __forceinline__ void encode_core(const DevParams& P, const double* __
       b = 0.0;
     }
     out(k, (i64)a, (i64)b);
+  };
+  // split: X[k] from G[k] and G[h-k] (G[h] = G[0]); X[n-k] = conj(X[k])
+  for (int k = threadIdx.x; k <= h; k += blockDim.x) {
+    const int ka = k == h ? 0 : k, kb = k == 0 ? 0 : h - k;
+    const double ar = re[ka], ai = im[ka], br = re[kb], bi = im[kb];
+    const double sr = __dadd_rn(ar, br), si = __dsub_rn(ai, bi);
+    const double dr = __dsub_rn(ar, br), di = __dadd_rn(ai, bi);
+    const double er = __dmul_rn(0.5, sr), ei = __dmul_rn(0.5, si);
+    const double o_r = __dmul_rn(0.5, di), o_i = -__dmul_rn(0.5, dr);
+    const double wr = k < h ? __ldg(twr + 4 * k) : -1.0;
+    const double wi = k < h ? __ldg(twi + 4 * k) : 0.0;
+    const double t_r = __dsub_rn(__dmul_rn(o_r, wr), __dmul_rn(o_i, wi));
+    const double t_i = __dadd_rn(__dmul_rn(o_r, wi), __dmul_rn(o_i, wr));
+    const double xr = __dadd_rn(er, t_r), xi = __dadd_rn(ei, t_i);
+    emit(k, xr, xi);
+    if (k > 0 && k < h) emit(n - k, xr, -xi);
   }
 }
 
@@ -52,17 +71,9 @@ __device__ __forceinline__ void encode_one(const DevParams& P, const double* __r
 
 __global__ void k_encode_smem(DevParams P, const double* __restrict__ slots, uint32_t n_slots, i64* __restrict__ out) {
   extern __shared__ double smd[];
-  const int N = 1 << P.log_n, n = N >> 1;
+  const int N = 1 << P.log_n, h = N >> 2;
   const size_t b = blockIdx.x;
-  encode_one(P, slots + b * n_slots, n_slots, smd, smd + n, out + b * N);
-}
-
-__global__ void k_encode_gmem(DevParams P, const double* __restrict__ slots, uint32_t n_slots, i64* __restrict__ out,
-                              double* __restrict__ work) {
-  const int N = 1 << P.log_n, n = N >> 1;
-  const size_t b = blockIdx.x;
-  double* re = work + b * 2 * (size_t)n;
-  encode_one(P, slots + b * n_slots, n_slots, re, re + n, out + b * N);
+  encode_one(P, slots + b * n_slots, n_slots, smd, smd + h, out + b * N);
 }
 
 // -------------------------------------------------------------------- prep
@@ -117,24 +128,15 @@ __device__ __forceinline__ void prep_one(const DevParams& P, const PrepArgs& A, 
 template <bool ZINC>
 __global__ void k_prep_smem(DevParams P, PrepArgs A) {
   extern __shared__ double smd[];
-  const int n = 1 << (P.log_n - 1);
-  prep_one<ZINC>(P, A, blockIdx.x, smd, smd + n);
-}
-
-template <bool ZINC>
-__global__ void k_prep_gmem(DevParams P, PrepArgs A) {
-  const int N = 1 << P.log_n, n = N >> 1;
-  double* re = A.work + (size_t)blockIdx.x * N;
-  prep_one<ZINC>(P, A, blockIdx.x, re, re + n);
+  const int h = 1 << (P.log_n - 2);
+  prep_one<ZINC>(P, A, blockIdx.x, smd, smd + h);
 }
 
 // Persistent prep over a mixed work list: one 512-thread block per SM takes
-// the next ciphertext from a global counter (zero at launch).  Rings up to
-// 2^14 transform in shared memory, 2^15 in this block's slice of `work`
-// (2^15 doubles per block).
+// the next ciphertext from a global counter (zero at launch); the FFT of
+// rings up to 2^15 fits in the block's 128 KiB of shared memory.
 __global__ void __launch_bounds__(512, 1) k_batch_prep(const JobDesc* __restrict__ jobs,
-                                                       const PrepUnit* __restrict__ units, int n_units, int* counter,
-                                                       double* work) {
+                                                       const PrepUnit* __restrict__ units, int n_units, int* counter) {
   extern __shared__ double smd[];
   __shared__ int s_next;
   for (;;) {
@@ -145,10 +147,9 @@ __global__ void __launch_bounds__(512, 1) k_batch_prep(const JobDesc* __restrict
     if (p >= n_units) break;
     const PrepUnit u = units[p];
     const JobDesc& J = jobs[u.job];
-    const int n = 1 << (J.P.log_n - 1);
-    double* re = J.P.log_n <= 14 ? smd : work + (size_t)blockIdx.x * (2 * (size_t)n);
-    if (J.zinc) prep_one<true>(J.P, J.Pr, u.b, re, re + n);
-    else prep_one<false>(J.P, J.Pr, u.b, re, re + n);
+    const int h = 1 << (J.P.log_n - 2);
+    if (J.zinc) prep_one<true>(J.P, J.Pr, u.b, smd, smd + h);
+    else prep_one<false>(J.P, J.Pr, u.b, smd, smd + h);
     __syncthreads();
   }
 }
@@ -254,7 +255,7 @@ __global__ void k_decode(DevParams P, const u64* __restrict__ coeffs, uint32_t n
     im[r] = mr * wi + mi * wr;
   }
   __syncthreads();
-  fft_dit(re, im, log_n, P.etw, true);
+  fft_dit(re, im, log_n - 1, log_n, P.etw, true);
   const double inv_delta = ldexp(1.0, -P.log2_delta);
   // slot j sits at t_j = (5^j mod 2N - 1)/4; slot_of_t is the inverse map
   for (int t = threadIdx.x; t < n; t += blockDim.x) {
@@ -300,33 +301,25 @@ static unsigned grid_for(size_t total, int block) {
 }
 
 cudaError_t launch_encode(const DevParams& P, const double* slots, uint32_t n_slots, uint32_t batch, i64* out,
-                          double* work, cudaStream_t st) {
+                          cudaStream_t st) {
   if (batch == 0) return cudaSuccess;
-  const int n = 1 << (P.log_n - 1);
-  const int block = n / 2 < 512 ? (n / 2 < 32 ? 32 : n / 2) : 512;
-  if (P.log_n <= 14) {
-    const size_t smem = 2 * sizeof(double) * (size_t)n;
-    cudaError_t e = cudaFuncSetAttribute(k_encode_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_encode_smem<<<batch, block, smem, st>>>(P, slots, n_slots, out);
-  } else {
-    k_encode_gmem<<<batch, block, 0, st>>>(P, slots, n_slots, out, work);
-  }
+  const int h = 1 << (P.log_n - 2);
+  const int block = h / 2 < 512 ? (h / 2 < 32 ? 32 : h / 2) : 512;
+  const size_t smem = 2 * sizeof(double) * (size_t)h;
+  cudaError_t e = cudaFuncSetAttribute(k_encode_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_encode_smem<<<batch, block, smem, st>>>(P, slots, n_slots, out);
   return cudaGetLastError();
 }
 
 template <bool ZINC>
 static cudaError_t prep_launch(const DevParams& P, const PrepArgs& A, uint32_t batch, cudaStream_t st) {
-  const int n = 1 << (P.log_n - 1);
-  const int block = n / 2 < 512 ? (n / 2 < 32 ? 32 : n / 2) : 512;
-  if (P.log_n <= 14) {
-    const size_t smem = A.n_slots ? 2 * sizeof(double) * (size_t)n : 0;
-    cudaError_t e = cudaFuncSetAttribute(k_prep_smem<ZINC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_prep_smem<ZINC><<<batch, block, smem, st>>>(P, A);
-  } else {
-    k_prep_gmem<ZINC><<<batch, block, 0, st>>>(P, A);
-  }
+  const int h = 1 << (P.log_n - 2);
+  const int block = h / 2 < 512 ? (h / 2 < 32 ? 32 : h / 2) : 512;
+  const size_t smem = A.n_slots ? 2 * sizeof(double) * (size_t)h : 0;
+  cudaError_t e = cudaFuncSetAttribute(k_prep_smem<ZINC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_prep_smem<ZINC><<<batch, block, smem, st>>>(P, A);
   return cudaGetLastError();
 }
 
@@ -335,9 +328,9 @@ cudaError_t launch_prep(const DevParams& P, const PrepArgs& A, bool zinc, uint32
   return zinc ? prep_launch<true>(P, A, batch, st) : prep_launch<false>(P, A, batch, st);
 }
 
-cudaError_t launch_batch_prep(const JobDesc* jobs, const PrepUnit* units, int n_units, int* counter, double* work,
-                              int grid, cudaStream_t st) {
-  k_batch_prep<<<grid, 512, sizeof(double) << 14, st>>>(jobs, units, n_units, counter, work);
+cudaError_t launch_batch_prep(const JobDesc* jobs, const PrepUnit* units, int n_units, int* counter, int grid,
+                              cudaStream_t st) {
+  k_batch_prep<<<grid, 512, sizeof(double) << 14, st>>>(jobs, units, n_units, counter);
   return cudaGetLastError();
 }
 

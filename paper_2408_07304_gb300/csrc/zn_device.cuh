@@ -376,31 +376,43 @@ __device__ __forceinline__ void gen_copy_half(u64* sm, int h, const u64* __restr
 
 // --------------------------------------------------------- encoder FFT (FP64)
 
-// Radix-2 decimation-in-time FFT of length n = N/2 on (re, im), input already
-// in bit-reversed order; stage with half-size h uses w = T[k N / h].  The
-// butterfly performs, in this order and each separately rounded:
+// Radix-2 decimation-in-time FFT of length 2^log_len on (re, im), input
+// already in bit-reversed order; the stage with half-size hh uses
+// w = T[k N / hh] (N = 2^log_n).  The butterfly performs, in this order and
+// each separately rounded:
 //   tr = c.re*w.re - c.im*w.im; ti = c.re*w.im + c.im*w.re;
 //   (a.re + tr, a.im + ti), (a.re - tr, a.im - ti).
-// `conj` selects conj(T) (the decoder's inverse transform).
-__device__ __forceinline__ void fft_dit(double* re, double* im, int log_n, const double* etw, bool conj) {
-  const int n = 1 << (log_n - 1), N = 1 << log_n;
+// For w = T[0] = 1 and w = T[N/2] = -i the products are exact and are
+// skipped (the results can differ from the full formula only in the sign of
+// a zero).  `conj` selects conj(T) (the decoder's inverse transform).
+__device__ __forceinline__ void fft_dit(double* re, double* im, int log_len, int log_n, const double* etw, bool conj) {
+  const int len = 1 << log_len, N = 1 << log_n;
   const double* twr = etw;
   const double* twi = etw + N;
-  for (int lh = 0; (1 << lh) < n; ++lh) {
-    const int h = 1 << lh;
-    for (int idx = threadIdx.x; idx < n / 2; idx += blockDim.x) {
-      const int k = idx & (h - 1);
+  for (int lh = 0; lh < log_len; ++lh) {
+    const int hh = 1 << lh;
+    for (int idx = threadIdx.x; idx < len / 2; idx += blockDim.x) {
+      const int k = idx & (hh - 1);
       const int p = ((idx >> lh) << (lh + 1)) + k;
-      const int ti_ = k * (N >> lh);
-      const double wr = __ldg(twr + ti_);
-      const double wi = conj ? -__ldg(twi + ti_) : __ldg(twi + ti_);
-      const double ar = re[p], ai = im[p], cr = re[p + h], ci = im[p + h];
-      const double tr = __dsub_rn(__dmul_rn(cr, wr), __dmul_rn(ci, wi));
-      const double tim = __dadd_rn(__dmul_rn(cr, wi), __dmul_rn(ci, wr));
+      const double ar = re[p], ai = im[p], cr = re[p + hh], ci = im[p + hh];
+      double tr, tim;
+      if (k == 0) {                  // w = 1
+        tr = cr;
+        tim = ci;
+      } else if (2 * k == hh) {      // w = -i (conj: +i)
+        tr = conj ? -ci : ci;
+        tim = conj ? cr : -cr;
+      } else {
+        const int ti_ = k * (N >> lh);
+        const double wr = __ldg(twr + ti_);
+        const double wi = conj ? -__ldg(twi + ti_) : __ldg(twi + ti_);
+        tr = __dsub_rn(__dmul_rn(cr, wr), __dmul_rn(ci, wi));
+        tim = __dadd_rn(__dmul_rn(cr, wi), __dmul_rn(ci, wr));
+      }
       re[p] = __dadd_rn(ar, tr);
       im[p] = __dadd_rn(ai, tim);
-      re[p + h] = __dsub_rn(ar, tr);
-      im[p + h] = __dsub_rn(ai, tim);
+      re[p + hh] = __dsub_rn(ar, tr);
+      im[p + hh] = __dsub_rn(ai, tim);
     }
     __syncthreads();
   }

@@ -122,17 +122,22 @@ __device__ __forceinline__ void encrypt_half_unit(const DevParams& P, const EncA
 
 // ------------------------------------------------------- one ring per launch
 
+// grid (L, B), or (B, L) when A.swap
 template <int LOGN, bool ZINC, int LOGPER>
 __global__ void __launch_bounds__(NttShape<LOGN, LOGPER>::T) k_encrypt(DevParams P, EncArgs A) {
   extern __shared__ u64 sm[];
-  encrypt_unit<LOGN, ZINC, LOGPER>(P, A, blockIdx.x, blockIdx.y, sm, threadIdx.x, true);
+  const int i = A.swap ? blockIdx.y : blockIdx.x;
+  const size_t b = A.swap ? blockIdx.x : blockIdx.y;
+  encrypt_unit<LOGN, ZINC, LOGPER>(P, A, i, b, sm, threadIdx.x, true);
 }
 
-// grid (2L, B); block x = 2i + h produces output half h of prime i
+// grid (2L, B), or (B, 2L) when A.swap; unit 2i + h produces output half h of prime i
 template <int LOGH, bool ZINC, int LOGPER>
 __global__ void __launch_bounds__(NttShape<LOGH, LOGPER>::T) k_encrypt_half(DevParams P, EncArgs A) {
   extern __shared__ u64 sm[];
-  encrypt_half_unit<LOGH, ZINC, LOGPER>(P, A, blockIdx.x >> 1, blockIdx.x & 1, blockIdx.y, sm, threadIdx.x);
+  const int u = A.swap ? blockIdx.y : blockIdx.x;
+  const size_t b = A.swap ? blockIdx.x : blockIdx.y;
+  encrypt_half_unit<LOGH, ZINC, LOGPER>(P, A, u >> 1, u & 1, b, sm, threadIdx.x);
 }
 
 template <int LOGN, bool ZINC, int LOGPER>
@@ -142,7 +147,8 @@ static cudaError_t enc_full(const DevParams& P, const EncArgs& A, uint32_t batch
   auto kern = k_encrypt<LOGN, ZINC, LOGPER>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<dim3(P.L, batch), S::T, smem, st>>>(P, A);
+  const dim3 grid = A.swap ? dim3(batch, P.L) : dim3(P.L, batch);
+  kern<<<grid, S::T, smem, st>>>(P, A);
   return cudaGetLastError();
 }
 
@@ -153,14 +159,18 @@ static cudaError_t enc_half(const DevParams& P, const EncArgs& A, uint32_t batch
   auto kern = k_encrypt_half<LOGH, ZINC, LOGPER>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<dim3(2 * P.L, batch), S::T, smem, st>>>(P, A);
+  const dim3 grid = A.swap ? dim3(batch, 2 * P.L) : dim3(2 * P.L, batch);
+  kern<<<grid, S::T, smem, st>>>(P, A);
   return cudaGetLastError();
 }
 
 // variant 0: 32 elements per thread; variant 1: 16 elements per thread (rings >= 2^12)
 template <bool ZINC>
-static cudaError_t enc_dispatch(const DevParams& P, const EncArgs& A, uint32_t batch, int variant, cudaStream_t st) {
-  const bool v1 = variant == 1;
+static cudaError_t enc_dispatch(const DevParams& P, const EncArgs& A_in, uint32_t batch, int variant,
+                                cudaStream_t st) {
+  const bool v1 = (variant & 1) != 0;
+  EncArgs A = A_in;
+  A.swap = (variant >> 1) & 1;
   switch (P.log_n) {
     case 4: return enc_full<4, ZINC, 5>(P, A, batch, st);
     case 5: return enc_full<5, ZINC, 5>(P, A, batch, st);

@@ -14,10 +14,10 @@ struct PrepArgs {
   unsigned domain;      // sampling domain (0 vanilla, 1 Zinc, 3 Zinc cache)
   i64* me;              // [B][N] encoded message plus its noise polynomial
   int8_t* small;        // [B][2][N] small polynomials (vanilla: u, e1; Zinc: e2')
-  double* work;         // FFT scratch for rings above 2^14: [B][N] doubles
 };
 
 struct EncArgs {
+  int swap;             // grid order: 0 = (prime, ciphertext), 1 = (ciphertext, prime)
   const u64* key;       // vanilla: pk [2][L][N]; Zinc: cache [2][L][N]
   const u64* keys;      // vanilla: pk Shoup companions [2][L][N]; Zinc: unused
   const i64* me;        // [B][N] from the prep kernel
@@ -26,7 +26,7 @@ struct EncArgs {
 };
 
 cudaError_t launch_encode(const DevParams& P, const double* slots, uint32_t n_slots, uint32_t batch, i64* out,
-                          double* work, cudaStream_t st);
+                          cudaStream_t st);
 cudaError_t launch_prep(const DevParams& P, const PrepArgs& A, bool zinc, uint32_t batch, cudaStream_t st);
 // Mixed-ring batches (persistent kernels): one descriptor per job (a ring,
 // a mode, a key or cache, buffers), a work list of encrypt packets and one of
@@ -34,7 +34,7 @@ cudaError_t launch_prep(const DevParams& P, const PrepArgs& A, bool zinc, uint32
 struct JobDesc {
   DevParams P;
   EncArgs E;      // me / small point into this job's scratch
-  PrepArgs Pr;    // idem; Pr.work unused (large rings use the per-block area)
+  PrepArgs Pr;    // idem
   int zinc;
   int pad;
 };
@@ -51,12 +51,14 @@ struct PrepUnit {
 };
 cudaError_t batch_set_attributes();
 cudaError_t batch_encrypt_attributes();
-cudaError_t launch_batch_prep(const JobDesc* jobs, const PrepUnit* units, int n_units, int* counter, double* work,
-                              int grid, cudaStream_t st);
+cudaError_t launch_batch_prep(const JobDesc* jobs, const PrepUnit* units, int n_units, int* counter, int grid,
+                              cudaStream_t st);
 cudaError_t launch_batch_encrypt(const JobDesc* jobs, const EncPacket* packets, int n_packets, int* counter, int grid,
                                  cudaStream_t st);
 
-// variant: 0 = 32 NTT elements per thread, 1 = 16 (selected by the autotuner)
+// variant bit 0: 16 (instead of 32) NTT elements per thread; bit 1: ciphertext-major
+// grid (all blocks of a wave share one prime's twiddles and keys).  Selected by
+// the autotuner.
 cudaError_t launch_encrypt(const DevParams& P, const EncArgs& A, bool zinc, uint32_t batch, int variant,
                            cudaStream_t st);
 cudaError_t launch_keygen(const DevParams& P, u64 seed, u64* sk_ntt, u64* pk, u64* pks, cudaStream_t st);
