@@ -166,6 +166,20 @@ int zinc_encrypt_noalloc(zn_ctx* ctx, const zn_zcache* zc, const double* slots, 
                          uint32_t batch, uint64_t seed, const uint64_t* ct_index, uint64_t* ct,
                          void* stream);
 
+/* Host memory in, host memory out: copies slot vectors and ct indices to the
+ * device, encrypts -- vanilla (Eq. 8) under pk when zc is NULL, Zinc
+ * (Algorithm 1) under zc otherwise (pass exactly one) -- and copies the
+ * ciphertexts back, in chunks of `chunk` ciphertexts (0: 256) pipelined over
+ * three internal streams so that the transfers of one chunk overlap the
+ * kernels of the next.  host_slots [batch][n_slots] double, host_ct_index
+ * [batch] uint64, host_ct [batch][2][L][N] uint64: page-locked host memory
+ * gives asynchronous full-speed copies (pageable memory works, slower).
+ * Results equal ckks_encrypt / zinc_encrypt.  Synchronous: returns when the
+ * ciphertexts are in host_ct.  Device staging comes from the context's pool. */
+int zn_encrypt_host(zn_ctx* ctx, const zn_pk* pk, const zn_zcache* zc, const double* host_slots,
+                    uint32_t n_slots, uint32_t batch, uint64_t seed, const uint64_t* host_ct_index,
+                    uint64_t* host_ct, uint32_t chunk);
+
 /* -------------------------------------------------------------- decrypt */
 
 /* Dec, paper Eq. 10: c0 + c1*s (mod each q_i), returned in the coefficient
@@ -239,12 +253,11 @@ int zn_batch_info(const zn_batch* b, uint32_t* prep_units, uint32_t* packets);
 
 /* -------------------------------------------------------------- autotuning */
 
-/* Launch shapes of the encryption kernels.  Bit 0 of the variant: each thread
- * owns 16 NTT elements (twice the threads) instead of 32 (rings of 2^12 and
- * above; smaller rings always use 32).  Bit 1: ciphertext-major grid (the
- * blocks of a wave share one prime's twiddles and keys) instead of
- * prime-major. */
-#define ZN_VARIANTS 4
+/* Launch shapes of the encryption kernels.  Variant 0: prime-major grid
+ * (the blocks of one ciphertext run together and share its prepared
+ * integers in L2); variant 1: ciphertext-major grid (the blocks of a wave
+ * share one prime's twiddles and keys). */
+#define ZN_VARIANTS 2
 int zn_set_variant(zn_ctx* ctx, int variant);
 int zn_get_variant(const zn_ctx* ctx);
 

@@ -69,6 +69,7 @@ _SIGS = {
     "zn_ntt_forward": (_i32, [_vp, _vp, _u32, _vp]),
     "zn_ntt_inverse": (_i32, [_vp, _vp, _u32, _vp]),
     "zn_sample": (_i32, [_vp, _i32, _u64, _u32, _u32, _u32, _u64, _u32, _vp, _vp]),
+    "zn_encrypt_host": (_i32, [_vp, _vp, _vp, _vp, _u32, _u32, _u64, _vp, _vp, _u32]),
     "zn_batch_create": (_i32, [_vp, _u32, _i32, _pp]),
     "zn_batch_destroy": (None, [_vp]),
     "zn_batch_run": (_i32, [_vp, _vp, _i32]),
@@ -331,6 +332,26 @@ def zinc_encrypt_noalloc(ctx, zc, slots, seed, ct_index, out, stream=None):
     return out
 
 
+def zn_encrypt_host(ctx, key, slots, seed, ct_index, out, chunk=0):
+    """Host-to-host encryption (pipelined copies + kernels).  key: PublicKey
+    (vanilla) or ZincCache (Zinc); slots: CPU float64 [B, n_slots]; ct_index:
+    CPU int64 [B]; out: CPU int64 [B, 2, L, N] (pinned tensors give
+    asynchronous copies).  Synchronous."""
+    import torch
+    B, ns = slots.shape
+    for t, dt, shape, nm in ((slots, torch.float64, None, "slots"), (ct_index, torch.int64, (B,), "ct_index"),
+                             (out, torch.int64, (B, 2, ctx.L, ctx.n), "out")):
+        if not isinstance(t, torch.Tensor) or t.is_cuda or t.dtype != dt or not t.is_contiguous():
+            raise TypeError(f"{nm}: expected a contiguous CPU tensor of {dt}")
+        if shape is not None and tuple(t.shape) != tuple(shape):
+            raise ValueError(f"{nm}: expected shape {shape}")
+    zinc = isinstance(key, ZincCache)
+    _check(lib().zn_encrypt_host(ctx.handle, None if zinc else key.handle, key.handle if zinc else None,
+                                 slots.data_ptr(), ns, B, seed, ct_index.data_ptr(), out.data_ptr(), chunk),
+           "zn_encrypt_host")
+    return out
+
+
 def ckks_decrypt(ctx, sk, ct, out=None, stream=None):
     """Dec (Eq. 10): int64 [B, 2, L, N] -> coefficient residues int64 [B, L, N]."""
     import torch
@@ -454,7 +475,7 @@ def zn_batch_run(batch, stream=None, graph=True):
     _check(lib().zn_batch_run(batch.handle, _stream(stream), 1 if graph else 0), "zn_batch_run")
 
 
-VARIANTS = 4
+VARIANTS = 2
 
 
 def zn_set_variant(ctx, variant):

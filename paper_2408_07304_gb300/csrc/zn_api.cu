@@ -30,6 +30,7 @@ struct zn_ctx {
   unsigned* d_status;
   cudaMemPool_t pool; // stream-ordered scratch (prep outputs)
   int variant;        // encryption launch shape (zn_autotune)
+  cudaStream_t hs[3]; // internal streams of zn_encrypt_host (created on first use)
   // launch timing (benchmark instrumentation)
   bool timing;
   std::vector<cudaEvent_t> ev[ZN_TIME_KINDS];   // start/stop pairs
@@ -324,6 +325,8 @@ void zn_ctx_destroy(zn_ctx* c) {
   if (!c) return;
   DeviceGuard g(c->device);
   zn_timing_enable(c, 0);
+  for (cudaStream_t& h : c->hs)
+    if (h) cudaStreamDestroy(h);
   cudaFree(c->d_tw);
   cudaFree(c->d_etw);
   cudaFree(c->d_slot);
@@ -863,6 +866,62 @@ int zn_batch_info(const zn_batch* b, uint32_t* prep_units, uint32_t* packets) {
   if (prep_units) *prep_units = b->n_prep;
   if (packets) *packets = b->n_packets;
   return ZN_OK;
+}
+
+// ------------------------------------------------------ host-buffer pipeline
+
+int zn_encrypt_host(zn_ctx* c, const zn_pk* pk, const zn_zcache* zc, const double* host_slots, uint32_t n_slots,
+                    uint32_t batch, uint64_t seed, const uint64_t* host_ct_index, uint64_t* host_ct,
+                    uint32_t chunk) {
+  if (!c || (pk && zc) || (!pk && !zc) || (pk && !pk_of(pk, c)) || (zc && !zc_of(zc, c)) || n_slots > c->n / 2)
+    return ZN_EINVAL;
+  if (batch == 0) return ZN_OK;
+  if (!host_ct || !host_ct_index || (n_slots && !host_slots)) return ZN_EINVAL;
+  if (chunk == 0) chunk = 256;
+  if (chunk > batch) chunk = batch;
+  DeviceGuard g(c->device);
+  for (cudaStream_t& h : c->hs)
+    if (!h && cudaStreamCreateWithFlags(&h, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      h = nullptr;
+      return ZN_ECUDA;
+    }
+  const size_t ct_b = sizeof(u64) * 2 * ring_words(c) * chunk;
+  const size_t sl_b = (sizeof(double) * n_slots * chunk + 255) / 256 * 256;
+  const size_t ix_b = (sizeof(u64) * chunk + 255) / 256 * 256;
+  const bool zinc = zc != nullptr;
+  int rc = ZN_OK;
+  {
+    Scratch st0(c, c->hs[0]), st1(c, c->hs[1]), st2(c, c->hs[2]);
+    Scratch* stage[3] = {&st0, &st1, &st2};
+    for (int k = 0; k < 3 && !rc; ++k)
+      if (!stage[k]->alloc(ct_b + sl_b + ix_b)) rc = ZN_ENOMEM;
+    for (uint32_t b0 = 0, k = 0; b0 < batch && !rc; b0 += chunk, k = (k + 1) % 3) {
+      const uint32_t nb = (batch - b0) < chunk ? (batch - b0) : chunk;
+      cudaStream_t st = c->hs[k];
+      char* base = (char*)stage[k]->p;
+      u64* d_ct = (u64*)base;
+      double* d_sl = (double*)(base + ct_b);
+      u64* d_ix = (u64*)(base + ct_b + sl_b);
+      if ((n_slots && cudaMemcpyAsync(d_sl, host_slots + (size_t)b0 * n_slots, sizeof(double) * n_slots * nb,
+                                      cudaMemcpyHostToDevice, st) != cudaSuccess) ||
+          cudaMemcpyAsync(d_ix, host_ct_index + b0, sizeof(u64) * nb, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        rc = ZN_ECUDA;
+        break;
+      }
+      rc = zinc ? encrypt_common(c, true, zc->d, nullptr, d_sl, n_slots, nb, seed, d_ix, d_ct, st)
+                : encrypt_common(c, false, pk->d, pk->d + 2 * ring_words(c), d_sl, n_slots, nb, seed, d_ix, d_ct,
+                                 st);
+      if (!rc && cudaMemcpyAsync(host_ct + (size_t)b0 * 2 * ring_words(c), d_ct,
+                                 sizeof(u64) * 2 * ring_words(c) * nb, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        rc = ZN_ECUDA;
+    }
+    // staging is returned to the pool in stream order by the Scratch destructors
+  }
+  for (cudaStream_t h : c->hs)
+    if (cudaStreamSynchronize(h) != cudaSuccess) rc = rc ? rc : ZN_ECUDA;
+  cudaGetLastError();
+  return rc;
 }
 
 // ------------------------------------------------------------- autotuning

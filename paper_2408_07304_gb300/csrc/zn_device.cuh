@@ -88,6 +88,28 @@ __device__ __forceinline__ void ct_bfly(u64& x, u64& y, u64 w, u64 wp, u64 q) {
 }
 __device__ __forceinline__ void ct_bfly(u64& x, u64& y, ulonglong2 w, u64 q) { ct_bfly(x, y, w.x, w.y, q); }
 
+// Relaxed forward butterfly for q < 2^59: no correction step.  If both
+// inputs are below B, both outputs are below B + 2q; a transform starting
+// from [0, 4q) stays below 4q + 14 * 2q = 32q < 2^64 over 14 stages.
+constexpr u64 kRelaxLimit = 1ull << 59;
+__device__ __forceinline__ void ct_bfly_relaxed(u64& x, u64& y, ulonglong2 w, u64 q) {
+  const u64 t = mul_shoup(y, w.x, w.y, q);   // [0, 2q)
+  const u64 a = x;
+  x = a + t;
+  y = a - t + 2 * q;
+}
+
+// Output of a transform -> [0, q): Harvey range [0, 4q), relaxed range [0, 32q).
+template <bool RELAX>
+__device__ __forceinline__ u64 reduce_out(u64 x, u64 q) {
+  if constexpr (RELAX) {
+    if (x >= 16 * q) x -= 16 * q;
+    if (x >= 8 * q) x -= 8 * q;
+    if (x >= 4 * q) x -= 4 * q;
+  }
+  return reduce4(x, q);
+}
+
 // ------------------------------------------------------------------ Philox
 
 __device__ __forceinline__ uint4 philox10(uint4 c, uint2 k) {
@@ -170,7 +192,7 @@ __host__ __device__ constexpr int swz(int i) {
 // pass (LO == 0), hands every output to store(idx, x).  The twiddle of stage
 // bit b for index idx is tw[tmul * 2^(LOGN-1-b) + (idx >> (b+1))]; tmul = 1
 // for a full transform, 2 + h for half h of a transform of twice the size.
-template <int LOGN, int LOGPER, int LO, int K, class Store>
+template <int LOGN, int LOGPER, int LO, int K, bool RELAX, class Store>
 __device__ __forceinline__ void ntt_pass(u64* sm, int t, const ulonglong2* __restrict__ twp, int tmul, u64 q,
                                          Store& store) {
   using S = NttShape<LOGN, LOGPER>;
@@ -190,12 +212,13 @@ __device__ __forceinline__ void ntt_pass(u64* sm, int t, const ulonglong2* __res
 #pragma unroll
       for (int r = 0; r < (1 << K); ++r) {
         if (r & (1 << s)) continue;
-        ct_bfly(v[r], v[r + (1 << s)], __ldg(tws + (r >> (s + 1))), q);
+        if constexpr (RELAX) ct_bfly_relaxed(v[r], v[r + (1 << s)], __ldg(tws + (r >> (s + 1))), q);
+        else ct_bfly(v[r], v[r + (1 << s)], __ldg(tws + (r >> (s + 1))), q);
       }
     }
     if constexpr (LO == 0) {
 #pragma unroll
-      for (int r = 0; r < (1 << K); ++r) store(base | r, v[r]);
+      for (int r = 0; r < (1 << K); ++r) store(base | r, reduce_out<RELAX>(v[r], q));
     } else {
 #pragma unroll
       for (int r = 0; r < (1 << K); ++r) sm[sb ^ swz<LOGN>(r << LO)] = v[r];
@@ -203,33 +226,34 @@ __device__ __forceinline__ void ntt_pass(u64* sm, int t, const ulonglong2* __res
   }
 }
 
-template <int LOGN, int LOGPER, int HI, class Store>
+template <int LOGN, int LOGPER, int HI, bool RELAX, class Store>
 __device__ __forceinline__ void ntt_chain(u64* sm, int t, const ulonglong2* twp, int tmul, u64 q, Store& store) {
   constexpr int K = HI < NttShape<LOGN>::KMAX ? HI : NttShape<LOGN>::KMAX;
   constexpr int LO = HI - K;
   __syncthreads();
-  ntt_pass<LOGN, LOGPER, LO, K, Store>(sm, t, twp, tmul, q, store);
-  if constexpr (LO > 0) ntt_chain<LOGN, LOGPER, LO, Store>(sm, t, twp, tmul, q, store);
+  ntt_pass<LOGN, LOGPER, LO, K, RELAX, Store>(sm, t, twp, tmul, q, store);
+  if constexpr (LO > 0) ntt_chain<LOGN, LOGPER, LO, RELAX, Store>(sm, t, twp, tmul, q, store);
 }
 
 // Forward negacyclic NTT of one length-2^LOGN polynomial by the block's
 // 2^LOGT threads.  On entry sm[swz(k)] holds coefficient k in [0, 4q) (written
 // by one of the generators below; the call begins with a barrier).  store(idx,
-// x) is called once per output index with x in [0, 4q) congruent to ahat[idx].
-// The shared buffer may be reused after a barrier.
-template <int LOGN, class Store, int LOGPER = 5>
+// x) is called once per output index with x in [0, q), x = ahat[idx].
+// RELAX (only for q < 2^59) drops the butterflies' correction steps.  The
+// shared buffer may be reused after a barrier.
+template <int LOGN, class Store, int LOGPER = 5, bool RELAX = false>
 __device__ __forceinline__ void ntt_forward(u64* sm, const ulonglong2* twp, int tmul, u64 q, Store& store) {
-  ntt_chain<LOGN, LOGPER, LOGN, Store>(sm, threadIdx.x, twp, tmul, q, store);
+  ntt_chain<LOGN, LOGPER, LOGN, RELAX, Store>(sm, threadIdx.x, twp, tmul, q, store);
 }
 
 // The same transform run by a sub-group of the block: thread t of the 2^LOGT
 // threads that own this polynomial (several sub-groups may share one block;
 // all of them must execute the same sequence of transforms, because the
 // passes are separated by block-wide barriers).
-template <int LOGN, class Store, int LOGPER = 5>
+template <int LOGN, class Store, int LOGPER = 5, bool RELAX = false>
 __device__ __forceinline__ void ntt_forward_sub(u64* sm, int t, const ulonglong2* twp, int tmul, u64 q,
                                                 Store& store) {
-  ntt_chain<LOGN, LOGPER, LOGN, Store>(sm, t, twp, tmul, q, store);
+  ntt_chain<LOGN, LOGPER, LOGN, RELAX, Store>(sm, t, twp, tmul, q, store);
 }
 
 // ------------------------------------------------------------- generators

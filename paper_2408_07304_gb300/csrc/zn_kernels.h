@@ -56,9 +56,8 @@ cudaError_t launch_batch_prep(const JobDesc* jobs, const PrepUnit* units, int n_
 cudaError_t launch_batch_encrypt(const JobDesc* jobs, const EncPacket* packets, int n_packets, int* counter, int grid,
                                  cudaStream_t st);
 
-// variant bit 0: 16 (instead of 32) NTT elements per thread; bit 1: ciphertext-major
-// grid (all blocks of a wave share one prime's twiddles and keys).  Selected by
-// the autotuner.
+// variant: 0 = prime-major grid, 1 = ciphertext-major grid (all blocks of a wave
+// share one prime's twiddles and keys).  Selected by the autotuner.
 cudaError_t launch_encrypt(const DevParams& P, const EncArgs& A, bool zinc, uint32_t batch, int variant,
                            cudaStream_t st);
 cudaError_t launch_keygen(const DevParams& P, u64 seed, u64* sk_ntt, u64* pk, u64* pks, cudaStream_t st);

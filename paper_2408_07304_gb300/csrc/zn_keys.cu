@@ -25,12 +25,12 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T) k_keygen(DevParams P, KeyAr
   u64* p0s = A.pks + (size_t)i * S::N;
   u64* p1s = p0s + (size_t)L * S::N;
   gen_ternary<LOGN>(sm, A.seed, rand_tag(2, 0, 0), 0, q);
-  auto st_s = [&](int idx, u64 x) { sh[idx] = reduce4(x, q); };
+  auto st_s = [&](int idx, u64 x) { sh[idx] = x; };
   ntt_forward<LOGN>(sm, tw, 1, q, st_s);
   __syncthreads();
   gen_uniform<LOGN>(sm, A.seed, rand_tag(2, 1, (unsigned)i), 0, q);
   auto st_a = [&](int idx, u64 x) {
-    const u64 a = reduce4(x, q);
+    const u64 a = x;
     p1[idx] = a;
     p1s[idx] = shoup_of(a, q);
   };
@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T) k_keygen(DevParams P, KeyAr
   __syncthreads();
   gen_gauss<LOGN>(sm, A.seed, rand_tag(2, 2, 0), 0, P.cdt, nullptr, q, P.mu[i]);
   auto st_e = [&](int idx, u64 x) {
-    const u64 e = reduce4(x, q);
+    const u64 e = x;
     const u64 as = mulmod_slow(p1[idx], sh[idx], q);
     const u64 pk0 = e >= as ? e - as : e + q - as;
     p0[idx] = pk0;
@@ -64,12 +64,12 @@ __global__ void __launch_bounds__(NttShape<LOGH>::T) k_keygen_half(DevParams P, 
   u64* p1s = p0s + (size_t)L * N;
   const int tmul = 2 + h;
   gen_ternary_half<LOGH>(sm, h, A.seed, rand_tag(2, 0, 0), 0, q, w1, w1s);
-  auto st_s = [&](int idx, u64 x) { sh[idx] = reduce4(x, q); };
+  auto st_s = [&](int idx, u64 x) { sh[idx] = x; };
   ntt_forward<LOGH>(sm, tw, tmul, q, st_s);
   __syncthreads();
   gen_uniform_half<LOGH>(sm, h, A.seed, rand_tag(2, 1, (unsigned)i), 0, q, w1, w1s);
   auto st_a = [&](int idx, u64 x) {
-    const u64 a = reduce4(x, q);
+    const u64 a = x;
     p1[idx] = a;
     p1s[idx] = shoup_of(a, q);
   };
@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(NttShape<LOGH>::T) k_keygen_half(DevParams P, 
   __syncthreads();
   gen_gauss_half<LOGH>(sm, h, A.seed, rand_tag(2, 2, 0), 0, P.cdt, nullptr, q, P.mu[i], w1, w1s);
   auto st_e = [&](int idx, u64 x) {
-    const u64 e = reduce4(x, q);
+    const u64 e = x;
     const u64 as = mulmod_slow(p1[idx], sh[idx], q);
     const u64 pk0 = e >= as ? e - as : e + q - as;
     p0[idx] = pk0;
@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T) k_ntt_fwd(DevParams P, cons
   const size_t off = ((size_t)blockIdx.y * P.L + i) * S::N;
   gen_copy<LOGN>(sm, src + off);
   u64* o = dst + off;
-  auto st = [&](int idx, u64 x) { o[idx] = reduce4(x, q); };
+  auto st = [&](int idx, u64 x) { o[idx] = x; };
   ntt_forward<LOGN>(sm, P.twp + (size_t)i * S::N, 1, q, st);
 }
 
@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(NttShape<LOGH>::T) k_ntt_fwd_half(DevParams P,
   const size_t off = ((size_t)blockIdx.y * P.L + i) * N;
   gen_copy_half<LOGH>(sm, h, src + off, q, w1p.x, w1p.y);
   u64* o = dst + off + (size_t)h * HALF;
-  auto st = [&](int idx, u64 x) { o[idx] = reduce4(x, q); };
+  auto st = [&](int idx, u64 x) { o[idx] = x; };
   ntt_forward<LOGH>(sm, tw, 2 + h, q, st);
 }
 

@@ -101,3 +101,21 @@ def test_batch_rejects_bad_jobs():
     with pytest.raises(api.ZincError):
         api.zn_batch_create([{"ctx": tiny, "zinc": False, "key": tpk, "slots": z, "seed": 0, "ct_index": idx,
                               "out": torch.empty((1, 2, 1, 512), dtype=torch.int64, device="cuda:0")}])
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_pipeline_matches_device_api(pinned):
+    """zn_encrypt_host (host buffers, chunked copy/compute overlap) gives the
+    device entry points' ciphertexts, with a ragged last chunk."""
+    ctx, _, pk, zc = ring(13, (60, 40, 40, 60), 40)
+    B, ns = 37, 1500
+    w = workloads.small(13, (60, 40, 40, 60), 40, B, ns, seed=77)
+    z = torch.tensor(workloads.slots(w), dtype=torch.float64)
+    idx = torch.arange(B, dtype=torch.int64) * 5 + 3
+    if pinned:
+        z, idx = z.pin_memory(), idx.pin_memory()
+    for key, fn in ((pk, api.ckks_encrypt), (zc, api.zinc_encrypt)):
+        out = torch.empty((B, 2, ctx.L, ctx.n), dtype=torch.int64, pin_memory=pinned)
+        api.zn_encrypt_host(ctx, key, z, 4, idx, out, chunk=8)
+        ref = fn(ctx, key, z.cuda(), 4, idx.cuda()).cpu()
+        assert torch.equal(out, ref)
