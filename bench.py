@@ -174,7 +174,11 @@ def run_ours(args, w):
     out_v = torch.empty((B, 2, w.L, w.n), dtype=torch.int64, device=dev)
     out_z = torch.empty_like(out_v)
     stream = torch.cuda.current_stream(dev)
-    tune = api.zn_autotune(ctx, pk, zc, min(B, 512))
+    if args.variant is None:
+        tune = api.zn_autotune(ctx, pk, zc, min(B, 512))
+    else:
+        api.zn_set_variant(ctx, args.variant)
+        tune = (args.variant, None)
 
     def step():
         api.ckks_encrypt(ctx, pk, slots, w.seed, idx, out=out_v, stream=stream)
@@ -350,6 +354,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="throughput", choices=sorted(workloads.WORKLOADS))
     ap.add_argument("--batch", type=int, default=None, help="override the workload's batch (profiling runs)")
+    ap.add_argument("--variant", type=int, default=None, help="fixed encryption launch shape instead of autotuning")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving (p50/p99) run")

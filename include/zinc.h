@@ -253,11 +253,20 @@ int zn_batch_info(const zn_batch* b, uint32_t* prep_units, uint32_t* packets);
 
 /* -------------------------------------------------------------- autotuning */
 
-/* Launch shapes of the encryption kernels.  Variant 0: prime-major grid
- * (the blocks of one ciphertext run together and share its prepared
- * integers in L2); variant 1: ciphertext-major grid (the blocks of a wave
- * share one prime's twiddles and keys). */
-#define ZN_VARIANTS 2
+/* Launch shapes of the encryption kernels: variant = 2 * kind + order.
+ * order 0 = prime-major grid (the blocks of one ciphertext run together and
+ * share its prepared integers in L2), 1 = ciphertext-major grid (the blocks
+ * of a wave share one prime's twiddles and keys).  kind 0 = one block per
+ * limb that transforms the polynomials one after another; kind 1 = one block
+ * per limb (per output half for N = 2^14) holding all of the limb's
+ * polynomials at once, sharing each twiddle load between them and writing
+ * each ciphertext word once (2^10 <= N <= 2^14 with 16-byte aligned key and
+ * output pointers); kind 2 = kind 0 capped at 128 registers per thread so
+ * that several blocks share an SM, N = 2^14 split into output halves
+ * (2^10 <= N <= 2^14); kind 3 = kind 2 with radix-8 passes capped at 80
+ * registers (three blocks of 256 threads per SM).  Where a kind does not
+ * apply, kind 0 runs. */
+#define ZN_VARIANTS 8
 int zn_set_variant(zn_ctx* ctx, int variant);
 int zn_get_variant(const zn_ctx* ctx);
 

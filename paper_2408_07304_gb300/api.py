@@ -475,7 +475,7 @@ def zn_batch_run(batch, stream=None, graph=True):
     _check(lib().zn_batch_run(batch.handle, _stream(stream), 1 if graph else 0), "zn_batch_run")
 
 
-VARIANTS = 2
+VARIANTS = 8
 
 
 def zn_set_variant(ctx, variant):

@@ -168,7 +168,7 @@ struct NttShape {
   static constexpr int LOGT = LOGN >= LOGPER ? LOGN - LOGPER : 0;
   static constexpr int T = 1 << LOGT;                 // threads per transform
   static constexpr int PER = N / T;                   // elements per thread
-  static constexpr int KMAX = 4;                      // butterfly stages per register pass
+  static constexpr int KMAX = 4;                      // default butterfly stages per register pass
   // shared-memory swizzle i ^ ((i >> SA) & 15) ^ ((i >> SB) & 15): a bijection that
   // keeps every phase's 64-bit accesses (and the generators' consecutive
   // writes) free of bank conflicts; parameters found by exhaustive check per N
@@ -226,13 +226,14 @@ __device__ __forceinline__ void ntt_pass(u64* sm, int t, const ulonglong2* __res
   }
 }
 
-template <int LOGN, int LOGPER, int HI, bool RELAX, class Store>
+// Passes of KM bits (radix 2^KM) from the top index bit down.
+template <int LOGN, int LOGPER, int HI, bool RELAX, class Store, int KM = NttShape<LOGN>::KMAX>
 __device__ __forceinline__ void ntt_chain(u64* sm, int t, const ulonglong2* twp, int tmul, u64 q, Store& store) {
-  constexpr int K = HI < NttShape<LOGN>::KMAX ? HI : NttShape<LOGN>::KMAX;
+  constexpr int K = HI < KM ? HI : KM;
   constexpr int LO = HI - K;
   __syncthreads();
   ntt_pass<LOGN, LOGPER, LO, K, RELAX, Store>(sm, t, twp, tmul, q, store);
-  if constexpr (LO > 0) ntt_chain<LOGN, LOGPER, LO, RELAX, Store>(sm, t, twp, tmul, q, store);
+  if constexpr (LO > 0) ntt_chain<LOGN, LOGPER, LO, RELAX, Store, KM>(sm, t, twp, tmul, q, store);
 }
 
 // Forward negacyclic NTT of one length-2^LOGN polynomial by the block's
@@ -250,10 +251,10 @@ __device__ __forceinline__ void ntt_forward(u64* sm, const ulonglong2* twp, int 
 // threads that own this polynomial (several sub-groups may share one block;
 // all of them must execute the same sequence of transforms, because the
 // passes are separated by block-wide barriers).
-template <int LOGN, class Store, int LOGPER = 5, bool RELAX = false>
+template <int LOGN, class Store, int LOGPER = 5, bool RELAX = false, int KM = NttShape<LOGN>::KMAX>
 __device__ __forceinline__ void ntt_forward_sub(u64* sm, int t, const ulonglong2* twp, int tmul, u64 q,
                                                 Store& store) {
-  ntt_chain<LOGN, LOGPER, LOGN, RELAX, Store>(sm, t, twp, tmul, q, store);
+  ntt_chain<LOGN, LOGPER, LOGN, RELAX, Store, KM>(sm, t, twp, tmul, q, store);
 }
 
 // ------------------------------------------------------------- generators

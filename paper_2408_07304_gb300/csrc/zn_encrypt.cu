@@ -1,60 +1,29 @@
-// Hot path, one ring per launch: k_encrypt (N <= 2^14, one block per prime
-// and ciphertext) and k_encrypt_half (N = 2^15, two blocks per prime and
-// ciphertext).  The unit code lives in zn_encrypt_unit.cuh.
-#include "zn_encrypt_unit.cuh"
+// Hot path, one ring per launch, and the launch-shape dispatch.  Kind 0 (this
+// file): k_encrypt (N <= 2^14, one block per prime and ciphertext) and
+// k_encrypt_half (N = 2^15, two blocks per prime and ciphertext).  Kind 1:
+// the multi-polynomial kernel (zn_encrypt_mp.cu).  Kinds 2 and 3:
+// register-capped shapes with two or three resident blocks per SM
+// (zn_encrypt_occ.cu, zn_encrypt_occ3.cu).
+#include "zn_encrypt_kern.cuh"
 
 namespace zn {
 
 // ------------------------------------------------------- one ring per launch
 
-// grid (L, B), or (B, L) when A.swap
-template <int LOGN, bool ZINC, int LOGPER>
-__global__ void __launch_bounds__(NttShape<LOGN, LOGPER>::T) k_encrypt(DevParams P, EncArgs A) {
-  extern __shared__ u64 sm[];
-  const int i = A.swap ? blockIdx.y : blockIdx.x;
-  const size_t b = A.swap ? blockIdx.x : blockIdx.y;
-  encrypt_unit<LOGN, ZINC, LOGPER>(P, A, i, b, sm, threadIdx.x, true);
-}
-
-// grid (2L, B), or (B, 2L) when A.swap; unit 2i + h produces output half h of prime i
-template <int LOGH, bool ZINC, int LOGPER>
-__global__ void __launch_bounds__(NttShape<LOGH, LOGPER>::T) k_encrypt_half(DevParams P, EncArgs A) {
-  extern __shared__ u64 sm[];
-  const int u = A.swap ? blockIdx.y : blockIdx.x;
-  const size_t b = A.swap ? blockIdx.x : blockIdx.y;
-  encrypt_half_unit<LOGH, ZINC, LOGPER>(P, A, u >> 1, u & 1, b, sm, threadIdx.x);
-}
-
-template <int LOGN, bool ZINC, int LOGPER>
-static cudaError_t enc_full(const DevParams& P, const EncArgs& A, uint32_t batch, cudaStream_t st) {
-  using S = NttShape<LOGN, LOGPER>;
-  const size_t smem = sizeof(u64) * S::N;
-  auto kern = k_encrypt<LOGN, ZINC, LOGPER>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  const dim3 grid = A.swap ? dim3(batch, P.L) : dim3(P.L, batch);
-  kern<<<grid, S::T, smem, st>>>(P, A);
-  return cudaGetLastError();
-}
-
-template <int LOGH, bool ZINC, int LOGPER>
-static cudaError_t enc_half(const DevParams& P, const EncArgs& A, uint32_t batch, cudaStream_t st) {
-  using S = NttShape<LOGH, LOGPER>;
-  const size_t smem = sizeof(u64) * S::N;
-  auto kern = k_encrypt_half<LOGH, ZINC, LOGPER>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  const dim3 grid = A.swap ? dim3(batch, 2 * P.L) : dim3(2 * P.L, batch);
-  kern<<<grid, S::T, smem, st>>>(P, A);
-  return cudaGetLastError();
-}
-
-// variant: grid order (0 prime-major, 1 ciphertext-major)
+// variant = 2 * kind + order; order 0 prime-major, 1 ciphertext-major.  Kind
+// 1 applies for 2^10 <= N <= 2^14 with 16-byte aligned key, companion and
+// output pointers, kinds 2 and 3 for 2^10 <= N <= 2^14; otherwise kind 0 runs.
 template <bool ZINC>
 static cudaError_t enc_dispatch(const DevParams& P, const EncArgs& A_in, uint32_t batch, int variant,
                                 cudaStream_t st) {
   EncArgs A = A_in;
   A.swap = variant & 1;
+  const int kind = variant >> 1;
+  if (kind == 1 && P.log_n >= 10 && P.log_n <= 14 && aligned16(A.key) && aligned16(A.out) &&
+      (ZINC || aligned16(A.keys)))
+    return launch_encrypt_mp(P, A, ZINC, batch, st);
+  if (kind == 2 && P.log_n >= 10 && P.log_n <= 14) return launch_encrypt_occ(P, A, ZINC, batch, st);
+  if (kind == 3 && P.log_n >= 10 && P.log_n <= 14) return launch_encrypt_occ3(P, A, ZINC, batch, st);
   switch (P.log_n) {
     case 4: return enc_full<4, ZINC, 5>(P, A, batch, st);
     case 5: return enc_full<5, ZINC, 5>(P, A, batch, st);

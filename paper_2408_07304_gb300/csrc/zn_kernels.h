@@ -56,10 +56,20 @@ cudaError_t launch_batch_prep(const JobDesc* jobs, const PrepUnit* units, int n_
 cudaError_t launch_batch_encrypt(const JobDesc* jobs, const EncPacket* packets, int n_packets, int* counter, int grid,
                                  cudaStream_t st);
 
-// variant: 0 = prime-major grid, 1 = ciphertext-major grid (all blocks of a wave
-// share one prime's twiddles and keys).  Selected by the autotuner.
+// variant = 2 * kind + order.  order 0 = prime-major grid, 1 =
+// ciphertext-major grid (all blocks of a wave share one prime's twiddles and
+// keys); kind 0 = per-polynomial kernel, 1 = multi-polynomial kernel, 2 and
+// 3 = register-capped per-polynomial kernels with two or three resident
+// blocks per SM (kinds 1-3 where they apply).
+// Selected by the autotuner.
 cudaError_t launch_encrypt(const DevParams& P, const EncArgs& A, bool zinc, uint32_t batch, int variant,
                            cudaStream_t st);
+// Multi-polynomial kernel (2^10 <= N <= 2^14; key, companion and output
+// pointers 16-byte aligned; grid order from A.swap).
+cudaError_t launch_encrypt_mp(const DevParams& P, const EncArgs& A, bool zinc, uint32_t batch, cudaStream_t st);
+// Register-capped per-polynomial kernels (2^10 <= N <= 2^14).
+cudaError_t launch_encrypt_occ(const DevParams& P, const EncArgs& A, bool zinc, uint32_t batch, cudaStream_t st);
+cudaError_t launch_encrypt_occ3(const DevParams& P, const EncArgs& A, bool zinc, uint32_t batch, cudaStream_t st);
 cudaError_t launch_keygen(const DevParams& P, u64 seed, u64* sk_ntt, u64* pk, u64* pks, cudaStream_t st);
 cudaError_t launch_ntt_fwd(const DevParams& P, u64* data, uint32_t batch, u64* tmp, cudaStream_t st);
 cudaError_t launch_ntt_inv(const DevParams& P, u64* data, uint32_t batch, cudaStream_t st);

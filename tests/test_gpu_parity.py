@@ -311,8 +311,8 @@ def test_invalid_arguments():
                      torch.empty((0,), dtype=torch.int64, device="cuda:0"), out=out)
 
 
-@pytest.mark.parametrize("log_n,bits,ld", [(12, (36, 36, 36), 30), (13, (60, 40), 40), (14, (60, 50, 60), 50),
-                                           (15, (55, 60), 55)])
+@pytest.mark.parametrize("log_n,bits,ld", [(10, (40, 60), 30), (11, (50,), 40), (12, (36, 36, 36), 30),
+                                           (13, (60, 40), 40), (14, (60, 50, 60), 50), (15, (55, 60), 55)])
 def test_launch_variants_bit_identical(log_n, bits, ld):
     """Every launch shape the autotuner may choose gives the same ciphertexts."""
     ctx = gpu_ctx(log_n, bits, ld)
@@ -332,3 +332,29 @@ def test_launch_variants_bit_identical(log_n, bits, ld):
     assert chosen in range(api.VARIANTS) and all(m > 0 for m in ms)
     assert api.zn_get_variant(ctx) == chosen
     api.zn_set_variant(ctx, 0)
+
+
+@pytest.mark.parametrize("zinc", [False, True])
+def test_multipoly_variant_misaligned_output(zinc):
+    """The multi-polynomial kernel needs 16-byte aligned output rows; an output
+    that starts 8 bytes off takes the per-polynomial kernel, same ciphertexts."""
+    log_n, bits, ld = 13, (60, 40), 40
+    ctx = gpu_ctx(log_n, bits, ld)
+    _, pk = gpu_keys(log_n, bits, ld, 1)
+    zc = gpu_cache(log_n, bits, ld, 1, 2)
+    key = zc if zinc else pk
+    fn = api.zinc_encrypt if zinc else api.ckks_encrypt
+    w = workloads.small(log_n, bits, ld, 2, 100, seed=9)
+    z = dev(workloads.slots(w), torch.float64)
+    idx = dev(np.array([1, 7]), torch.int64)
+    shape = (2, 2, len(bits), 1 << log_n)
+    api.zn_set_variant(ctx, 0)
+    ref = fn(ctx, key, z, 3, idx)
+    api.zn_set_variant(ctx, 2)                          # kind 1, prime-major
+    aligned = fn(ctx, key, z, 3, idx)
+    flat = torch.empty(int(np.prod(shape)) + 1, dtype=torch.int64, device="cuda:0")
+    off = flat[1:].view(shape)
+    assert off.data_ptr() % 16 == 8
+    fn(ctx, key, z, 3, idx, out=off)
+    api.zn_set_variant(ctx, 0)
+    assert torch.equal(aligned, ref) and torch.equal(off, ref)
