@@ -108,9 +108,15 @@ int zn_sk_import(zn_ctx* ctx, const int8_t* host_in, zn_sk** out);
 /* CKKS encoding (canonical embedding; the paper assumes a pre-encoded message,
  * Section "Construction").  slots: device double [batch][n_slots] (real
  * slots; slots n_slots..N/2-1 are zero); out: device int64 [batch][N],
- * m_k = rint(2^(log2_delta+1-log_n) * Re sum_j z_j zeta^(-5^j k)), computed by
- * a radix-2 FP64 FFT with a fixed IEEE operation order (bit-reproducible).
- * n_slots <= N/2.  Overflow (|m_k| >= 2^62) is latched for zn_sync_status. */
+ * m_k ~ 2^(log2_delta+1-log_n) * Re sum_j z_j zeta^(-5^j k), computed by a
+ * block-scaled fixed-point FFT on 64-bit integers: each vector is scaled by
+ * 2^F, F = 60 - log_n - e with 2^(e-1) <= max|z_j| < 2^e (so zero padding
+ * changes nothing); Q62
+ * twiddles; every complex product exact in 128 bits and rounded once
+ * (floor(x + 1/2)); bit-reproducible, with an error below
+ * 2^(s-F-1) (3.4 N/2 + 2) + 1/2 per coefficient (s = log2_delta + 1 - log_n).
+ * n_slots <= N/2.  Overflow (|m_k| >= 2^62, or a non-finite slot) is latched
+ * for zn_sync_status and the vector's coefficients are set to zero. */
 int ckks_encode(zn_ctx* ctx, const double* slots, uint32_t n_slots, uint32_t batch,
                 int64_t* out, void* stream);
 
@@ -213,6 +219,12 @@ int zn_ntt_inverse(zn_ctx* ctx, uint64_t* data, uint32_t batch, void* stream);
 int zn_sample(zn_ctx* ctx, int kind, uint64_t seed, uint32_t domain, uint32_t poly,
               uint32_t prime, uint64_t ct_index0, uint32_t count, int64_t* out, void* stream);
 
+/* chi's table step alone (no counterpart in the paper; a check of threshold
+ * boundaries): out[i] = -19 + #{j : u[i] >= T_j} for device uint64 u[n],
+ * device int32 out[n], computed by the binary search over the 38 thresholds
+ * that the encryption path uses. */
+int zn_chi_eval(zn_ctx* ctx, const uint64_t* u, uint32_t n, int32_t* out, void* stream);
+
 /* ------------------------------------------------ mixed-ring batched launch */
 
 /* One job of a batch: `count` encryptions under one parameter set and mode.
@@ -304,8 +316,12 @@ int zn_probe_butterfly(int device, double* butterflies_per_s);
  * checked without a GPU. */
 int zn_host_primes(uint32_t log_n, const uint32_t* bits, uint32_t n_primes, uint64_t* out);
 uint64_t zn_host_psi(uint64_t q, uint32_t log_n);
-/* T[k] = cos(pi k/N) - i sin(pi k/N), k < N, each part correctly rounded. */
+/* T[k] = cos(pi k/N) - i sin(pi k/N), k < N, each part correctly rounded
+ * (the decoder's FP64 twiddles). */
 int zn_host_encoder_twiddles(uint32_t log_n, double* re, double* im);
+/* The encoder's Q62 twiddles: c[k] = floor(2^62 cos(pi k/N) + 1/2),
+ * s[k] = floor(2^62 sin(pi k/N) + 1/2), k < N (host int64 arrays of N). */
+int zn_host_encoder_twiddles_q62(uint32_t log_n, int64_t* c, int64_t* s);
 /* The 38 chi thresholds T_j = floor(2^64 F(j - 20)), j = 1..38. */
 int zn_host_cdt(uint64_t* out);
 

@@ -6,7 +6,7 @@ Implementation").  Definition used (standard CKKS): for real slots z_j,
 j < n = N/2 (missing slots are zero), the plaintext polynomial m in
 Z[X]/(X^N + 1) has coefficients
 
-    m_k = rint( (2 Delta / N) * Re sum_j z_j * zeta^(-5^j k) ),   zeta = exp(i pi / N),
+    m_k = round( (2 Delta / N) * Re sum_j z_j * zeta^(-5^j k) ),   zeta = exp(i pi / N),
 
 i.e. m(zeta^(5^j)) ~ Delta z_j.  With t_j = (5^j mod 2N - 1)/4 (a bijection of
 [0, n)) the sum S_k = sum_j z_j zeta^(-5^j k), k < n, equals
@@ -14,31 +14,43 @@ zeta^(-k) * DFT_n(y)_k with y_{t_j} = z_j, and m_k = scale Re S_k,
 m_{k+n} = scale Im S_k (because zeta^(-5^j n) = -i).
 
 Two forms:
-* ``encode_direct``: the defining sum, evaluated term by term (pin only).
-* ``encode``: the FP64 procedure whose every IEEE operation is specified, so
-  that an independent implementation can reproduce the integers bit for bit.
-  y is real, so its length-n DFT is taken through a complex DFT of half the
-  length (the standard real-input split):
-    1. y[t_j] = z_j (other entries 0); g_s = y[2s] + i y[2s+1], s < h = n/2;
+* ``encode_direct``: the defining sum, evaluated term by term in FP64 (pin only).
+* ``encode``: a block-scaled fixed-point procedure on integers whose every
+  step is specified, so that an independent implementation reproduces the
+  coefficients bit for bit.  All roundings are rnd(x) = floor(x + 1/2) of an
+  exact rational x.  y is real, so its length-n DFT is taken through a
+  complex DFT of half the length (the standard real-input split):
+    0. scale: if no slot is given or all z_j = 0, m = 0.  M = max_j |z_j| (a
+       non-finite M is an overflow); e with 2^(e-1) <= M < 2^e;
+       F = 59 - log2 n - e = 60 - log2 N - e (the ring's slot count, not the
+       number of given slots, so that zero padding leaves m unchanged);
+       Y_j = rnd(z_j 2^F), so that sum_j |Y_j| < 2^59 + n/2 and no
+       intermediate below exceeds 2^61 in magnitude;
+    1. y[t_j] = Y_j (other entries 0); g_s = y[2s] + i y[2s+1], s < h = n/2;
     2. G = DFT_h(g) by radix-2 decimation in time: g in bit-reversed order
        (log2 h bits); for hh = 1, 2, .., h/2, every block of 2hh and k < hh:
-       w = T[k N / hh]; (a, c) = (X[b+k], X[b+k+hh]);
-       tr = c.re*w.re - c.im*w.im; ti = c.re*w.im + c.im*w.re;
-       X[b+k] = (a.re + tr, a.im + ti); X[b+k+hh] = (a.re - tr, a.im - ti);
+       (a, c) = (X[b+k], X[b+k+hh]); t = cmul(c, W[k N / hh]);
+       X[b+k] = a + t; X[b+k+hh] = a - t;
     3. split, for k = 0..h with G[h] = G[0]: a = G[k], b = G[h-k];
        sr = a.re + b.re; si = a.im - b.im; dr = a.re - b.re; di = a.im + b.im;
-       E = (0.5*sr, 0.5*si); O = (0.5*di, -(0.5*dr));
-       W = T[4k] for k < h, W = (-1, 0) for k = h;
-       t = (O.re*W.re - O.im*W.im, O.re*W.im + O.im*W.re);
-       X[k] = (E.re + t.re, E.im + t.im); X[n-k] = conj(X[k]) for 0 < k < h;
-    4. twist: S[k] = X[k] * T[k] (the same complex product formula), k < n;
-    5. m_k = rint(2^s Re S[k]), m_{k+n} = rint(2^s Im S[k]), s = log2 Delta + 1 - log2 N
-       (an exact power-of-two scaling), ties to even.
-  Each product and sum is a separate correctly rounded FP64 operation (no
-  fused multiply-add).  T[k] = cos(pi k / N) - i sin(pi k / N), k < N, each
-  part correctly rounded to FP64 (computed here in 50-digit decimal).
+       t = cmul((di, -dr), V) with V = W[4k] for k < h, V = (-2^62, 0) for k = h;
+       X2[k] = (sr + t.re, si + t.im)  (twice the split output, no halving);
+       X2[n-k] = conj(X2[k]) for 0 < k < h;
+    4. twist: S2[k] = cmul(X2[k], W[k]), k < n;
+    5. m_k = rnd(2^d S2[k].re), m_{k+n} = rnd(2^d S2[k].im), d = s - F - 1,
+       s = log2 Delta + 1 - log2 N; |m_k| >= 2^62 is an overflow.
+  Twiddles W[k] = (C[k], -S[k]) with C[k] = rnd(2^62 cos(pi k / N)) and
+  S[k] = rnd(2^62 sin(pi k / N)), k < N (computed here in 50-digit decimal);
+  cmul((ar, ai), (wr, wi)) = (rnd((ar wr - ai wi) / 2^62), rnd((ar wi + ai wr) / 2^62)),
+  each numerator exact (128-bit), rounded once.  Multiplication by
+  W[0] = (2^62, 0) and W[N/2] = (0, -2^62) is exact, so implementations may
+  skip those products.
+
+The FP64 twiddles ``twiddles`` (correctly rounded cos, -sin) serve the
+decoder and the direct sum only.
 """
 from decimal import Decimal, localcontext
+from fractions import Fraction
 import functools
 import math
 
@@ -140,82 +152,155 @@ def _brv_perm(bits):
     return r
 
 
-def _dit(xr, xi, log_n, tr_, ti_):
-    """Radix-2 DIT butterflies (step 2) on bit-reversed input, in place order."""
-    n_ring = 1 << log_n
-    size = xr.shape[0]
-    hh = 1
-    while hh < size:
-        k = np.arange(hh)
-        wr = tr_[k * (n_ring // hh)]
-        wi = ti_[k * (n_ring // hh)]
-        xr = xr.reshape(-1, 2 * hh)
-        xi = xi.reshape(-1, 2 * hh)
-        ar, ai = xr[:, :hh].copy(), xi[:, :hh].copy()
-        cr, ci = xr[:, hh:].copy(), xi[:, hh:].copy()
-        tr = cr * wr - ci * wi
-        ti = cr * wi + ci * wr
-        xr = np.concatenate([ar + tr, ar - tr], axis=1).reshape(-1)
-        xi = np.concatenate([ai + ti, ai - ti], axis=1).reshape(-1)
-        hh *= 2
-    return xr, xi
+@functools.lru_cache(maxsize=None)
+def twiddles_q62(log_n: int):
+    """(C, S) int64 arrays: C[k] = rnd(2^62 cos(pi k / N)), S[k] = rnd(2^62 sin(pi k / N)), k < N."""
+    n = 1 << log_n
+    quarter = n // 4
+    one = 1 << Q
+    with localcontext() as ctx:
+        ctx.prec = 50
+        pi = _pi(50)
+        scale = Decimal(2) ** Q
+        cs = []                  # (C, S) of pi k / N for k in [0, N/4]
+        for k in range(quarter + 1):
+            if k == 0:
+                cs.append((one, 0))
+                continue
+            s, c = _sin_cos(pi * k / n, 50)
+            cs.append((int((c * scale + Decimal("0.5")).to_integral_value(rounding="ROUND_FLOOR")),
+                       int((s * scale + Decimal("0.5")).to_integral_value(rounding="ROUND_FLOOR"))))
+    C = np.empty(n, dtype=np.int64)
+    S = np.empty(n, dtype=np.int64)
+    for k in range(n):
+        # the same exact symmetries as the FP64 table
+        if k <= quarter:
+            c, s_ = cs[k]
+        elif k <= n // 2:
+            s_, c = cs[n // 2 - k]
+        elif k <= 3 * quarter:
+            cx, sx = cs[k - n // 2]
+            c, s_ = -sx, cx
+        else:
+            cx, sx = cs[n - k]
+            c, s_ = -cx, sx
+        C[k] = c
+        S[k] = s_
+    return C, S
 
 
-def encode_real(z, log_n: int, log2_delta: int):
-    """Steps 1-4 of the specified procedure and the power-of-two scaling
-    (exact); returns the N unrounded coefficients as float64."""
+Q = 62
+HALF_Q = 1 << (Q - 1)
+
+
+def _obj(a):
+    return np.array([int(v) for v in a], dtype=object)
+
+
+def _cmul(ar, ai, wr, wi):
+    """Fixed-point complex product (Python integers, elementwise): each part's
+    numerator is exact and rounded once, floor(x / 2^62 + 1/2)."""
+    return (ar * wr - ai * wi + HALF_Q) >> Q, (ar * wi + ai * wr + HALF_Q) >> Q
+
+
+def block_scale(z, log_n: int):
+    """Step 0: (F, Y) with Y_j = rnd(z_j 2^F) as Python integers; F is None
+    for an all-zero (or empty) input."""
+    z = np.asarray(z, dtype=np.float64)
+    ns = z.shape[0]
+    if ns == 0:
+        return None, []
+    M = float(np.max(np.abs(z)))
+    if not math.isfinite(M):
+        raise OverflowError("non-finite slot value")
+    if M == 0.0:
+        return None, [0] * ns
+    e = math.frexp(M)[1]                       # 2^(e-1) <= M < 2^e
+    F = 59 - (log_n - 1) - e
+    Y = [math.floor(Fraction(float(v)) * Fraction(2) ** F + Fraction(1, 2)) for v in z]
+    return F, Y
+
+
+def encode_fixed(z, log_n: int):
+    """Steps 0-4: (F, S2re, S2im) with S2 = 2 * 2^F * S (Python integers, k < n),
+    or (None, zeros, zeros) for a zero input."""
     n_ring = 1 << log_n
     n = n_ring // 2
     h = n // 2
     z = np.asarray(z, dtype=np.float64)
     assert z.ndim == 1 and z.shape[0] <= n
-    y = np.zeros(n)
-    y[slot_index(log_n)[: z.shape[0]]] = z
+    F, Y = block_scale(z, log_n)
+    if F is None:
+        zero = np.zeros(n, dtype=object)
+        return None, zero, zero.copy()
+    y = [0] * n
+    t = slot_index(log_n)
+    for j, v in enumerate(Y):
+        y[int(t[j])] = v
+    C, S = twiddles_q62(log_n)
+    Wr, Wi = _obj(C), -_obj(S)
     lg = h.bit_length() - 1
     perm = _brv_perm(lg)
-    tr_, ti_ = twiddles(log_n)
-    gr, gi = _dit(y[0::2][perm].copy(), y[1::2][perm].copy(), log_n, tr_, ti_)   # steps 1, 2
-    # step 3: split the half-length transform into X[0..n)
-    k = np.arange(h + 1)
-    Gr = np.concatenate([gr, gr[:1]])
-    Gi = np.concatenate([gi, gi[:1]])
+    xr = _obj(y[0::2])[perm]                   # step 1
+    xi = _obj(y[1::2])[perm]
+    hh = 1                                     # step 2
+    while hh < h:
+        k = np.arange(hh)
+        wr, wi = Wr[k * (n_ring // hh)], Wi[k * (n_ring // hh)]
+        xr = xr.reshape(-1, 2 * hh)
+        xi = xi.reshape(-1, 2 * hh)
+        ar, ai = xr[:, :hh], xi[:, :hh]
+        tr, ti = _cmul(xr[:, hh:], xi[:, hh:], wr, wi)
+        xr = np.concatenate([ar + tr, ar - tr], axis=1).reshape(-1)
+        xi = np.concatenate([ai + ti, ai - ti], axis=1).reshape(-1)
+        hh *= 2
+    k = np.arange(h + 1)                       # step 3
+    Gr = np.concatenate([xr, xr[:1]])
+    Gi = np.concatenate([xi, xi[:1]])
     ar, ai = Gr[k], Gi[k]
     br, bi = Gr[h - k], Gi[h - k]
-    sr = ar + br
-    si = ai - bi
-    dr = ar - br
-    di = ai + bi
-    er = 0.5 * sr
-    ei = 0.5 * si
-    o_r = 0.5 * di
-    o_i = -(0.5 * dr)
-    wr = np.where(k < h, tr_[(4 * k) % n_ring], -1.0)
-    wi = np.where(k < h, ti_[(4 * k) % n_ring], 0.0)
-    t_r = o_r * wr - o_i * wi
-    t_i = o_r * wi + o_i * wr
-    xk_r = er + t_r
-    xk_i = ei + t_i
-    xr = np.empty(n)
-    xi = np.empty(n)
-    xr[: h + 1] = xk_r
-    xi[: h + 1] = xk_i
-    xr[h + 1:] = xk_r[1:h][::-1]
-    xi[h + 1:] = -xk_i[1:h][::-1]
-    # step 4: twist
-    wr = tr_[:n]
-    wi = ti_[:n]
-    sr = xr * wr - xi * wi
-    si = xr * wi + xi * wr
-    scale = 2.0 ** (log2_delta + 1 - log_n)
-    return np.concatenate([sr * scale, si * scale])
+    sr, si = ar + br, ai - bi
+    dr, di = ar - br, ai + bi
+    vr = np.concatenate([Wr[4 * k[:-1]], _obj([-(1 << Q)])])
+    vi = np.concatenate([Wi[4 * k[:-1]], _obj([0])])
+    tr, ti = _cmul(di, -dr, vr, vi)
+    x2r = np.empty(n, dtype=object)
+    x2i = np.empty(n, dtype=object)
+    x2r[: h + 1] = sr + tr
+    x2i[: h + 1] = si + ti
+    x2r[h + 1:] = x2r[1:h][::-1]
+    x2i[h + 1:] = -x2i[1:h][::-1]
+    s2r, s2i = _cmul(x2r, x2i, Wr[:n], Wi[:n])  # step 4
+    return F, s2r, s2i
+
+
+def encode_real(z, log_n: int, log2_delta: int):
+    """The unrounded coefficients 2^(s-F-1) S2 of step 5 (float64, length N)."""
+    F, s2r, s2i = encode_fixed(z, log_n)
+    if F is None:
+        return np.zeros(1 << log_n)
+    d = log2_delta + 1 - log_n - F - 1
+    return np.array([math.ldexp(float(v), d) for v in np.concatenate([s2r, s2i])])
+
+
+def _rnd_shift(v, d):
+    """rnd(2^d v) for a Python integer v."""
+    if d >= 0:
+        return v << d
+    return (v + (1 << (-d - 1))) >> (-d)
 
 
 def encode(z, log_n: int, log2_delta: int):
     """Integer plaintext coefficients m_k (int64 array of length N)."""
-    m = np.rint(encode_real(z, log_n, log2_delta))
-    if not np.all(np.isfinite(m)) or np.any(np.abs(m) >= OVERFLOW_LIMIT):
+    n_ring = 1 << log_n
+    F, s2r, s2i = encode_fixed(z, log_n)
+    if F is None:
+        return np.zeros(n_ring, dtype=np.int64)
+    d = log2_delta + 1 - log_n - F - 1
+    m = [_rnd_shift(int(v), d) for v in np.concatenate([s2r, s2i])]
+    if any(abs(v) >= OVERFLOW_LIMIT for v in m):
         raise OverflowError("encoded coefficient magnitude >= 2^62")
-    return m.astype(np.int64)
+    return np.array(m, dtype=np.int64)
 
 
 def encode_direct(z, log_n: int, log2_delta: int):
@@ -248,11 +333,17 @@ def decode(m, log_n: int, log2_delta: int, n_slots: int):
 
 
 def encode_error_bound(z, log_n: int, log2_delta: int):
-    """A bound on |encode_real - exact| from FP64 rounding: each of the
-    log2(n)+1 levels of products/sums adds at most ~4 ulp of the running
-    magnitude, which is bounded by sum |z| (times the scale)."""
-    n = 1 << log_n
-    lg = (n // 2).bit_length() - 1
-    scale = 2.0 ** (log2_delta + 1 - log_n)
-    mag = float(np.sum(np.abs(z))) * scale
-    return 8.0 * (lg + 2) * mag * 2.0 ** -53 + math.ulp(max(mag, 1.0))
+    """A bound on |encode_real - exact| (in coefficient units) for the
+    fixed-point procedure, in units of Y (2^-F): a cmul part is off by at most
+    1/2 (rounding) + 2^-63 (|a.re| + |a.im|) (twiddle quantisation, <= 0.18
+    for operands of modulus <= 2^60), so a cmul adds at most 0.96 in modulus;
+    an input part by at most 1/2 (0.71 for g).  Through the L = log2 h DIT
+    stages errors pass with unit-modulus weights: a DFT output is off by at
+    most 2^L (0.71 + 0.96); the split gives X2 off by at most 4 of those plus
+    0.96, the twist adds 0.96: 6.68 h + 1.92 <= 3.4 n + 2.  Coefficients are
+    2^(s-F-1) S2 (s = log2 Delta + 1 - log2 N)."""
+    n = 1 << (log_n - 1)
+    F, _ = block_scale(z, log_n)
+    if F is None:
+        return 0.0
+    return math.ldexp(3.4 * n + 2.0, log2_delta + 1 - log_n - F - 1)

@@ -69,6 +69,7 @@ _SIGS = {
     "zn_ntt_forward": (_i32, [_vp, _vp, _u32, _vp]),
     "zn_ntt_inverse": (_i32, [_vp, _vp, _u32, _vp]),
     "zn_sample": (_i32, [_vp, _i32, _u64, _u32, _u32, _u32, _u64, _u32, _vp, _vp]),
+    "zn_chi_eval": (_i32, [_vp, _vp, _u32, _vp, _vp]),
     "zn_encrypt_host": (_i32, [_vp, _vp, _vp, _vp, _u32, _u32, _u64, _vp, _vp, _u32]),
     "zn_batch_create": (_i32, [_vp, _u32, _i32, _pp]),
     "zn_batch_destroy": (None, [_vp]),
@@ -83,6 +84,7 @@ _SIGS = {
     "zn_host_primes": (_i32, [_u32, _vp, _u32, _vp]),
     "zn_host_psi": (_u64, [_u64, _u32]),
     "zn_host_encoder_twiddles": (_i32, [_u32, _vp, _vp]),
+    "zn_host_encoder_twiddles_q62": (_i32, [_u32, _vp, _vp]),
     "zn_host_cdt": (_i32, [_vp]),
 }
 
@@ -410,6 +412,15 @@ def zn_sample(ctx, kind, seed, domain, poly, prime, ct_index0, count, out=None, 
     return out
 
 
+def zn_chi_eval(ctx, u, stream=None):
+    """chi's table step on device uniforms u (int64 tensor holding uint64 bits) -> int32 tensor."""
+    import torch
+    _dev(u, torch.int64, None, "u")
+    out = torch.empty(u.shape, dtype=torch.int32, device=u.device)
+    _check(lib().zn_chi_eval(ctx.handle, u.data_ptr(), u.numel(), out.data_ptr(), _stream(stream)), "zn_chi_eval")
+    return out
+
+
 class _Job(ctypes.Structure):
     _fields_ = [("ctx", ctypes.c_void_p), ("zinc", ctypes.c_int), ("pk", ctypes.c_void_p), ("zc", ctypes.c_void_p),
                 ("slots", ctypes.c_void_p), ("n_slots", ctypes.c_uint32), ("count", ctypes.c_uint32),
@@ -536,6 +547,14 @@ def zn_host_encoder_twiddles(log_n):
     im = np.empty(n)
     _check(lib().zn_host_encoder_twiddles(log_n, re.ctypes.data, im.ctypes.data), "zn_host_encoder_twiddles")
     return re, im
+
+
+def zn_host_encoder_twiddles_q62(log_n):
+    n = 1 << log_n
+    c = np.empty(n, dtype=np.int64)
+    s = np.empty(n, dtype=np.int64)
+    _check(lib().zn_host_encoder_twiddles_q62(log_n, c.ctypes.data, s.ctypes.data), "zn_host_encoder_twiddles_q62")
+    return c, s
 
 
 def zn_host_cdt():

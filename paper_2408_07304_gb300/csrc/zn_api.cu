@@ -25,7 +25,7 @@ struct zn_ctx {
   DevParams dp;
   // device allocations owned by the context
   u64* d_tw;          // (tw, tws) pairs [L][N], itw [L][N], itws [L][N]: one allocation
-  double* d_etw;      // [2][N]
+  double* d_etw;      // [2][N] decoder twiddles, then [N] encoder Q62 pairs
   int* d_slot;        // [N/2]
   unsigned* d_status;
   cudaMemPool_t pool; // stream-ordered scratch (prep outputs)
@@ -210,6 +210,11 @@ int zn_host_encoder_twiddles(uint32_t log_n, double* re, double* im) {
   return zn::encoder_twiddles(log_n, re, im);
 }
 
+int zn_host_encoder_twiddles_q62(uint32_t log_n, int64_t* c, int64_t* s) {
+  if (!c || !s || log_n < 2 || log_n > 20) return ZN_EINVAL;
+  return zn::encoder_twiddles_q62(log_n, c, s);
+}
+
 int zn_host_cdt(uint64_t* out) {
   if (!out) return ZN_EINVAL;
   return zn::cdt_thresholds(out);
@@ -253,8 +258,19 @@ int zn_ctx_create(const zn_params* p, int device, zn_ctx** out) {
       }
     }
   }
-  std::vector<double> etw(2 * (size_t)n);
+  // decoder FP64 twiddles [2][N], then the encoder's Q62 pairs (C[k], -S[k]) [N]
+  std::vector<double> etw(4 * (size_t)n);
   zn::encoder_twiddles(p->log_n, etw.data(), etw.data() + n);
+  {
+    std::vector<int64_t> qc(n), qs(n);
+    zn::encoder_twiddles_q62(p->log_n, qc.data(), qs.data());
+    std::vector<int64_t> pairs(2 * (size_t)n);
+    for (uint32_t k = 0; k < n; ++k) {
+      pairs[2 * k] = qc[k];
+      pairs[2 * k + 1] = -qs[k];
+    }
+    std::memcpy(etw.data() + 2 * (size_t)n, pairs.data(), sizeof(int64_t) * pairs.size());
+  }
   std::vector<int> slot(n / 2);
   {
     u64 g = 1;
@@ -315,6 +331,7 @@ int zn_ctx_create(const zn_params* p, int device, zn_ctx** out) {
   dp.itw = c->d_tw + 2 * (size_t)L * n;
   dp.itws = c->d_tw + 3 * (size_t)L * n;
   dp.etw = c->d_etw;
+  dp.etq = reinterpret_cast<const longlong2*>(c->d_etw + 2 * (size_t)n);
   dp.slot_of_t = c->d_slot;
   dp.status = c->d_status;
   *out = c;
@@ -1032,6 +1049,15 @@ int zn_sample(zn_ctx* c, int kind, uint64_t seed, uint32_t domain, uint32_t poly
   if (!out) return ZN_EINVAL;
   DeviceGuard g(c->device);
   ZN_CUDA(zn::launch_sample(c->dp, kind, seed, domain, poly, prime, ct_index0, count, (i64*)out, S(stream)));
+  return ZN_OK;
+}
+
+int zn_chi_eval(zn_ctx* c, const uint64_t* u, uint32_t n, int32_t* out, void* stream) {
+  if (!c) return ZN_EINVAL;
+  if (n == 0) return ZN_OK;
+  if (!u || !out) return ZN_EINVAL;
+  DeviceGuard g(c->device);
+  ZN_CUDA(zn::launch_chi_eval(c->dp, u, n, out, S(stream)));
   return ZN_OK;
 }
 

@@ -1,66 +1,93 @@
-// Encoder (FP64 FFT with a fixed operation order), inverse NTT, decryption
-// (Eq. 10), decoding, homomorphic addition and small helpers.
+// Encoder (fixed-point FFT with exact 128-bit products), inverse NTT,
+// decryption (Eq. 10), decoding (FP64), homomorphic addition and small helpers.
 #include "zn_kernels.h"
 
 namespace zn {
 
 // ------------------------------------------------------------------ encode
 
-// Encoder core: one block per slot vector.  (re, im) hold h = N/4 doubles
-// each, in shared memory.  The real length-n DFT (n = N/2) is taken through a
-// complex DFT of length h and a split step; every FP64 operation follows the
-// specified order (see fft_dit and the split below).  out(k, m_k, m_{k+n})
-// receives the rounded coefficients, once for every k < n.
+// Encoder core: one block per slot vector.  (re, im) hold h = N/4 int64
+// each, in shared memory.  Fixed-point procedure (bit-reproducible):
+//   0. block scale F = 60 - log2 N - e, 2^(e-1) <= max|z| < 2^e;
+//      Y_j = floor(z_j 2^F + 1/2);
+//   1-2. g_s = y[2s] + i y[2s+1] (y[t_j] = Y_j) in bit-reversed order, radix-2
+//      DIT of length h with Q62 twiddles (fft_dit_q62);
+//   3. split: X2[k] = (sr, si) + cmul((di, -dr), V), V = W[4k] (k < h) or -1;
+//   4. twist S2[k] = cmul(X2[k], W[k]);
+//   5. m_k = floor(2^d S2[k].re + 1/2), m_{k+n} likewise with .im, d = s - F - 1.
+// out(k, m_k, m_{k+n}) is called once for every k < n.  A non-finite slot or
+// |m| >= 2^62 latches the overflow status and gives zero coefficients.
 template <class Out>
 __device__ __forceinline__ void encode_core(const DevParams& P, const double* __restrict__ z, uint32_t n_slots,
-                                            double* re, double* im, Out& out) {
+                                            i64* re, i64* im, Out& out) {
+  __shared__ u64 s_max[32];
   const int log_n = P.log_n, N = 1 << log_n, n = N >> 1, h = n >> 1, lh = log_n - 2;
-  // g_s = y[2s] + i y[2s+1] with y[t_j] = z_j, in bit-reversed order
+  const u64 kAbs = ~(1ull << 63);
+  // raw bit patterns in bit-reversed order, and max |z| (as ordered bits)
+  u64 mx = 0;
   for (int r = threadIdx.x; r < h; r += blockDim.x) {
     const int s2 = 2 * brv_bits(r, lh);
     const int j0 = __ldg(P.slot_of_t + s2), j1 = __ldg(P.slot_of_t + s2 + 1);
-    re[r] = (j0 < (int)n_slots) ? __ldg(z + j0) : 0.0;
-    im[r] = (j1 < (int)n_slots) ? __ldg(z + j1) : 0.0;
+    const u64 b0 = (j0 < (int)n_slots) ? (u64)__double_as_longlong(__ldg(z + j0)) : 0ull;
+    const u64 b1 = (j1 < (int)n_slots) ? (u64)__double_as_longlong(__ldg(z + j1)) : 0ull;
+    re[r] = (i64)b0;
+    im[r] = (i64)b1;
+    mx = max(mx, max(b0 & kAbs, b1 & kAbs));
+  }
+#pragma unroll
+  for (int off = 16; off; off >>= 1) mx = max(mx, (u64)__shfl_xor_sync(0xffffffffu, (unsigned long long)mx, off));
+  if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    u64 v = threadIdx.x < (blockDim.x + 31) / 32 ? s_max[threadIdx.x] : 0ull;
+#pragma unroll
+    for (int off = 16; off; off >>= 1) v = max(v, (u64)__shfl_xor_sync(0xffffffffu, (unsigned long long)v, off));
+    if (threadIdx.x == 0) s_max[0] = v;
   }
   __syncthreads();
-  fft_dit(re, im, lh, log_n, P.etw, false);
-  const double scale = ldexp(1.0, P.log2_delta + 1 - log_n);
-  const double* twr = P.etw;
-  const double* twi = P.etw + N;
-  const double lim = 4611686018427387904.0;   // 2^62
-  // twist by T[k], exact power-of-two scaling, rint (ties to even)
-  auto emit = [&](int k, double xr, double xi) {
-    const double wr = __ldg(twr + k), wi = __ldg(twi + k);
-    const double sr = __dsub_rn(__dmul_rn(xr, wr), __dmul_rn(xi, wi));
-    const double si = __dadd_rn(__dmul_rn(xr, wi), __dmul_rn(xi, wr));
-    double a = rint(__dmul_rn(sr, scale)), b = rint(__dmul_rn(si, scale));
-    if (!(fabs(a) < lim) || !(fabs(b) < lim)) {
+  const u64 M = s_max[0];
+  const int mex = (int)(M >> 52);
+  if (M == 0 || mex == 0x7FF) {                 // zero vector, or a non-finite slot
+    if (mex == 0x7FF && threadIdx.x == 0) atomicOr(P.status, kStatusOverflow);
+    for (int k = threadIdx.x; k < n; k += blockDim.x) out(k, (i64)0, (i64)0);
+    return;
+  }
+  const int e = mex ? mex - 1022 : (64 - __clzll((long long)(M & ((1ull << 52) - 1)))) - 1074;
+  const int F = 60 - log_n - e;     // the ring's slot count: zero padding changes nothing
+  for (int r = threadIdx.x; r < h; r += blockDim.x) {
+    re[r] = to_fixed((u64)re[r], F);
+    im[r] = to_fixed((u64)im[r], F);
+  }
+  __syncthreads();
+  fft_dit_q62(re, im, lh, log_n, P.etq);
+  const int d = P.log2_delta + 1 - log_n - F - 1;
+  auto emit = [&](int k, i64 xr, i64 xi) {
+    i64 sr, si, a, b;
+    cmul_q62(xr, xi, __ldg(P.etq + k), sr, si);
+    const bool ok = from_fixed(sr, d, a) & from_fixed(si, d, b);
+    if (!ok) {
       atomicOr(P.status, kStatusOverflow);
-      a = 0.0;
-      b = 0.0;
+      a = 0;
+      b = 0;
     }
-    out(k, (i64)a, (i64)b);
+    out(k, a, b);
   };
-  // split: X[k] from G[k] and G[h-k] (G[h] = G[0]); X[n-k] = conj(X[k])
+  // split: X2[k] from G[k] and G[h-k] (G[h] = G[0]); X2[n-k] = conj(X2[k])
   for (int k = threadIdx.x; k <= h; k += blockDim.x) {
     const int ka = k == h ? 0 : k, kb = k == 0 ? 0 : h - k;
-    const double ar = re[ka], ai = im[ka], br = re[kb], bi = im[kb];
-    const double sr = __dadd_rn(ar, br), si = __dsub_rn(ai, bi);
-    const double dr = __dsub_rn(ar, br), di = __dadd_rn(ai, bi);
-    const double er = __dmul_rn(0.5, sr), ei = __dmul_rn(0.5, si);
-    const double o_r = __dmul_rn(0.5, di), o_i = -__dmul_rn(0.5, dr);
-    const double wr = k < h ? __ldg(twr + 4 * k) : -1.0;
-    const double wi = k < h ? __ldg(twi + 4 * k) : 0.0;
-    const double t_r = __dsub_rn(__dmul_rn(o_r, wr), __dmul_rn(o_i, wi));
-    const double t_i = __dadd_rn(__dmul_rn(o_r, wi), __dmul_rn(o_i, wr));
-    const double xr = __dadd_rn(er, t_r), xi = __dadd_rn(ei, t_i);
+    const i64 ar = re[ka], ai = im[ka], br = re[kb], bi = im[kb];
+    const i64 sr = ar + br, si = ai - bi, dr = ar - br, di = ai + bi;
+    const longlong2 v = k < h ? __ldg(P.etq + 4 * k) : make_longlong2(-(1ll << 62), 0);
+    i64 tr, ti;
+    cmul_q62(di, -dr, v, tr, ti);
+    const i64 xr = sr + tr, xi = si + ti;
     emit(k, xr, xi);
     if (k > 0 && k < h) emit(n - k, xr, -xi);
   }
 }
 
 __device__ __forceinline__ void encode_one(const DevParams& P, const double* __restrict__ z, uint32_t n_slots,
-                                           double* re, double* im, i64* __restrict__ out) {
+                                           i64* re, i64* im, i64* __restrict__ out) {
   const int n = 1 << (P.log_n - 1);
   auto st = [&](int k, i64 a, i64 b) {
     out[k] = a;
@@ -70,10 +97,10 @@ __device__ __forceinline__ void encode_one(const DevParams& P, const double* __r
 }
 
 __global__ void k_encode_smem(DevParams P, const double* __restrict__ slots, uint32_t n_slots, i64* __restrict__ out) {
-  extern __shared__ double smd[];
+  extern __shared__ i64 smi[];
   const int N = 1 << P.log_n, h = N >> 2;
   const size_t b = blockIdx.x;
-  encode_one(P, slots + b * n_slots, n_slots, smd, smd + h, out + b * N);
+  encode_one(P, slots + b * n_slots, n_slots, smi, smi + h, out + b * N);
 }
 
 // -------------------------------------------------------------------- prep
@@ -82,27 +109,37 @@ __global__ void k_encode_smem(DevParams P, const double* __restrict__ slots, uin
 // for all q_i):
 //   vanilla (Eq. 8):    me = m + e0 (poly 1), small = [u (poly 0), e1 (poly 2)]
 //   Zinc (Algorithm 1): me = m + e1' (poly 0), small = [e2' (poly 1)]
-// chi block k yields coefficients k and k + N/2 -- exactly the pair that the
+// chi block k yields coefficients k and k + N/2 -- the pair that the
 // encoder's last loop produces at k.
+// cdt: the chi thresholds staged in shared memory by the calling kernel.
 template <bool ZINC>
-__device__ __forceinline__ void prep_one(const DevParams& P, const PrepArgs& A, size_t b, double* re, double* im) {
+__device__ __forceinline__ void prep_one(const DevParams& P, const PrepArgs& A, size_t b, i64* re, i64* im,
+                                         const u64* cdt) {
   const int N = 1 << P.log_n, n = N >> 1;
   const u64 ct = A.ct_index ? A.ct_index[b] : A.ct_index0 + b;
   i64* me = A.me + b * N;
   int8_t* sp = A.small + b * 2 * (size_t)N;
   const unsigned tag_e = rand_tag(A.domain, ZINC ? 0 : 1, 0);
-  auto st = [&](int k, i64 a, i64 c) {
-    const uint4 w = zn_rand(A.seed, (unsigned)k, tag_e, ct);
-    me[k] = a + cdt_of(w.x, w.y, P.cdt);
-    me[k + n] = c + cdt_of(w.z, w.w, P.cdt);
-  };
+  // m first (kept apart from the sampler, which would otherwise share the
+  // encoder's registers), then m + e once the block's stores are visible
   if (A.n_slots) {
+    auto st = [&](int k, i64 a, i64 c) {
+      me[k] = a;
+      me[k + n] = c;
+    };
     encode_core(P, A.slots + b * A.n_slots, A.n_slots, re, im, st);
-  } else {
-    for (int k = threadIdx.x; k < n; k += blockDim.x) st(k, 0, 0);
+    __syncthreads();
+  }
+#pragma unroll 1
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const uint4 w = zn_rand(A.seed, (unsigned)k, tag_e, ct);
+    const i64 a = A.n_slots ? me[k] : 0, c = A.n_slots ? me[k + n] : 0;
+    me[k] = a + cdt_search(w.x, w.y, cdt);
+    me[k + n] = c + cdt_search(w.z, w.w, cdt);
   }
   if constexpr (!ZINC) {
     const unsigned tag_u = rand_tag(A.domain, 0, 0), tag_1 = rand_tag(A.domain, 2, 0);
+#pragma unroll 1
     for (int blk = threadIdx.x; blk < N / 4; blk += blockDim.x) {
       const uint4 w = zn_rand(A.seed, (unsigned)blk, tag_u, ct);
       sp[blk] = (int8_t)ternary_of(w.x);
@@ -110,26 +147,35 @@ __device__ __forceinline__ void prep_one(const DevParams& P, const PrepArgs& A, 
       sp[blk + N / 2] = (int8_t)ternary_of(w.z);
       sp[blk + 3 * N / 4] = (int8_t)ternary_of(w.w);
     }
+#pragma unroll 1
     for (int blk = threadIdx.x; blk < n; blk += blockDim.x) {
       const uint4 w = zn_rand(A.seed, (unsigned)blk, tag_1, ct);
-      sp[N + blk] = (int8_t)cdt_of(w.x, w.y, P.cdt);
-      sp[N + blk + n] = (int8_t)cdt_of(w.z, w.w, P.cdt);
+      sp[N + blk] = (int8_t)cdt_search(w.x, w.y, cdt);
+      sp[N + blk + n] = (int8_t)cdt_search(w.z, w.w, cdt);
     }
   } else {
     const unsigned tag_2 = rand_tag(A.domain, 1, 0);
+#pragma unroll 1
     for (int blk = threadIdx.x; blk < n; blk += blockDim.x) {
       const uint4 w = zn_rand(A.seed, (unsigned)blk, tag_2, ct);
-      sp[blk] = (int8_t)cdt_of(w.x, w.y, P.cdt);
-      sp[blk + n] = (int8_t)cdt_of(w.z, w.w, P.cdt);
+      sp[blk] = (int8_t)cdt_search(w.x, w.y, cdt);
+      sp[blk + n] = (int8_t)cdt_search(w.z, w.w, cdt);
     }
   }
 }
 
+__device__ __forceinline__ void stage_cdt(const DevParams& P, u64* s_cdt) {
+  for (int j = threadIdx.x; j < kCdt; j += blockDim.x) s_cdt[j] = P.cdt[j];
+  __syncthreads();
+}
+
 template <bool ZINC>
-__global__ void k_prep_smem(DevParams P, PrepArgs A) {
-  extern __shared__ double smd[];
+__global__ void __launch_bounds__(512, 2) k_prep_smem(DevParams P, PrepArgs A) {
+  extern __shared__ i64 smi[];
+  __shared__ u64 s_cdt[kCdt];
+  stage_cdt(P, s_cdt);
   const int h = 1 << (P.log_n - 2);
-  prep_one<ZINC>(P, A, blockIdx.x, smd, smd + h);
+  prep_one<ZINC>(P, A, blockIdx.x, smi, smi + h, s_cdt);
 }
 
 // Persistent prep over a mixed work list: one 512-thread block per SM takes
@@ -137,8 +183,9 @@ __global__ void k_prep_smem(DevParams P, PrepArgs A) {
 // rings up to 2^15 fits in the block's 128 KiB of shared memory.
 __global__ void __launch_bounds__(512, 1) k_batch_prep(const JobDesc* __restrict__ jobs,
                                                        const PrepUnit* __restrict__ units, int n_units, int* counter) {
-  extern __shared__ double smd[];
+  extern __shared__ i64 smi[];
   __shared__ int s_next;
+  __shared__ u64 s_cdt[kCdt];
   for (;;) {
     if (threadIdx.x == 0) s_next = atomicAdd(counter, 1);
     __syncthreads();
@@ -148,8 +195,9 @@ __global__ void __launch_bounds__(512, 1) k_batch_prep(const JobDesc* __restrict
     const PrepUnit u = units[p];
     const JobDesc& J = jobs[u.job];
     const int h = 1 << (J.P.log_n - 2);
-    if (J.zinc) prep_one<true>(J.P, J.Pr, u.b, smd, smd + h);
-    else prep_one<false>(J.P, J.Pr, u.b, smd, smd + h);
+    stage_cdt(J.P, s_cdt);
+    if (J.zinc) prep_one<true>(J.P, J.Pr, u.b, smi, smi + h, s_cdt);
+    else prep_one<false>(J.P, J.Pr, u.b, smi, smi + h, s_cdt);
     __syncthreads();
   }
 }
@@ -305,7 +353,7 @@ cudaError_t launch_encode(const DevParams& P, const double* slots, uint32_t n_sl
   if (batch == 0) return cudaSuccess;
   const int h = 1 << (P.log_n - 2);
   const int block = h / 2 < 512 ? (h / 2 < 32 ? 32 : h / 2) : 512;
-  const size_t smem = 2 * sizeof(double) * (size_t)h;
+  const size_t smem = 2 * sizeof(i64) * (size_t)h;
   cudaError_t e = cudaFuncSetAttribute(k_encode_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_encode_smem<<<batch, block, smem, st>>>(P, slots, n_slots, out);
@@ -316,7 +364,7 @@ template <bool ZINC>
 static cudaError_t prep_launch(const DevParams& P, const PrepArgs& A, uint32_t batch, cudaStream_t st) {
   const int h = 1 << (P.log_n - 2);
   const int block = h / 2 < 512 ? (h / 2 < 32 ? 32 : h / 2) : 512;
-  const size_t smem = A.n_slots ? 2 * sizeof(double) * (size_t)h : 0;
+  const size_t smem = A.n_slots ? 2 * sizeof(i64) * (size_t)h : 0;
   cudaError_t e = cudaFuncSetAttribute(k_prep_smem<ZINC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_prep_smem<ZINC><<<batch, block, smem, st>>>(P, A);
@@ -330,13 +378,13 @@ cudaError_t launch_prep(const DevParams& P, const PrepArgs& A, bool zinc, uint32
 
 cudaError_t launch_batch_prep(const JobDesc* jobs, const PrepUnit* units, int n_units, int* counter, int grid,
                               cudaStream_t st) {
-  k_batch_prep<<<grid, 512, sizeof(double) << 14, st>>>(jobs, units, n_units, counter);
+  k_batch_prep<<<grid, 512, sizeof(i64) << 14, st>>>(jobs, units, n_units, counter);
   return cudaGetLastError();
 }
 
 cudaError_t batch_set_attributes() {
   cudaError_t e = cudaFuncSetAttribute(k_batch_prep, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)(sizeof(double) << 14));
+                                       (int)(sizeof(i64) << 14));
   if (e != cudaSuccess) return e;
   return batch_encrypt_attributes();
 }

@@ -3,7 +3,8 @@
 //     constant, Barrett reduction of signed integers, Harvey lazy butterflies);
 //   * Philox4x32-10 and the three samplers (R_2, chi, R_q);
 //   * a shared-memory-staged negacyclic NTT with radix-16 register passes;
-//   * the FP64 radix-2 FFT of the CKKS encoder with a fixed operation order.
+//   * the fixed-point (Q62, exact 128-bit products) radix-2 FFT of the CKKS
+//     encoder and the FP64 one of the decoder.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -30,7 +31,8 @@ struct DevParams {
   const ulonglong2* twp;     // [L][N] (psi^brv(k), Shoup companion) pairs
   const u64* itw;            // [L][N] psi^-brv(k)
   const u64* itws;
-  const double* etw;         // [2][N] encoder twiddles: re, then im
+  const double* etw;         // [2][N] decoder twiddles (FP64): re, then im
+  const longlong2* etq;      // [N] encoder twiddles (C[k], -S[k]), Q62
   const int* slot_of_t;      // [N/2] slot j with (5^j mod 2N - 1)/4 = t
   unsigned* status;          // device status word (bit 0: encode overflow)
 };
@@ -147,6 +149,18 @@ __device__ __forceinline__ int cdt_of(unsigned lo, unsigned hi, const u64* cdt) 
 #pragma unroll
   for (int j = 0; j < kCdt; ++j) c += (u >= cdt[j]) ? 1 : 0;
   return c - kBound;
+}
+
+// The same count by a branchless binary search over the sorted thresholds
+// (pos ends at #{j : T_j <= U}), for a table in shared memory: six dependent
+// loads and compares instead of 38 compares against live constants.
+__device__ __forceinline__ int cdt_search(unsigned lo, unsigned hi, const u64* tab) {
+  const u64 u = ((u64)hi << 32) | lo;
+  int pos = 0;
+#pragma unroll
+  for (int step = 32; step; step >>= 1)
+    if (pos + step <= kCdt && u >= tab[pos + step - 1]) pos += step;
+  return pos - kBound;
 }
 
 // R_q: floor(W q / 2^128), W = w3:w2:w1:w0
@@ -441,6 +455,93 @@ __device__ __forceinline__ void fft_dit(double* re, double* im, int log_len, int
     }
     __syncthreads();
   }
+}
+
+// ------------------------------------------------ encoder FFT (fixed point)
+// Signed 128-bit values as (lo, hi) two's-complement halves.
+struct i128 {
+  u64 lo;
+  i64 hi;
+};
+__device__ __forceinline__ i128 mul_wide(i64 a, i64 b) { return {(u64)a * (u64)b, __mul64hi(a, b)}; }
+__device__ __forceinline__ i128 add128(i128 x, i128 y) {
+  const u64 lo = x.lo + y.lo;
+  return {lo, x.hi + y.hi + (i64)(lo < x.lo)};
+}
+__device__ __forceinline__ i128 sub128(i128 x, i128 y) {
+  return {x.lo - y.lo, x.hi - y.hi - (i64)(x.lo < y.lo)};
+}
+// floor(x / 2^62 + 1/2) for a result that fits in 64 bits
+__device__ __forceinline__ i64 rnd62(i128 x) {
+  const u64 lo = x.lo + (1ull << 61);
+  const i64 hi = x.hi + (i64)(lo < x.lo);
+  return (i64)(((u64)hi << 2) | (lo >> 62));
+}
+// (a_r + i a_i)(w_r + i w_i) with Q62 w: each part exact, rounded once
+__device__ __forceinline__ void cmul_q62(i64 ar, i64 ai, longlong2 w, i64& re, i64& im) {
+  re = rnd62(sub128(mul_wide(ar, w.x), mul_wide(ai, w.y)));
+  im = rnd62(add128(mul_wide(ar, w.y), mul_wide(ai, w.x)));
+}
+
+// Radix-2 decimation-in-time FFT of length 2^log_len on (re, im) int64 in
+// shared memory, input in bit-reversed order; the stage with half-size hh
+// uses W[k N / hh] (N = 2^log_n): t = cmul(c, W), (a + t, a - t).  W[0] = 1
+// and W[N/2] = -i make the product exact, so those are taken directly.
+__device__ __forceinline__ void fft_dit_q62(i64* re, i64* im, int log_len, int log_n, const longlong2* etq) {
+  const int len = 1 << log_len, N = 1 << log_n;
+  for (int lh = 0; lh < log_len; ++lh) {
+    const int hh = 1 << lh;
+    for (int idx = threadIdx.x; idx < len / 2; idx += blockDim.x) {
+      const int k = idx & (hh - 1);
+      const int p = ((idx >> lh) << (lh + 1)) + k;
+      const i64 ar = re[p], ai = im[p], cr = re[p + hh], ci = im[p + hh];
+      i64 tr, ti;
+      if (k == 0) {
+        tr = cr;
+        ti = ci;
+      } else if (2 * k == hh) {      // W = (0, -2^62)
+        tr = ci;
+        ti = -cr;
+      } else {
+        cmul_q62(cr, ci, __ldg(etq + k * (N >> lh)), tr, ti);
+      }
+      re[p] = ar + tr;
+      im[p] = ai + ti;
+      re[p + hh] = ar - tr;
+      im[p + hh] = ai - ti;
+    }
+    __syncthreads();
+  }
+}
+
+// floor(z 2^F + 1/2) for the double with bit pattern `bits`, given that
+// |z| 2^F < 2^59 (true for every slot once F is the vector's block scale).
+__device__ __forceinline__ i64 to_fixed(u64 bits, int F) {
+  const int ex = (int)((bits >> 52) & 0x7FF);
+  const u64 frac = bits & ((1ull << 52) - 1);
+  if (ex == 0 && frac == 0) return 0;
+  const i64 mant = (i64)(ex ? (frac | (1ull << 52)) : frac);
+  const int sh = (ex ? ex : 1) - 1075 + F;          // z = mant 2^((ex|1) - 1075)
+  const i64 v = (bits >> 63) ? -mant : mant;
+  if (sh >= 0) return (i64)((u64)v << sh);
+  const int r = -sh;
+  if (r >= 63) return 0;                             // |z 2^F| < 2^-10
+  return (v + (1ll << (r - 1))) >> r;
+}
+
+// m = floor(x 2^d + 1/2); false if |m| >= 2^62 (then m = 0).  |x| < 2^62.
+__device__ __forceinline__ bool from_fixed(i64 x, int d, i64& m) {
+  m = 0;
+  if (d >= 0) {
+    if (d >= 62) return x == 0;
+    const i64 lim = 1ll << (62 - d);
+    if (x >= lim || x <= -lim) return false;
+    m = (i64)((u64)x << d);
+    return true;
+  }
+  const int r = -d;
+  if (r < 63) m = (x + (1ll << (r - 1))) >> r;
+  return true;
 }
 
 __device__ __forceinline__ int brv_bits(int x, int bits) { return (int)(__brev((unsigned)x) >> (32 - bits)); }

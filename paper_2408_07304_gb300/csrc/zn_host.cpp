@@ -212,6 +212,49 @@ int encoder_twiddles(uint32_t log_n, double* re, double* im) {
   return 0;
 }
 
+// floor(2^62 x + 1/2) for a double-double x in [0, 1]: hi * 2^62 and
+// lo * 2^62 are exact; the integer part of the first is exact, and the
+// fractional remainder plus the second decides the rounding (correct except
+// within ~2^-40 of a tie).
+static int64_t q62_of(dd x) {
+  const double a = std::ldexp(x.hi, 62), b = std::ldexp(x.lo, 62);
+  const double ai = std::floor(a);
+  const double f = (a - ai) + b;
+  return (int64_t)ai + (int64_t)std::floor(f + 0.5);
+}
+
+// C[k] = floor(2^62 cos(pi k/N) + 1/2), S[k] = floor(2^62 sin(pi k/N) + 1/2),
+// k < N, with the same exact angle reductions as encoder_twiddles.
+int encoder_twiddles_q62(uint32_t log_n, int64_t* c_out, int64_t* s_out) {
+  const uint32_t n = 1u << log_n, quarter = n / 4;
+  int64_t* cs = new int64_t[2 * (quarter + 1)];
+  for (uint32_t k = 0; k <= quarter; ++k) {
+    if (k == 0) { cs[0] = (int64_t)1 << 62; cs[1] = 0; continue; }
+    dd th = dd_mul_d(kPi, (double)k);
+    th = {th.hi / n, th.lo / n};
+    dd s, c;
+    dd_sincos(th, &s, &c);
+    cs[2 * k] = q62_of(c);
+    cs[2 * k + 1] = q62_of(s);
+  }
+  for (uint32_t k = 0; k < n; ++k) {
+    int64_t c, s;
+    if (k <= quarter) {
+      c = cs[2 * k]; s = cs[2 * k + 1];
+    } else if (k <= n / 2) {
+      uint32_t j = n / 2 - k; c = cs[2 * j + 1]; s = cs[2 * j];
+    } else if (k <= 3 * quarter) {
+      uint32_t j = k - n / 2; c = -cs[2 * j + 1]; s = cs[2 * j];
+    } else {
+      uint32_t j = n - k; c = -cs[2 * j]; s = cs[2 * j + 1];
+    }
+    c_out[k] = c;
+    s_out[k] = s;
+  }
+  delete[] cs;
+  return 0;
+}
+
 // sum_n (-1)^n x^(2n+1) / (n! (2n+1)) = erf(x) sqrt(pi)/2, double-double
 static dd erf_core(dd x) {
   dd x2 = dd_mul(x, x);

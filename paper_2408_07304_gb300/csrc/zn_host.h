@@ -12,5 +12,6 @@ u64 find_psi(u64 q, uint32_t log_n);
 u64 shoup(u64 w, u64 q);
 void ntt_tables(u64 q, u64 psi, uint32_t log_n, u64* tw, u64* tws, u64* itw, u64* itws);
 int encoder_twiddles(uint32_t log_n, double* re, double* im);
+int encoder_twiddles_q62(uint32_t log_n, int64_t* c, int64_t* s);
 int cdt_thresholds(u64 out[38]);
 }  // namespace zn

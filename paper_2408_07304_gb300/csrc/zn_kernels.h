@@ -80,6 +80,7 @@ cudaError_t launch_decode(const DevParams& P, const u64* coeffs, uint32_t batch,
 cudaError_t launch_add(const DevParams& P, const u64* a, const u64* b, uint32_t batch, u64* out, cudaStream_t st);
 cudaError_t launch_sample(const DevParams& P, int kind, u64 seed, unsigned domain, unsigned poly, unsigned prime,
                           u64 ct_index0, uint32_t count, i64* out, cudaStream_t st);
+cudaError_t launch_chi_eval(const DevParams& P, const u64* u, uint32_t n, int* out, cudaStream_t st);
 cudaError_t launch_shoup(const DevParams& P, const u64* w, u64* ws, uint32_t polys, cudaStream_t st);
 // Butterflies per second of k_probe_butterfly (register-only ceiling).
 cudaError_t probe_butterfly(int sms, double* per_s);

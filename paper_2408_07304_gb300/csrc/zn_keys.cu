@@ -141,6 +141,18 @@ __global__ void k_sample(DevParams P, int kind, u64 seed, unsigned domain, unsig
   }
 }
 
+// chi's CDT step on given uniforms, by the shared-memory binary search of the
+// encryption path (a test hook for threshold boundaries).
+__global__ void k_chi_eval(DevParams P, const u64* __restrict__ u, uint32_t n, int* __restrict__ out) {
+  __shared__ u64 s_cdt[kCdt];
+  for (int j = threadIdx.x; j < kCdt; j += blockDim.x) s_cdt[j] = P.cdt[j];
+  __syncthreads();
+  for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < n; x += (size_t)gridDim.x * blockDim.x) {
+    const u64 v = u[x];
+    out[x] = cdt_search((unsigned)v, (unsigned)(v >> 32), s_cdt);
+  }
+}
+
 // ---------------------------------------------------------------- launchers
 
 template <class K>
@@ -221,6 +233,14 @@ cudaError_t launch_ntt_fwd(const DevParams& P, u64* data, uint32_t batch, u64* t
     }
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_chi_eval(const DevParams& P, const u64* u, uint32_t n, int* out, cudaStream_t st) {
+  size_t g = (n + 255) / 256;
+  if (g > 152 * 16) g = 152 * 16;
+  if (g < 1) g = 1;
+  k_chi_eval<<<(unsigned)g, 256, 0, st>>>(P, u, n, out);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_sample(const DevParams& P, int kind, u64 seed, unsigned domain, unsigned poly, unsigned prime,

@@ -57,6 +57,13 @@ def test_encoder_twiddles_bitwise(built, log_n):
     assert np.array_equal(im_.view(np.uint64), oim.view(np.uint64))
 
 
+@pytest.mark.parametrize("log_n", [4, 8, 12, 13, 14, 15])
+def test_encoder_twiddles_q62_equal(built, log_n):
+    c, s = api.zn_host_encoder_twiddles_q62(log_n)
+    oc, os_ = encoder.twiddles_q62(log_n)
+    assert np.array_equal(c, oc) and np.array_equal(s, os_)
+
+
 def test_cdt_thresholds_equal(built):
     assert api.zn_host_cdt() == list(sampler.cdt_thresholds())
 

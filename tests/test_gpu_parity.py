@@ -116,6 +116,22 @@ def test_ntt_large_sampled(log_n, bits):
     assert np.array_equal(api.as_u64(d), x)
 
 
+def test_chi_table_search_boundaries():
+    # the binary search of the encryption path equals -19 + #{j : U >= T_j} at
+    # every threshold, one below and one above it, the extremes and random U
+    from oracle import sampler as OS
+    ctx = gpu_ctx(10, (50,), 30)
+    T = [int(t) for t in OS.cdt_thresholds()]
+    us = {0, 1, 2 ** 64 - 1, 2 ** 63}
+    for t in T:
+        us.update({t - 1, t, t + 1})
+    us = sorted(v for v in us if 0 <= v < 2 ** 64)
+    rnd = np.random.default_rng(12).integers(0, 2 ** 63, 5000, dtype=np.uint64) * np.uint64(2) + np.uint64(1)
+    u = np.concatenate([np.array(us, dtype=np.uint64), rnd])
+    got = api.zn_chi_eval(ctx, torch.tensor(u.view(np.int64), device="cuda:0")).cpu().numpy()
+    assert np.array_equal(got, OS.cdt_lookup(u).astype(np.int32))
+
+
 # ------------------------------------------------------------------ encoder
 @pytest.mark.parametrize("log_n,ld,n_slots,lo,hi", [(4, 20, 8, -1, 1), (4, 20, 3, -1, 1), (10, 30, 512, -1, 1),
                                                     (10, 40, 37, -5, 5), (12, 30, 2048, -1, 1),
@@ -131,6 +147,28 @@ def test_encode_bit_exact(log_n, ld, n_slots, lo, hi):
     got = out.cpu().numpy()
     for b in range(3):
         assert np.array_equal(got[b], OE.encode(z[b], log_n, ld)), b
+
+
+@pytest.mark.parametrize("z", [np.array([[5e-324, -1e-310, 3e-300, 0.0]]), np.array([[1e9, -1.0, 1e-300, 2.5]]),
+                               np.array([[0.0, 0.0, -0.0]]), np.array([[1.0]]), np.array([[-2.0 ** -30] * 7]),
+                               np.array([[0.5, -0.5, 0.5, 1.5, -2.5, 3.5, 1e-17, 7.0]])])
+def test_encode_edge_inputs_bit_exact(z):
+    # subnormal, mixed-magnitude, all-zero, single-slot and tie-prone vectors
+    log_n, ld = 10, 30
+    ctx = gpu_ctx(log_n, (50,), ld)
+    out = api.ckks_encode(ctx, dev(z, torch.float64))
+    api.zn_sync_status(ctx)
+    assert np.array_equal(out.cpu().numpy()[0], OE.encode(z[0], log_n, ld))
+
+
+def test_encode_non_finite_latched():
+    ctx = gpu_ctx(10, (50,), 30)
+    for bad in (np.nan, np.inf, -np.inf):
+        api.ckks_encode(ctx, dev(np.array([[1.0, bad, 0.5]]), torch.float64))
+        with pytest.raises(api.ZincError) as e:
+            api.zn_sync_status(ctx)
+        assert e.value.status == api.ZN_EOVERFLOW
+    api.zn_sync_status(ctx)
 
 
 def test_encode_overflow_latched():

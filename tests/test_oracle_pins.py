@@ -6,6 +6,8 @@ dropped term, a wrong sign or index, or a transposed operand fails here.
 import math
 import os
 
+from fractions import Fraction
+
 import numpy as np
 import pytest
 
@@ -288,23 +290,110 @@ def test_twiddles_near_libm():
         assert re[(1 << log_n) // 2] == 0.0 and im[(1 << log_n) // 2] == -1.0
 
 
+@pytest.mark.parametrize("log_n", [4, 9])
+def test_twiddles_q62_correctly_rounded(log_n):
+    # C[k] = floor(2^62 cos(pi k/N) + 1/2), S[k] likewise with sin, against 200-bit mpmath
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.prec = 200
+    n = 1 << log_n
+    C, S = encoder.twiddles_q62(log_n)
+    for k in range(n):
+        x = mpmath.mpf(k) / n
+        assert int(C[k]) == int(mpmath.floor(mpmath.cospi(x) * 2 ** 62 + mpmath.mpf(1) / 2)), k
+        assert int(S[k]) == int(mpmath.floor(mpmath.sinpi(x) * 2 ** 62 + mpmath.mpf(1) / 2)), k
+
+
+def test_twiddles_q62_exact_points():
+    # the two twiddles whose products the kernels may skip are exact
+    for log_n in (4, 14):
+        C, S = encoder.twiddles_q62(log_n)
+        n = 1 << log_n
+        assert (C[0], S[0]) == (1 << 62, 0) and (C[n // 2], S[n // 2]) == (0, 1 << 62)
+        # |W| = 1 up to the quantisation (|C|, |S| off by <= 1/2 each)
+        mod2 = C.astype(object) ** 2 + S.astype(object) ** 2
+        assert all(abs(v - (1 << 124)) <= (1 << 63) + 1 for v in mod2)
+
+
 def test_slot_index_is_bijection():
     for log_n in (4, 10, 13):
         t = encoder.slot_index(log_n)
         assert sorted(t.tolist()) == list(range(1 << (log_n - 1)))
 
 
+@pytest.mark.parametrize("z", [np.array([1.0, -0.5, 0.25]), np.array([5e-324, -1e-310, 3e-300]),
+                               np.array([1e300, -1.0, 1e-300]), np.random.default_rng(4).uniform(-8, 8, 4096),
+                               np.array([-2.0 ** 40])])
+def test_block_scale_invariants(z):
+    # step 0: |Y_j - z_j 2^F| <= 1/2 exactly, sum |Y| < 2^59 + n/2, and the
+    # scale is the largest that keeps n max|z| 2^F <= 2^59 (n = N/2 slots)
+    log_n = 13
+    n = 1 << (log_n - 1)
+    F, Y = encoder.block_scale(z, log_n)
+    frac2 = Fraction(2)
+    for v, y in zip(z, Y):
+        assert abs(Fraction(float(v)) * frac2 ** F - y) <= Fraction(1, 2)
+    assert sum(abs(y) for y in Y) < 2 ** 59 + n / 2
+    M = Fraction(float(np.max(np.abs(z))))
+    assert n * M * frac2 ** F < 2 ** 59 <= n * M * frac2 ** (F + 1)
+
+
+def test_encode_zero_padding_invariant():
+    # appending zero slots changes nothing (batches pad vectors to a common length)
+    log_n, ld = 10, 30
+    z = np.random.default_rng(8).uniform(-3, 3, 37)
+    m = encoder.encode(z, log_n, ld)
+    for pad in (1, 100, 512 - 37):
+        assert np.array_equal(encoder.encode(np.concatenate([z, np.zeros(pad)]), log_n, ld), m)
+
+
+def _canonical(z, log_n, ld, mpmath):
+    """(2 Delta / N) Re sum_j z_j zeta^(-5^j k), k < N, at 60 digits."""
+    n = 1 << log_n
+    g = [pow(5, j, 2 * n) for j in range(len(z))]
+    out = []
+    for k in range(n):
+        acc = mpmath.mpf(0)
+        for j, v in enumerate(z):
+            acc += mpmath.mpf(float(v)) * mpmath.cospi(mpmath.mpf((g[j] * k) % (2 * n)) / n)
+        out.append(acc * 2 * mpmath.mpf(2) ** ld / n)
+    return out
+
+
+@pytest.mark.parametrize("log_n,ld,z", [
+    (4, 20, np.array([0.3, -0.7, 0.1, 0.9, -0.2, 0.5, -1.0, 0.25])),
+    (4, 40, np.array([1e-12, -3.0, 0.0])),
+    (5, 30, np.random.default_rng(6).uniform(-1, 1, 16)),
+    (6, 25, np.concatenate([np.random.default_rng(7).uniform(-100, 100, 5), [1e-9, -1e-20]])),
+    (6, 60, np.array([2.0 ** -1060, -2.0 ** -1050])),
+])
+def test_encode_vs_canonical_embedding_brute_force(log_n, ld, z):
+    # brute force on tiny rings: the unrounded fixed-point result is within the
+    # derived bound of the exact embedding, and m is its rounding (within 1/2 + bound)
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 60
+    exact = _canonical(z, log_n, ld, mpmath)
+    real = encoder.encode_real(z, log_n, ld)
+    m = encoder.encode(z, log_n, ld)
+    bound = encoder.encode_error_bound(z, log_n, ld)
+    for k in range(1 << log_n):
+        err = abs(mpmath.mpf(float(real[k])) - exact[k])
+        assert err <= bound * (1 + 1e-12) + abs(float(real[k])) * 2.0 ** -52, (k, err, bound)
+        assert abs(mpmath.mpf(int(m[k])) - exact[k]) <= 0.5 + bound * (1 + 1e-12) + 1e-9, k
+
+
 @pytest.mark.parametrize("c", [0.5, -0.75, 1.0 / 3.0])
 def test_encode_constant_closed_form(c):
-    # z_j = c for all j encodes to the constant polynomial rint(Delta c)
+    # z_j = c for all j encodes to the constant polynomial Delta c (up to rounding)
     log_n, ld = 12, 30
-    m = encoder.encode(np.full(1 << (log_n - 1), c), log_n, ld)
-    assert m[0] == np.rint(c * 2.0 ** ld) and not m[1:].any()
+    z = np.full(1 << (log_n - 1), c)
+    m = encoder.encode(z, log_n, ld)
+    tol = 0.5 + encoder.encode_error_bound(z, log_n, ld)
+    assert abs(m[0] - c * 2.0 ** ld) <= tol and np.max(np.abs(m[1:])) <= tol
 
 
 @pytest.mark.parametrize("j", [0, 1, 7, 1000])
 def test_encode_single_slot_closed_form(j):
-    # z = e_j encodes to m_k = rint((2 Delta / N) cos(pi 5^j k / N))
+    # z = e_j encodes to m_k = rnd((2 Delta / N) cos(pi 5^j k / N))
     log_n, ld = 12, 30
     n = 1 << log_n
     z = np.zeros(n // 2)
@@ -313,15 +402,18 @@ def test_encode_single_slot_closed_form(j):
     k = np.arange(n)
     e = (pow(5, j, 2 * n) * k) % (2 * n)
     ref = (2.0 * 2.0 ** ld / n) * np.cos(np.pi * e / n)
-    assert np.max(np.abs(m - ref)) <= 0.5 + 1e-6
+    assert np.max(np.abs(m - ref)) <= 0.5 + encoder.encode_error_bound(z, log_n, ld) + 1e-6
 
 
-@pytest.mark.parametrize("log_n,ld,n_slots", [(10, 30, 512), (12, 30, 2048), (12, 40, 700)])
+@pytest.mark.parametrize("log_n,ld,n_slots", [(10, 30, 512), (12, 30, 2048), (12, 40, 700), (4, 20, 8)])
 def test_encode_fft_vs_definition(log_n, ld, n_slots):
+    # against the FP64 direct sum; its own error is at most (n_s + 2) ulp-sized
+    # terms of the sum of |z| times the scale
     z = np.random.default_rng(log_n + n_slots).uniform(-1, 1, n_slots)
     real = encoder.encode_real(z, log_n, ld)
     direct = encoder.encode_direct(z, log_n, ld)
-    assert np.max(np.abs(real - direct)) <= encoder.encode_error_bound(z, log_n, ld)
+    direct_err = (n_slots + 2) * 2.0 ** -52 * np.sum(np.abs(z)) * 2.0 ** (ld + 1 - log_n)
+    assert np.max(np.abs(real - direct)) <= encoder.encode_error_bound(z, log_n, ld) + direct_err
 
 
 def test_encode_linear_and_decode_roundtrip():
@@ -331,13 +423,22 @@ def test_encode_linear_and_decode_roundtrip():
     m1, m2, m12 = (encoder.encode(z, log_n, ld) for z in (z1, z2, z1 + z2))
     assert np.max(np.abs(m12 - m1 - m2)) <= 2
     back = encoder.decode(m1, log_n, ld, 1024)
-    # rint error <= 1/2 per coefficient: |z - z'| <= N/2 / Delta (loose, deterministic)
+    # rounding error <= 1/2 per coefficient: |z - z'| <= N/2 / Delta (loose, deterministic)
     assert np.max(np.abs(back - z1)) < (1 << log_n) / 2 / 2.0 ** ld
+
+
+def test_encode_zero_and_empty():
+    assert not encoder.encode(np.zeros(5), 6, 30).any()
+    assert not encoder.encode(np.zeros(0), 6, 30).any()
 
 
 def test_encode_overflow_detected():
     with pytest.raises(OverflowError):
         encoder.encode(np.full(8, 2.0 ** 30), 4, 40)
+    with pytest.raises(OverflowError):
+        encoder.encode(np.array([1.0, np.nan]), 4, 20)
+    with pytest.raises(OverflowError):
+        encoder.encode(np.array([np.inf]), 4, 20)
 
 
 # ----------------------------------------------------------- Gen / Enc / Dec
