@@ -101,6 +101,16 @@ __device__ __forceinline__ void ct_bfly_relaxed(u64& x, u64& y, ulonglong2 w, u6
   y = a - t + 2 * q;
 }
 
+// A sum below 32q (relaxed, q < 2^59) or below 8q (Harvey) -> [0, q).
+template <bool RELAX>
+__device__ __forceinline__ u64 reduce_sum(u64 x, u64 q) {
+  if constexpr (RELAX) {
+    if (x >= 16 * q) x -= 16 * q;
+    if (x >= 8 * q) x -= 8 * q;
+  }
+  return reduce8(x, q);
+}
+
 // Output of a transform -> [0, q): Harvey range [0, 4q), relaxed range [0, 32q).
 template <bool RELAX>
 __device__ __forceinline__ u64 reduce_out(u64 x, u64 q) {
@@ -192,9 +202,14 @@ struct NttShape {
                           : LOGN == 12 ? 4 : LOGN == 13 ? 5 : 4;
 };
 
-template <int LOGN>
+// KM = 4: the layout of radix-16 pass schedules (parameters above); KM = 3:
+// the layout of radix-8 schedules (passes of 3 bits, one of 4 absorbing a
+// remainder of 1), i ^ ((i >> 1) & 15) ^ ((i >> 3) & 15), conflict-free for
+// those schedules at 2^10 <= N <= 2^13 by the same exhaustive check.
+template <int LOGN, int KM = 4>
 __host__ __device__ constexpr int swz(int i) {
   using S = NttShape<LOGN>;
+  if constexpr (KM == 3) return i ^ ((i >> 1) & 15) ^ ((i >> 3) & 15);
   return S::SA == S::SB ? (i ^ ((i >> S::SA) & 15)) : (i ^ ((i >> S::SA) & 15) ^ ((i >> S::SB) & 15));
 }
 // The swizzle is linear over GF(2): swz(a ^ b) = swz(a) ^ swz(b).  A group's
@@ -203,10 +218,14 @@ __host__ __device__ constexpr int swz(int i) {
 // One pass over index bits [LO, LO+K): each thread takes its groups of 2^K
 // elements (one group at a time, in registers), runs K butterfly stages and
 // writes the group back to the same shared-memory slots -- or, in the last
-// pass (LO == 0), hands every output to store(idx, x).  The twiddle of stage
-// bit b for index idx is tw[tmul * 2^(LOGN-1-b) + (idx >> (b+1))]; tmul = 1
-// for a full transform, 2 + h for half h of a transform of twice the size.
-template <int LOGN, int LOGPER, int LO, int K, bool RELAX, class Store>
+// pass (LO == 0), hands every output to store(idx, x): x reduced to [0, q),
+// or (RAW) as the butterflies left it, below the input bound plus 2q per
+// stage (relaxed) or below 4q (Harvey).  The twiddle of stage bit b for index
+// idx is tw[tmul * 2^(LOGN-1-b) + (idx >> (b+1))]; tmul = 1 for a full
+// transform, 2 + h for half h of a transform of twice the size.  KM selects
+// the shared-memory layout (swz).
+template <int LOGN, int LOGPER, int LO, int K, bool RELAX, class Store, int KM = 4, bool RAW = false,
+          bool STAGED = false>
 __device__ __forceinline__ void ntt_pass(u64* sm, int t, const ulonglong2* __restrict__ twp, int tmul, u64 q,
                                          Store& store) {
   using S = NttShape<LOGN, LOGPER>;
@@ -216,10 +235,10 @@ __device__ __forceinline__ void ntt_pass(u64* sm, int t, const ulonglong2* __res
     const int g = t + j * S::T;
     const int ghi = g >> LO;
     const int base = (g & ((1 << LO) - 1)) | (ghi << (LO + K));
-    const int sb = swz<LOGN>(base);
+    const int sb = swz<LOGN, KM>(base);
     u64 v[1 << K];
 #pragma unroll
-    for (int r = 0; r < (1 << K); ++r) v[r] = sm[sb ^ swz<LOGN>(r << LO)];
+    for (int r = 0; r < (1 << K); ++r) v[r] = sm[sb ^ swz<LOGN, KM>(r << LO)];
 #pragma unroll
     for (int s = K - 1; s >= 0; --s) {
       const ulonglong2* tws = twp + (tmul << (LOGN - 1 - LO - s)) + (ghi << (K - s - 1));
@@ -230,24 +249,43 @@ __device__ __forceinline__ void ntt_pass(u64* sm, int t, const ulonglong2* __res
         else ct_bfly(v[r], v[r + (1 << s)], __ldg(tws + (r >> (s + 1))), q);
       }
     }
-    if constexpr (LO == 0) {
+    if constexpr (LO == 0 && !STAGED) {
 #pragma unroll
-      for (int r = 0; r < (1 << K); ++r) store(base | r, reduce_out<RELAX>(v[r], q));
+      for (int r = 0; r < (1 << K); ++r) {
+        if constexpr (RAW) store(base | r, v[r]);
+        else store(base | r, reduce_out<RELAX>(v[r], q));
+      }
     } else {
 #pragma unroll
-      for (int r = 0; r < (1 << K); ++r) sm[sb ^ swz<LOGN>(r << LO)] = v[r];
+      for (int r = 0; r < (1 << K); ++r) sm[sb ^ swz<LOGN, KM>(r << LO)] = v[r];
     }
   }
 }
 
-// Passes of KM bits (radix 2^KM) from the top index bit down.
-template <int LOGN, int LOGPER, int HI, bool RELAX, class Store, int KM = NttShape<LOGN>::KMAX>
+// Passes of KM bits (radix 2^KM) over index bits [0, HI), from the top down
+// (HI < LOGN when a generator has already run the stages above HI).
+// STAGED: the last pass writes back to shared memory like the others and the
+// outputs are handed to store() in natural index order (consecutive lanes,
+// consecutive indices), which keeps the epilogue's global accesses coalesced
+// when the last pass owns several adjacent outputs per thread.
+template <int LOGN, int LOGPER, int HI, bool RELAX, class Store, int KM = NttShape<LOGN>::KMAX, bool RAW = false,
+          bool STAGED = false>
 __device__ __forceinline__ void ntt_chain(u64* sm, int t, const ulonglong2* twp, int tmul, u64 q, Store& store) {
   constexpr int K = HI < KM ? HI : KM;
   constexpr int LO = HI - K;
   __syncthreads();
-  ntt_pass<LOGN, LOGPER, LO, K, RELAX, Store>(sm, t, twp, tmul, q, store);
-  if constexpr (LO > 0) ntt_chain<LOGN, LOGPER, LO, RELAX, Store, KM>(sm, t, twp, tmul, q, store);
+  ntt_pass<LOGN, LOGPER, LO, K, RELAX, Store, KM, RAW, STAGED>(sm, t, twp, tmul, q, store);
+  if constexpr (LO > 0) {
+    ntt_chain<LOGN, LOGPER, LO, RELAX, Store, KM, RAW, STAGED>(sm, t, twp, tmul, q, store);
+  } else if constexpr (STAGED) {
+    __syncthreads();
+#pragma unroll 4
+    for (int idx = t; idx < (1 << LOGN); idx += NttShape<LOGN, LOGPER>::T) {
+      const u64 x = sm[swz<LOGN, KM>(idx)];
+      if constexpr (RAW) store(idx, x);
+      else store(idx, reduce_out<RELAX>(x, q));
+    }
+  }
 }
 
 // Forward negacyclic NTT of one length-2^LOGN polynomial by the block's
@@ -265,10 +303,11 @@ __device__ __forceinline__ void ntt_forward(u64* sm, const ulonglong2* twp, int 
 // threads that own this polynomial (several sub-groups may share one block;
 // all of them must execute the same sequence of transforms, because the
 // passes are separated by block-wide barriers).
-template <int LOGN, class Store, int LOGPER = 5, bool RELAX = false, int KM = NttShape<LOGN>::KMAX>
+template <int LOGN, class Store, int LOGPER = 5, bool RELAX = false, int KM = NttShape<LOGN>::KMAX,
+          bool RAW = false>
 __device__ __forceinline__ void ntt_forward_sub(u64* sm, int t, const ulonglong2* twp, int tmul, u64 q,
                                                 Store& store) {
-  ntt_chain<LOGN, LOGPER, LOGN, RELAX, Store, KM>(sm, t, twp, tmul, q, store);
+  ntt_chain<LOGN, LOGPER, LOGN, RELAX, Store, KM, RAW>(sm, t, twp, tmul, q, store);
 }
 
 // ------------------------------------------------------------- generators
@@ -323,15 +362,48 @@ __device__ __forceinline__ void gen_copy(u64* sm, const u64* __restrict__ a) {
 
 // Encoded message plus noise (int64) from the per-ciphertext scratch; thread t
 // of nt.
-template <int LOGN>
+template <int LOGN, int KM = 4>
 __device__ __forceinline__ void gen_i64(u64* sm, int t, int nt, const i64* __restrict__ a, u64 q, u64 mu) {
-  for (int k = t; k < (1 << LOGN); k += nt) sm[swz<LOGN>(k)] = reduce_signed(__ldg(a + k), q, mu);
+  for (int k = t; k < (1 << LOGN); k += nt) sm[swz<LOGN, KM>(k)] = reduce_signed(__ldg(a + k), q, mu);
 }
 
 // Small signed polynomial (int8) from the per-ciphertext scratch.
-template <int LOGN>
+template <int LOGN, int KM = 4>
 __device__ __forceinline__ void gen_i8(u64* sm, int t, int nt, const int8_t* __restrict__ a, u64 q) {
-  for (int k = t; k < (1 << LOGN); k += nt) sm[swz<LOGN>(k)] = small_res(__ldg(a + k), q);
+  for (int k = t; k < (1 << LOGN); k += nt) sm[swz<LOGN, KM>(k)] = small_res(__ldg(a + k), q);
+}
+
+// Generators that also run the transform's top stage (distance N/2, twiddle
+// tw[1]) on the pair (k, k + N/2), for radix-8 schedules whose bit count
+// leaves a remainder of one.  Outputs below 4q (Harvey) or 3q (relaxed).
+template <bool RELAX>
+__device__ __forceinline__ void bfly(u64& x, u64& y, ulonglong2 w, u64 q) {
+  if constexpr (RELAX) ct_bfly_relaxed(x, y, w, q);
+  else ct_bfly(x, y, w, q);
+}
+
+template <int LOGN, int KM, bool RELAX>
+__device__ __forceinline__ void gen_i64_top(u64* sm, int t, int nt, const i64* __restrict__ a, u64 q, u64 mu,
+                                            ulonglong2 w1) {
+  constexpr int H = (1 << LOGN) / 2;
+  for (int k = t; k < H; k += nt) {
+    u64 x = reduce_signed(__ldg(a + k), q, mu), y = reduce_signed(__ldg(a + k + H), q, mu);
+    bfly<RELAX>(x, y, w1, q);
+    sm[swz<LOGN, KM>(k)] = x;
+    sm[swz<LOGN, KM>(k + H)] = y;
+  }
+}
+
+template <int LOGN, int KM, bool RELAX>
+__device__ __forceinline__ void gen_i8_top(u64* sm, int t, int nt, const int8_t* __restrict__ a, u64 q,
+                                           ulonglong2 w1) {
+  constexpr int H = (1 << LOGN) / 2;
+  for (int k = t; k < H; k += nt) {
+    u64 x = small_res(__ldg(a + k), q), y = small_res(__ldg(a + k + H), q);
+    bfly<RELAX>(x, y, w1, q);
+    sm[swz<LOGN, KM>(k)] = x;
+    sm[swz<LOGN, KM>(k + H)] = y;
+  }
 }
 
 // ---------------------------------------------- generators, half transforms
@@ -390,21 +462,52 @@ __device__ __forceinline__ void gen_uniform_half(u64* sm, int h, u64 seed, unsig
   }
 }
 
-template <int LOGH>
+template <int LOGH, int KM = 4>
 __device__ __forceinline__ void gen_i64_half(u64* sm, int t, int nt, int h, const i64* __restrict__ a, u64 q, u64 mu,
                                              u64 w1, u64 w1s) {
   constexpr int HALF = 1 << LOGH;
   for (int k = t; k < HALF; k += nt)
-    sm[swz<LOGH>(k)] = first_stage(reduce_signed(__ldg(a + k), q, mu), reduce_signed(__ldg(a + k + HALF), q, mu), h,
-                                   w1, w1s, q);
+    sm[swz<LOGH, KM>(k)] = first_stage(reduce_signed(__ldg(a + k), q, mu), reduce_signed(__ldg(a + k + HALF), q, mu),
+                                       h, w1, w1s, q);
 }
 
-template <int LOGH>
+template <int LOGH, int KM = 4>
 __device__ __forceinline__ void gen_i8_half(u64* sm, int t, int nt, int h, const int8_t* __restrict__ a, u64 q, u64 w1,
                                             u64 w1s) {
   constexpr int HALF = 1 << LOGH;
   for (int k = t; k < HALF; k += nt)
-    sm[swz<LOGH>(k)] = first_stage(small_res(__ldg(a + k), q), small_res(__ldg(a + k + HALF), q), h, w1, w1s, q);
+    sm[swz<LOGH, KM>(k)] = first_stage(small_res(__ldg(a + k), q), small_res(__ldg(a + k + HALF), q), h, w1, w1s, q);
+}
+
+// Half generators that also run the half transform's top stage (slots k and
+// k + HALF/2, twiddle w2 = tw[2 + h]): four coefficients k + {0, 1, 2, 3} HALF/2
+// per loop trip.  Outputs below 4q (Harvey) or 6q (relaxed).
+template <int LOGH, int KM, bool RELAX>
+__device__ __forceinline__ void gen_i64_half2(u64* sm, int t, int nt, int h, const i64* __restrict__ a, u64 q, u64 mu,
+                                              ulonglong2 w1, ulonglong2 w2) {
+  constexpr int HALF = 1 << LOGH, Q2 = HALF / 2;
+  for (int k = t; k < Q2; k += nt) {
+    u64 x = first_stage(reduce_signed(__ldg(a + k), q, mu), reduce_signed(__ldg(a + k + HALF), q, mu), h, w1.x,
+                        w1.y, q);
+    u64 y = first_stage(reduce_signed(__ldg(a + k + Q2), q, mu), reduce_signed(__ldg(a + k + Q2 + HALF), q, mu), h,
+                        w1.x, w1.y, q);
+    bfly<RELAX>(x, y, w2, q);
+    sm[swz<LOGH, KM>(k)] = x;
+    sm[swz<LOGH, KM>(k + Q2)] = y;
+  }
+}
+
+template <int LOGH, int KM, bool RELAX>
+__device__ __forceinline__ void gen_i8_half2(u64* sm, int t, int nt, int h, const int8_t* __restrict__ a, u64 q,
+                                             ulonglong2 w1, ulonglong2 w2) {
+  constexpr int HALF = 1 << LOGH, Q2 = HALF / 2;
+  for (int k = t; k < Q2; k += nt) {
+    u64 x = first_stage(small_res(__ldg(a + k), q), small_res(__ldg(a + k + HALF), q), h, w1.x, w1.y, q);
+    u64 y = first_stage(small_res(__ldg(a + k + Q2), q), small_res(__ldg(a + k + Q2 + HALF), q), h, w1.x, w1.y, q);
+    bfly<RELAX>(x, y, w2, q);
+    sm[swz<LOGH, KM>(k)] = x;
+    sm[swz<LOGH, KM>(k + Q2)] = y;
+  }
 }
 
 template <int LOGH>

@@ -16,11 +16,20 @@ namespace zn {
 
 
 // Full transform (N <= 2^14).  Sub-group thread t; an inactive sub-group
-// runs the same barriers but touches no global memory.
+// runs the same barriers but touches no global memory.  The last NTT pass
+// hands its outputs over unreduced where the epilogue can absorb them: the
+// Shoup product pk*u-hat takes any 64-bit input, and a sum below 32q (relaxed:
+// 2q or q plus q + 2q*LOGN) or 8q (Harvey) is reduced once (reduce_sum).
+// Radix-8 schedules (KM = 3) with LOGN = 1 mod 3 run the top stage in the
+// generator and 3-bit passes over the rest, and stage the last pass through
+// shared memory (its threads own 8 adjacent outputs each).
 template <int LOGN, bool ZINC, int LOGPER, bool RELAX, int KM = 4>
 __device__ __forceinline__ void encrypt_unit_q(const DevParams& P, const EncArgs& A, int i, size_t b, u64* sm, int t,
                                                bool active) {
   using S = NttShape<LOGN, LOGPER>;
+  static_assert(!RELAX || 1 + 2 * LOGN + 2 <= 32, "relaxed sums must stay below 32q");
+  constexpr bool TOP = KM == 3 && LOGN % 3 == 1;
+  constexpr int HI = TOP ? LOGN - 1 : LOGN;
   const int L = P.L;
   const u64 q = P.q[i], mu = P.mu[i];
   const ulonglong2* tw = P.twp + (size_t)i * S::N;
@@ -30,53 +39,68 @@ __device__ __forceinline__ void encrypt_unit_q(const DevParams& P, const EncArgs
   const int8_t* sp = A.small + b * 2 * S::N;
   const u64* k0 = A.key + (size_t)i * S::N;
   const u64* k1 = k0 + (size_t)L * S::N;
+  auto load_small = [&](const int8_t* src) {
+    if (!active) return;
+    if constexpr (TOP) gen_i8_top<LOGN, KM, RELAX>(sm, t, S::T, src, q, __ldg(tw + 1));
+    else gen_i8<LOGN, KM>(sm, t, S::T, src, q);
+  };
+  auto load_me = [&]() {
+    if (!active) return;
+    if constexpr (TOP) gen_i64_top<LOGN, KM, RELAX>(sm, t, S::T, me, q, mu, __ldg(tw + 1));
+    else gen_i64<LOGN, KM>(sm, t, S::T, me, q, mu);
+  };
   if constexpr (!ZINC) {
     const u64* k0s = A.keys + (size_t)i * S::N;
     const u64* k1s = k0s + (size_t)L * S::N;
     // u-hat, then the two key products (kept lazily in [0, 2q) in the output)
-    if (active) gen_i8<LOGN>(sm, t, S::T, sp, q);
-    auto st_u = [&](int idx, u64 x) {
+    load_small(sp);
+    auto st_u = [&](int idx, u64 uh) {
       if (!active) return;
-      const u64 uh = x;
       c0[idx] = mul_shoup(uh, __ldg(k0 + idx), __ldg(k0s + idx), q);
       c1[idx] = mul_shoup(uh, __ldg(k1 + idx), __ldg(k1s + idx), q);
     };
-    ntt_forward_sub<LOGN, decltype(st_u), LOGPER, RELAX, KM>(sm, t, tw, 1, q, st_u);
+    ntt_chain<LOGN, LOGPER, HI, RELAX, decltype(st_u), KM, true, KM == 3>(sm, t, tw, 1, q, st_u);
     // m + e0 -> c0
     __syncthreads();
-    if (active) gen_i64<LOGN>(sm, t, S::T, me, q, mu);
+    load_me();
     auto st_0 = [&](int idx, u64 x) {
-      if (active) c0[idx] = reduce4(c0[idx] + x, q);
+      if (active) c0[idx] = reduce_sum<RELAX>(c0[idx] + x, q);
     };
-    ntt_forward_sub<LOGN, decltype(st_0), LOGPER, RELAX, KM>(sm, t, tw, 1, q, st_0);
+    ntt_chain<LOGN, LOGPER, HI, RELAX, decltype(st_0), KM, true, KM == 3>(sm, t, tw, 1, q, st_0);
     // e1 -> c1
     __syncthreads();
-    if (active) gen_i8<LOGN>(sm, t, S::T, sp + S::N, q);
+    load_small(sp + S::N);
     auto st_1 = [&](int idx, u64 x) {
-      if (active) c1[idx] = reduce4(c1[idx] + x, q);
+      if (active) c1[idx] = reduce_sum<RELAX>(c1[idx] + x, q);
     };
-    ntt_forward_sub<LOGN, decltype(st_1), LOGPER, RELAX, KM>(sm, t, tw, 1, q, st_1);
+    ntt_chain<LOGN, LOGPER, HI, RELAX, decltype(st_1), KM, true, KM == 3>(sm, t, tw, 1, q, st_1);
   } else {
-    if (active) gen_i64<LOGN>(sm, t, S::T, me, q, mu);
+    load_me();
     auto st_0 = [&](int idx, u64 x) {
-      if (active) c0[idx] = reduce4(__ldg(k0 + idx) + x, q);
+      if (active) c0[idx] = reduce_sum<RELAX>(__ldg(k0 + idx) + x, q);
     };
-    ntt_forward_sub<LOGN, decltype(st_0), LOGPER, RELAX, KM>(sm, t, tw, 1, q, st_0);
+    ntt_chain<LOGN, LOGPER, HI, RELAX, decltype(st_0), KM, true, KM == 3>(sm, t, tw, 1, q, st_0);
     __syncthreads();
-    if (active) gen_i8<LOGN>(sm, t, S::T, sp, q);
+    load_small(sp);
     auto st_1 = [&](int idx, u64 x) {
-      if (active) c1[idx] = reduce4(__ldg(k1 + idx) + x, q);
+      if (active) c1[idx] = reduce_sum<RELAX>(__ldg(k1 + idx) + x, q);
     };
-    ntt_forward_sub<LOGN, decltype(st_1), LOGPER, RELAX, KM>(sm, t, tw, 1, q, st_1);
+    ntt_chain<LOGN, LOGPER, HI, RELAX, decltype(st_1), KM, true, KM == 3>(sm, t, tw, 1, q, st_1);
   }
 }
 
 // N = 2^(LOGH+1): output half h of prime i (one limb exceeds shared memory).
+// Relaxed outputs start below 4q (the first stage; 6q when the generator also
+// runs the half's top stage) and stay below 4q + 2q*LOGH; the sums take them
+// unreduced only while that plus 2q is at most 32q (LOGH <= 13).
 template <int LOGH, bool ZINC, int LOGPER, bool RELAX, int KM = 4>
 __device__ __forceinline__ void encrypt_half_unit_q(const DevParams& P, const EncArgs& A, int i, int h, size_t b,
                                                     u64* sm, int t) {
   using S = NttShape<LOGH, LOGPER>;
   constexpr int N = 2 << LOGH, HALF = 1 << LOGH;
+  constexpr bool RAW = !RELAX || 4 + 2 * LOGH + 2 <= 32;
+  constexpr bool TOP = KM == 3 && LOGH % 3 == 1;
+  constexpr int HI = TOP ? LOGH - 1 : LOGH;
   const int L = P.L;
   const u64 q = P.q[i], mu = P.mu[i];
   const ulonglong2* tw = P.twp + (size_t)i * N;
@@ -90,32 +114,40 @@ __device__ __forceinline__ void encrypt_half_unit_q(const DevParams& P, const En
   const u64* k0 = A.key + (size_t)i * N + off;
   const u64* k1 = k0 + (size_t)L * N;
   const int tmul = 2 + h;
+  auto sum = [&](u64 a, u64 x) { return RAW ? reduce_sum<RELAX>(a + x, q) : reduce4(a + x, q); };
+  auto load_small = [&](const int8_t* src) {
+    if constexpr (TOP) gen_i8_half2<LOGH, KM, RELAX>(sm, t, S::T, h, src, q, w1p, __ldg(tw + tmul));
+    else gen_i8_half<LOGH, KM>(sm, t, S::T, h, src, q, w1, w1s);
+  };
+  auto load_me = [&]() {
+    if constexpr (TOP) gen_i64_half2<LOGH, KM, RELAX>(sm, t, S::T, h, me, q, mu, w1p, __ldg(tw + tmul));
+    else gen_i64_half<LOGH, KM>(sm, t, S::T, h, me, q, mu, w1, w1s);
+  };
   if constexpr (!ZINC) {
     const u64* k0s = A.keys + (size_t)i * N + off;
     const u64* k1s = k0s + (size_t)L * N;
-    gen_i8_half<LOGH>(sm, t, S::T, h, sp, q, w1, w1s);
-    auto st_u = [&](int idx, u64 x) {
-      const u64 uh = x;
+    load_small(sp);
+    auto st_u = [&](int idx, u64 uh) {
       c0[idx] = mul_shoup(uh, __ldg(k0 + idx), __ldg(k0s + idx), q);
       c1[idx] = mul_shoup(uh, __ldg(k1 + idx), __ldg(k1s + idx), q);
     };
-    ntt_forward_sub<LOGH, decltype(st_u), LOGPER, RELAX, KM>(sm, t, tw, tmul, q, st_u);
+    ntt_chain<LOGH, LOGPER, HI, RELAX, decltype(st_u), KM, true, KM == 3>(sm, t, tw, tmul, q, st_u);
     __syncthreads();
-    gen_i64_half<LOGH>(sm, t, S::T, h, me, q, mu, w1, w1s);
-    auto st_0 = [&](int idx, u64 x) { c0[idx] = reduce4(c0[idx] + x, q); };
-    ntt_forward_sub<LOGH, decltype(st_0), LOGPER, RELAX, KM>(sm, t, tw, tmul, q, st_0);
+    load_me();
+    auto st_0 = [&](int idx, u64 x) { c0[idx] = sum(c0[idx], x); };
+    ntt_chain<LOGH, LOGPER, HI, RELAX, decltype(st_0), KM, RAW, KM == 3>(sm, t, tw, tmul, q, st_0);
     __syncthreads();
-    gen_i8_half<LOGH>(sm, t, S::T, h, sp + N, q, w1, w1s);
-    auto st_1 = [&](int idx, u64 x) { c1[idx] = reduce4(c1[idx] + x, q); };
-    ntt_forward_sub<LOGH, decltype(st_1), LOGPER, RELAX, KM>(sm, t, tw, tmul, q, st_1);
+    load_small(sp + N);
+    auto st_1 = [&](int idx, u64 x) { c1[idx] = sum(c1[idx], x); };
+    ntt_chain<LOGH, LOGPER, HI, RELAX, decltype(st_1), KM, RAW, KM == 3>(sm, t, tw, tmul, q, st_1);
   } else {
-    gen_i64_half<LOGH>(sm, t, S::T, h, me, q, mu, w1, w1s);
-    auto st_0 = [&](int idx, u64 x) { c0[idx] = reduce4(__ldg(k0 + idx) + x, q); };
-    ntt_forward_sub<LOGH, decltype(st_0), LOGPER, RELAX, KM>(sm, t, tw, tmul, q, st_0);
+    load_me();
+    auto st_0 = [&](int idx, u64 x) { c0[idx] = sum(__ldg(k0 + idx), x); };
+    ntt_chain<LOGH, LOGPER, HI, RELAX, decltype(st_0), KM, RAW, KM == 3>(sm, t, tw, tmul, q, st_0);
     __syncthreads();
-    gen_i8_half<LOGH>(sm, t, S::T, h, sp, q, w1, w1s);
-    auto st_1 = [&](int idx, u64 x) { c1[idx] = reduce4(__ldg(k1 + idx) + x, q); };
-    ntt_forward_sub<LOGH, decltype(st_1), LOGPER, RELAX, KM>(sm, t, tw, tmul, q, st_1);
+    load_small(sp);
+    auto st_1 = [&](int idx, u64 x) { c1[idx] = sum(__ldg(k1 + idx), x); };
+    ntt_chain<LOGH, LOGPER, HI, RELAX, decltype(st_1), KM, RAW, KM == 3>(sm, t, tw, tmul, q, st_1);
   }
 }
 
