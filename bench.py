@@ -34,6 +34,18 @@ METRIC = "encryptions/s, vanilla CKKS vs Zinc, at N=2^14, 1 GB300; HBM roofline 
 UNIT = "encryptions/s"
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one encrypt
+# launch -- 256 ciphertexts of the throughput workload -- from the ncu capture
+# summarised in profiles/k_encrypt_half_n16384_l8.md, keyed by the kernel it
+# was taken on.  Valid only while that kernel is unchanged and selected.
+NCU_TRAFFIC = {
+    ("throughput", "k_encrypt_half<13,vanilla,radix-8,3 blocks/SM>", 256): 55.218944e6 + 527.176704e6,
+    ("throughput", "k_encrypt_half<13,Zinc,radix-8,3 blocks/SM>", 256): 42.100992e6 + 495.347456e6,
+}
+VARIANT_KERNEL = {6: "k_encrypt_half<13,{mode},radix-8,3 blocks/SM>",
+                  7: "k_encrypt_half<13,{mode},radix-8,3 blocks/SM,ciphertext-major>"}
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -249,9 +261,13 @@ def run_ours(args, w):
     bfly_z = chunk_cts * modmuls_per_ct(w, True)
     achieved = bfly_v / (kv_avg / 1e3) / 1e9
     hbm_achieved = chunk_cts * ct_bytes / (kv_avg / 1e3) / 1e9
+    kname = VARIANT_KERNEL.get(tune[0], "k_encrypt<{mode}> variant %d" % tune[0]) if w.log_n == 14 else \
+        f"k_encrypt<{w.log_n},{{mode}}> variant {tune[0]}"
+    traffic = NCU_TRAFFIC.get((w.name, kname.format(mode="vanilla"), int(round(chunk_cts))))
     roofline = {"bound": "alu", "achieved": achieved, "peak": derived_peak, "unit": "Gbutterfly/s",
-                "frac": achieved / derived_peak, "traffic": None,
-                "kernel": f"k_encrypt<{w.log_n},vanilla> variant {tune[0]}",
+                "frac": achieved / derived_peak, "traffic": traffic,
+                "traffic_unit": "DRAM bytes per launch (ncu)", "algorithmic_bytes": chunk_cts * ct_bytes,
+                "kernel": kname.format(mode="vanilla") + f" (variant {tune[0]})",
                 "peak_source": "derived: SMs x 64 IMAD/clk x 2.07 GHz / 10 IMAD per butterfly",
                 "probe_peak": probe, "probe_frac": achieved / probe,
                 "zinc_kernel_achieved": bfly_z / (kz_avg / 1e3) / 1e9,
