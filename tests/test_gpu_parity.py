@@ -354,6 +354,9 @@ def test_invalid_arguments():
 def test_launch_variants_bit_identical(log_n, bits, ld):
     """Every launch shape the autotuner may choose gives the same ciphertexts."""
     ctx = gpu_ctx(log_n, bits, ld)
+    # a new context starts at the radix-8 kernels where they apply
+    default = api.zn_get_variant(ctx)
+    assert default == (6 if 10 <= log_n <= 14 else 0)
     _, pk = gpu_keys(log_n, bits, ld, 1)
     zc = gpu_cache(log_n, bits, ld, 1, 2)
     w = workloads.small(log_n, bits, ld, 3, (1 << log_n) // 2 - 5, seed=8)
@@ -369,7 +372,7 @@ def test_launch_variants_bit_identical(log_n, bits, ld):
     chosen, ms = api.zn_autotune(ctx, pk, zc, 8)
     assert chosen in range(api.VARIANTS) and all(m > 0 for m in ms)
     assert api.zn_get_variant(ctx) == chosen
-    api.zn_set_variant(ctx, 0)
+    api.zn_set_variant(ctx, default)
 
 
 @pytest.mark.parametrize("zinc", [False, True])
@@ -386,6 +389,7 @@ def test_multipoly_variant_misaligned_output(zinc):
     z = dev(workloads.slots(w), torch.float64)
     idx = dev(np.array([1, 7]), torch.int64)
     shape = (2, 2, len(bits), 1 << log_n)
+    default = api.zn_get_variant(ctx)
     api.zn_set_variant(ctx, 0)
     ref = fn(ctx, key, z, 3, idx)
     api.zn_set_variant(ctx, 2)                          # kind 1, prime-major
@@ -394,5 +398,5 @@ def test_multipoly_variant_misaligned_output(zinc):
     off = flat[1:].view(shape)
     assert off.data_ptr() % 16 == 8
     fn(ctx, key, z, 3, idx, out=off)
-    api.zn_set_variant(ctx, 0)
+    api.zn_set_variant(ctx, default)
     assert torch.equal(aligned, ref) and torch.equal(off, ref)
