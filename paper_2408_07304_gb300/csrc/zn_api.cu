@@ -724,11 +724,11 @@ int ckks_add(zn_ctx* c, const uint64_t* a, const uint64_t* b, uint32_t batch, ui
 struct zn_batch {
   int device;
   int sms;
-  uint32_t n_prep, n_packets;
+  uint32_t n_prep, n_packets, n_small;   // packets: [rings up to 2^14 | 2^15]
   zn::JobDesc* d_jobs;
   zn::PrepUnit* d_units;
   zn::EncPacket* d_packets;
-  int* d_counters;        // [2]: prep, encrypt
+  int* d_counters;        // [3]: prep, encrypt (up to 2^14), encrypt (2^15)
   i64* d_me;
   int8_t* d_small;
   cudaGraphExec_t exec;
@@ -780,10 +780,10 @@ int zn_batch_create(const zn_job* jobs, uint32_t n_jobs, int device, zn_batch** 
   int rc = ZN_OK;
   if ((me_words && cudaMalloc(&b->d_me, sizeof(i64) * me_words) != cudaSuccess) ||
       (small_bytes && cudaMalloc(&b->d_small, small_bytes) != cudaSuccess) ||
-      cudaMalloc(&b->d_counters, 2 * sizeof(int)) != cudaSuccess)
+      cudaMalloc(&b->d_counters, 3 * sizeof(int)) != cudaSuccess)
     rc = ZN_ENOMEM;
   std::vector<zn::PrepUnit> units;
-  std::vector<zn::EncPacket> packets;
+  std::vector<zn::EncPacket> packets, big;
   size_t me_off = 0, sm_off = 0;
   for (uint32_t j = 0; j < n_jobs && !rc; ++j) {
     const zn_job& J = jobs[j];
@@ -813,18 +813,21 @@ int zn_batch_create(const zn_job* jobs, uint32_t n_jobs, int device, zn_batch** 
     const zn_job& J = jobs[j];
     const uint32_t log_n = J.ctx->prm.log_n, L = J.ctx->L;
     for (uint32_t k = 0; k < J.count; ++k) units.push_back({j, k});
-    if (log_n == 15) {
+    if (log_n >= 14) {                 // output halves, one per block
+      std::vector<zn::EncPacket>& list = log_n == 15 ? big : packets;
       for (uint32_t i = 0; i < L; ++i)
         for (uint32_t k = 0; k < J.count; ++k)
-          for (uint8_t h = 0; h < 2; ++h) packets.push_back({j, k, (uint16_t)i, 1, h});
-    } else {
-      const uint32_t per = 1u << (14 - log_n);
+          for (uint8_t h = 0; h < 2; ++h) list.push_back({j, k, (uint16_t)i, 1, h});
+    } else {                           // 2^(13 - log_n) limbs per 256-thread block
+      const uint32_t per = 1u << (13 - log_n);
       for (uint32_t i = 0; i < L; ++i)
         for (uint32_t k = 0; k < J.count; k += per)
           packets.push_back({j, k, (uint16_t)i, (uint8_t)std::min(per, J.count - k), 0});
     }
   }
   b->n_prep = (uint32_t)units.size();
+  b->n_small = (uint32_t)packets.size();
+  packets.insert(packets.end(), big.begin(), big.end());     // [small list | 2^15 list]
   b->n_packets = (uint32_t)packets.size();
   if (!rc && (cudaMalloc(&b->d_jobs, sizeof(zn::JobDesc) * n_jobs) != cudaSuccess ||
               (b->n_prep && cudaMalloc(&b->d_units, sizeof(zn::PrepUnit) * b->n_prep) != cudaSuccess) ||
@@ -847,11 +850,14 @@ int zn_batch_create(const zn_job* jobs, uint32_t n_jobs, int device, zn_batch** 
 }
 
 static int batch_enqueue(zn_batch* b, cudaStream_t st) {
-  ZN_CUDA(cudaMemsetAsync(b->d_counters, 0, 2 * sizeof(int), st));
+  ZN_CUDA(cudaMemsetAsync(b->d_counters, 0, 3 * sizeof(int), st));
   if (b->n_prep)
     ZN_CUDA(zn::launch_batch_prep(b->d_jobs, b->d_units, (int)b->n_prep, b->d_counters, b->sms, st));
-  if (b->n_packets)
-    ZN_CUDA(zn::launch_batch_encrypt(b->d_jobs, b->d_packets, (int)b->n_packets, b->d_counters + 1, b->sms, st));
+  if (b->n_small)
+    ZN_CUDA(zn::launch_batch_encrypt(b->d_jobs, b->d_packets, (int)b->n_small, b->d_counters + 1, b->sms, false, st));
+  if (b->n_packets > b->n_small)
+    ZN_CUDA(zn::launch_batch_encrypt(b->d_jobs, b->d_packets + b->n_small, (int)(b->n_packets - b->n_small),
+                                     b->d_counters + 2, b->sms, true, st));
   return ZN_OK;
 }
 
