@@ -12,6 +12,13 @@ called (c0, c1) and (pk0, pk1) here; c0 carries the message.
 * Enc_z (Algorithm 1, Eq. 9): c = zero + m; e1', e2' <- chi;
   c' = (c0 + e1', c1 + e2').
 * Dec (Eq. 10): c0 + c1 s (mod q).
+* Modulus-switched vanilla Enc (the paper's SEAL implementation, Sections
+  "System Implementation" and "Theoretical Analysis"): the last prime of the
+  chain is the special prime p; Enc computes (pk0 u + e0, pk1 u + e1) at the
+  key level (every prime), then divides and rounds by p -- for each data
+  prime q_i, c'_i = (c_i + h - r) p^-1 mod q_i with h = floor(p/2) and
+  r = (c_p + h) mod p, i.e. c' = floor((c + h) / p) mod Q -- and adds m at
+  the data level (every prime but p).
 
 Everything is computed in the coefficient domain with schoolbook negacyclic
 products; the stored ciphertexts, keys and cache are the NTT images of those
@@ -168,6 +175,48 @@ def ct_ntt_sampled(P: Params, ct, positions):
 def pk_ntt(P: Params, K: Keys):
     """Public key as the library lays it out: uint64 [2][L][N], NTT form."""
     return np.stack([np.stack(to_ntt(P, K.pk0)), np.stack(to_ntt(P, K.pk1))])
+
+
+def data_params(P: Params) -> Params:
+    """The data level of a key-level chain: every prime but the last (the special prime)."""
+    return Params(P.log_n, P.bits[:-1], P.log2_delta, primes=list(P.primes[:-1]), psis=list(P.psis[:-1]))
+
+
+def mod_switch_coeff(P: Params, polys):
+    """Divide and round by the special prime p = P.primes[-1]: per data prime
+    q_i, (c_i + h - r) p^-1 mod q_i with h = floor(p/2), r = (c_p + h) mod p
+    (coefficient domain, a per-prime list of residue vectors in, data-level list out)."""
+    p = P.primes[-1]
+    h = p // 2
+    r = (polys[-1].astype(object) + h) % p
+    out = []
+    for i, q in enumerate(P.primes[:-1]):
+        pinv = pow(p, -1, q)
+        out.append((((polys[i].astype(object) + h - r) % q) * pinv % q).astype(np.uint64))
+    return out
+
+
+def encrypt_ms_coeff(P: Params, K: Keys, z, seed: int, ct_index: int, domain=DOM_ENC) -> CoeffCt:
+    """Modulus-switched vanilla Enc: (pk0 u + e0, pk1 u + e1) at the key level,
+    divided and rounded by the special prime, then + m at the data level.  The
+    randomness (u, e0, e1) is that of encrypt_coeff with the same arguments."""
+    n = P.n
+    m = encoder.encode(z, P.log_n, P.log2_delta) if z is not None else np.zeros(n, dtype=np.int64)
+    u = sampler.sample_ternary(n, seed, domain, 0, ct_index)
+    e0 = sampler.sample_gaussian(n, seed, domain, 1, ct_index)
+    e1 = sampler.sample_gaussian(n, seed, domain, 2, ct_index)
+    zero = np.zeros(n, dtype=np.int64)
+    key_level = _enc_with(P, K, zero, u, e0, e1)          # pk u + e at every prime
+    c0 = mod_switch_coeff(P, key_level.c0)
+    c1 = mod_switch_coeff(P, key_level.c1)
+    Pd = data_params(P)
+    c0 = [_add_small(c, m, q) for c, q in zip(c0, Pd.primes)]
+    return CoeffCt(c0=c0, c1=c1, m=m, u=u, e0=e0, e1=e1)
+
+
+def zinc_precompute_ms_coeff(P: Params, K: Keys, seed: int) -> CoeffCt:
+    """The cached Enc(0) at the data level, made by modulus-switched Enc (cache domain, ct_index 0)."""
+    return encrypt_ms_coeff(P, K, None, seed, 0, domain=DOM_CACHE)
 
 
 def decrypt_coeff(P: Params, K: Keys, c0, c1):

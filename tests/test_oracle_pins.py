@@ -523,6 +523,103 @@ def test_decrypt_decode_and_homomorphism():
     assert np.max(np.abs(ckks.decrypt_decode(P, K, s0, s1, 512) - (za + zb))) < 2 * bound
 
 
+# ---------------------------------------- modulus-switched (SEAL-ordered) Enc
+def _crt(residues, primes):
+    M = 1
+    for q in primes:
+        M *= q
+    x = 0
+    for r, q in zip(residues, primes):
+        Mi = M // q
+        x += int(r) * Mi * pow(Mi, -1, q)
+    return x % M, M
+
+
+def test_mod_switch_is_divide_and_round():
+    # per coefficient, c' = floor((C + floor(p/2)) / p) mod Q for the CRT value
+    # C in [0, Q p), checked with Python big integers -- including C = k p + h
+    # (rounds down) and k p + h + 1 (rounds up), the nearest-integer boundary
+    P = ckks.Params(4, (40, 41, 50), 20)
+    p, qs = P.primes[-1], P.primes[:-1]
+    Q = qs[0] * qs[1]
+    h = p // 2
+    rng = np.random.default_rng(3)
+    Cs = [int(v) for v in rng.integers(0, 2 ** 62, 10)]
+    Cs = [(c * 977 + 12345) % (Q * p) for c in Cs]
+    Cs += [0, p - 1, 5 * p + h, 5 * p + h + 1, Q * p - 1, (Q - 1) * p + h + 1]
+    Cs = Cs[:16]
+    polys = [np.array([C % q for C in Cs], dtype=np.uint64) for q in P.primes]
+    out = ckks.mod_switch_coeff(P, polys)
+    for k, C in enumerate(Cs):
+        want = ((C + h) // p) % Q
+        got, _ = _crt([out[0][k], out[1][k]], qs)
+        assert got == want, (k, C)
+    assert int(out[0][10]) == 0 and int(out[0][12]) == 5 and int(out[0][13]) == 6
+
+
+@pytest.fixture(scope="module")
+def small3():
+    P = ckks.Params(6, (40, 41, 50), 20)
+    K = ckks.keygen(P, 11)
+    return P, K
+
+
+@pytest.mark.parametrize("bits,ld", [((40, 41, 50), 20), ((40, 41, 30), 35)])
+def test_modswitch_noise_identity(bits, ld):
+    # p (Dec(c') - m) = v + (h - r0) + (h - r1) s exactly, v = e u + e0 + e1 s the
+    # key-level noise, r_j = (c_j,p + h) mod p from the special-prime component;
+    # the second set has m much larger than p (m enters only after the division)
+    P = ckks.Params(6, bits, ld)
+    K = ckks.keygen(P, 11)
+    Pd = ckks.data_params(P)
+    p = P.primes[-1]
+    h = p // 2
+    z = np.random.default_rng(2).uniform(-1, 1, 16)
+    ct = ckks.encrypt_ms_coeff(P, K, z, seed=5, ct_index=9)
+    v = _small_conv(K.e, ct.u, P.n) + ct.e0 + _small_conv(ct.e1, K.s, P.n)
+    cp0 = ring.negacyclic_mul_small(K.pk0[-1], ct.u, p).astype(object) + ct.e0.astype(object)
+    cp1 = ring.negacyclic_mul_small(K.pk1[-1], ct.u, p).astype(object) + ct.e1.astype(object)
+    r0 = (cp0 + h) % p
+    r1 = (cp1 + h) % p
+    d1 = [h - int(x) for x in r1]
+    d1s = [0] * P.n                                   # (h - r1) * s, negacyclic, exact
+    for i in range(P.n):
+        for j in range(P.n):
+            if K.s[j]:
+                k = i + j
+                sgn = 1 if k < P.n else -1
+                d1s[k % P.n] += sgn * d1[i] * int(K.s[j])
+    rhs = [int(v[k]) + (h - int(r0[k])) + d1s[k] for k in range(P.n)]
+    dec = ckks.decrypt_coeff(Pd, K, ct.c0, ct.c1)
+    cen = ckks.crt_centered(Pd, dec, Pd.n_primes)
+    assert [p * (cen[k] - int(ct.m[k])) for k in range(P.n)] == rhs
+    # and therefore |Dec - m| <= (19 (2N + 1)) / p + (1 + N) / 2
+    assert max(abs(cen[k] - int(ct.m[k])) for k in range(P.n)) <= (1 + P.n) / 2 + 1
+
+
+def test_modswitch_randomness_is_vanilla(small3):
+    # the same (u, e0, e1) as vanilla Enc with the same seed and index; data level = all primes but the last
+    P, K = small3
+    a = ckks.encrypt_ms_coeff(P, K, np.ones(3), seed=4, ct_index=7)
+    b = ckks.encrypt_coeff(P, K, np.ones(3), seed=4, ct_index=7)
+    assert np.array_equal(a.u, b.u) and np.array_equal(a.e0, b.e0) and np.array_equal(a.e1, b.e1)
+    Pd = ckks.data_params(P)
+    assert Pd.primes == P.primes[:-1] and len(a.c0) == len(a.c1) == Pd.n_primes
+
+
+def test_zinc_on_modswitched_cache(small3):
+    # Enc_z over a modulus-switched cache: Dec = m + e1' + e2' s + (the cache's Dec), exactly
+    P, K = small3
+    Pd = ckks.data_params(P)
+    zero = ckks.zinc_precompute_ms_coeff(P, K, seed=2)
+    z = np.random.default_rng(5).uniform(-1, 1, 32)
+    ct = ckks.zinc_encrypt_coeff(Pd, zero, z, seed=5, ct_index=3)
+    dz = ckks.crt_centered(Pd, ckks.decrypt_coeff(Pd, K, zero.c0, zero.c1), Pd.n_primes)
+    dc = ckks.crt_centered(Pd, ckks.decrypt_coeff(Pd, K, ct.c0, ct.c1), Pd.n_primes)
+    e = ct.e1p + _small_conv(ct.e2p, K.s, P.n)
+    assert [dc[k] - dz[k] for k in range(P.n)] == [int(ct.m[k]) + int(e[k]) for k in range(P.n)]
+
+
 def test_ntt_form_ciphertext_matches_sampled(small):
     P, K = small
     ct = ckks.encrypt_coeff(P, K, np.ones(3), seed=1, ct_index=0)
