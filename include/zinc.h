@@ -172,6 +172,40 @@ int zinc_encrypt_noalloc(zn_ctx* ctx, const zn_zcache* zc, const double* slots, 
                          uint32_t batch, uint64_t seed, const uint64_t* ct_index, uint64_t* ct,
                          void* stream);
 
+/* ------------------------- special prime and modulus switching (SEAL order)
+ *
+ * The paper's measurements ran SEAL (Section "System Implementation"), whose
+ * public-key encryption works at the key level -- the data primes plus one
+ * special prime p -- and then divides by p and rounds (modulus switching)
+ * before the message is added; Section "Theoretical Analysis" counts the
+ * resulting transforms.  Here a key-level context holds the whole chain
+ * q_0..q_{L-1} (L >= 2) and its LAST prime is the special prime p; the data
+ * level is q_0..q_{L-2}, and a context created from the same parameters
+ * without the last bit size holds exactly those primes (the chain rule works
+ * left to right).
+ *
+ * Modulus-switched vanilla encryption: u <- R_2, e0, e1 <- chi (domain 0,
+ * exactly the samples of ckks_encrypt with the same seed and ct_index);
+ * c_j = pk_j*u + e_j over the key level, then per coefficient
+ * c'_j = floor((c_j + floor(p/2)) / p) mod (q_0 ... q_{L-2}) -- computed per
+ * data prime as (c_{j,i} + h - r_j) p^-1 mod q_i, r_j = (c_{j,p} + h) mod p --
+ * and finally c'_0 += m.  pk: a key of ctx (the key level); slots and
+ * ct_index as ckks_encrypt; ct: device uint64 [batch][2][L-1][N], NTT form,
+ * at the data level.  Decryption with the same secret key at the data level
+ * (import it into the data-level context) leaves m + v/p + rounding noise
+ * below (N + 1)/2 + 1 in magnitude per coefficient.  ZN_EINVAL if L < 2.
+ * Scratch comes from the context's pool. */
+int ckks_encrypt_ms(zn_ctx* ctx, const zn_pk* pk, const double* slots, uint32_t n_slots, uint32_t batch,
+                    uint64_t seed, const uint64_t* ct_index, uint64_t* ct, void* stream);
+
+/* Zinc precomputation over a modulus-switched Enc(0): the cached zero is
+ * ckks_encrypt_ms of the zero plaintext (domain 3, ct_index 0) under pk of
+ * the key-level ctx, and the cache belongs to data_ctx -- a context on the
+ * same device with the same log_n and log2_delta whose primes are ctx's first
+ * L-1 (ZN_EINVAL otherwise).  zinc_encrypt(data_ctx, cache, ...) then runs
+ * Algorithm 1 at the data level.  Synchronous. */
+int zinc_precompute_ms(zn_ctx* ctx, const zn_pk* pk, uint64_t seed, zn_ctx* data_ctx, zn_zcache** out);
+
 /* Host memory in, host memory out: copies slot vectors and ct indices to the
  * device, encrypts -- vanilla (Eq. 8) under pk when zc is NULL, Zinc
  * (Algorithm 1) under zc otherwise (pass exactly one) -- and copies the
@@ -296,10 +330,17 @@ int zn_autotune(zn_ctx* ctx, const zn_pk* pk, const zn_zcache* zc, uint32_t batc
 /* ---------------------------------------------------- launch timing (bench) */
 
 /* Kernel kinds that can be timed. */
-enum { ZN_TIME_ENCODE = 0, ZN_TIME_ENCRYPT = 1, ZN_TIME_ZINC = 2, ZN_TIME_KINDS = 3 };
+enum {
+  ZN_TIME_ENCODE = 0,      /* prep (encode + sampling), every encryption form  */
+  ZN_TIME_ENCRYPT = 1,     /* vanilla encryption kernel                        */
+  ZN_TIME_ZINC = 2,        /* Zinc encryption kernel                           */
+  ZN_TIME_MS_SPECIAL = 3,  /* modulus-switched vanilla: special-prime kernels  */
+  ZN_TIME_MS_DATA = 4,     /* modulus-switched vanilla: data-prime kernel      */
+  ZN_TIME_KINDS = 5
+};
 
-/* on != 0: every later encode / vanilla-encrypt / Zinc-encrypt kernel launch
- * of this context is bracketed by CUDA events recorded on its launch stream.
+/* on != 0: every later kernel launch of the kinds above in this context is
+ * bracketed by CUDA events recorded on its launch stream.
  * Recording stays on until switched off; on = 0 also discards pending
  * records. */
 int zn_timing_enable(zn_ctx* ctx, int on);

@@ -63,6 +63,8 @@ _SIGS = {
     "zn_zcache_import": (_i32, [_vp, _vp, _pp]),
     "zinc_encrypt": (_i32, [_vp, _vp, _vp, _u32, _u32, _u64, _vp, _vp, _vp]),
     "zinc_encrypt_noalloc": (_i32, [_vp, _vp, _vp, _u32, _u32, _u64, _vp, _vp, _vp]),
+    "ckks_encrypt_ms": (_i32, [_vp, _vp, _vp, _u32, _u32, _u64, _vp, _vp, _vp]),
+    "zinc_precompute_ms": (_i32, [_vp, _vp, _u64, _vp, _pp]),
     "ckks_decrypt": (_i32, [_vp, _vp, _vp, _u32, _vp, _vp]),
     "ckks_decrypt_decode": (_i32, [_vp, _vp, _vp, _u32, _u32, _vp, _vp]),
     "ckks_add": (_i32, [_vp, _vp, _vp, _u32, _vp, _vp]),
@@ -334,6 +336,38 @@ def zinc_encrypt_noalloc(ctx, zc, slots, seed, ct_index, out, stream=None):
     return out
 
 
+def data_level(ctx):
+    """The data-level context of a key-level one: the same ring and scale, the
+    chain without its last (special) prime."""
+    if ctx.L < 2:
+        raise ZincError(ZN_EINVAL, "data_level")
+    return Context(ctx.log_n, ctx.prime_bits[:-1], ctx.log2_delta, ctx.device)
+
+
+def ckks_encrypt_ms(ctx, pk, slots, seed, ct_index, out=None, stream=None):
+    """Modulus-switched vanilla encryption (SEAL's order) under a key-level pk:
+    CUDA float64 [B, n_slots] -> int64 [B, 2, L-1, N] at the data level."""
+    import torch
+    B, ns = slots.shape
+    shape = (B, 2, ctx.L - 1, ctx.n)
+    out = _out(out, shape, torch.int64, slots.device)
+    _dev(slots, torch.float64, None, "slots")
+    _dev(ct_index, torch.int64, (B,), "ct_index")
+    _dev(out, torch.int64, shape, "out")
+    _check(lib().ckks_encrypt_ms(ctx.handle, pk.handle, slots.data_ptr(), ns, B, seed, ct_index.data_ptr(),
+                                 out.data_ptr(), _stream(stream)), "ckks_encrypt_ms")
+    return out
+
+
+def zinc_precompute_ms(ctx, pk, seed, data_ctx):
+    """Zinc cache made by modulus-switched Enc(0) under the key-level pk; it
+    belongs to data_ctx (see data_level) and serves zinc_encrypt there."""
+    h = ctypes.c_void_p()
+    _check(lib().zinc_precompute_ms(ctx.handle, pk.handle, seed, data_ctx.handle, ctypes.byref(h)),
+           "zinc_precompute_ms")
+    return ZincCache(data_ctx, h)
+
+
 def zn_encrypt_host(ctx, key, slots, seed, ct_index, out, chunk=0):
     """Host-to-host encryption (pipelined copies + kernels).  key: PublicKey
     (vanilla) or ZincCache (Zinc); slots: CPU float64 [B, n_slots]; ct_index:
@@ -513,7 +547,7 @@ def zn_probe_butterfly(device=0):
     return r.value
 
 
-TIME_ENCODE, TIME_ENCRYPT, TIME_ZINC = 0, 1, 2
+TIME_ENCODE, TIME_ENCRYPT, TIME_ZINC, TIME_MS_SPECIAL, TIME_MS_DATA = 0, 1, 2, 3, 4
 
 
 def zn_timing_enable(ctx, on=True):

@@ -28,6 +28,7 @@ struct zn_ctx {
   double* d_etw;      // [2][N] decoder twiddles, then [N] encoder Q62 pairs
   int* d_slot;        // [N/2]
   unsigned* d_status;
+  u64 pinv[ZN_MAX_PRIMES], pinvs[ZN_MAX_PRIMES];   // p^-1 mod q_i (p the last prime), Shoup companions
   cudaMemPool_t pool; // stream-ordered scratch (prep outputs)
   int variant;        // encryption launch shape (zn_autotune)
   cudaStream_t hs[3]; // internal streams of zn_encrypt_host (created on first use)
@@ -43,6 +44,9 @@ struct zn_pk {
   uint32_t tag = kTagPk;
   zn_ctx* ctx;
   u64* d;    // [2][L][N] then Shoup companions [2][L][N]
+  // L >= 2: the modulus-switched encryption's key forms -- pk_j p^-1 mod q_i
+  // [2][L-1][N] + companions, then pk_{j,p} N^-1 mod p [2][N] + companions
+  u64* ms = nullptr;
 };
 struct zn_sk {
   uint32_t tag = kTagSk;
@@ -178,6 +182,97 @@ int encrypt_common(zn_ctx* c, bool zinc, const u64* key, const u64* keys, const 
   return ZN_OK;
 }
 
+// The modulus-switched encryption's arguments that depend only on the context.
+zn::MsArgs ms_args(const zn_ctx* c, const zn_pk* pk) {
+  zn::MsArgs A;
+  std::memset(&A, 0, sizeof(A));
+  A.keyms = pk->ms;
+  A.keyn = pk->ms + 4 * (size_t)(c->L - 1) * c->n;
+  for (uint32_t i = 0; i + 1 < c->L; ++i) {
+    A.pinv[i] = c->pinv[i];
+    A.pinvs[i] = c->pinvs[i];
+  }
+  return A;
+}
+
+// Key forms of the modulus-switched encryption for a key-level public key
+// (L >= 2; nothing to do for L = 1).  Synchronous.
+int ms_key_forms(zn_ctx* c, zn_pk* k) {
+  if (c->L < 2) return ZN_OK;
+  const size_t words = 4 * (size_t)c->L * c->n;
+  if (cudaMalloc(&k->ms, sizeof(u64) * words) != cudaSuccess) {
+    cudaGetLastError();
+    k->ms = nullptr;
+    return ZN_ENOMEM;
+  }
+  const zn::MsArgs A = ms_args(c, k);
+  if (zn::launch_ms_keys(c->dp, A, k->d, k->ms, const_cast<u64*>(A.keyn), 0) != cudaSuccess ||
+      cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+    return ZN_ECUDA;
+  }
+  return ZN_OK;
+}
+
+// Ciphertexts per prep/special/data launch triple of the modulus-switched
+// encryption: its scratch -- m (8N), d_0, d_1 (16N), small (3N) and, at
+// N = 2^15, the inverse-transform halves (16N) -- within ~128 MiB (the data
+// kernel re-reads it once per prime, mostly from L2; DRAM has ample headroom
+// either way), and the batch split into equal chunks so that no launch is a
+// small tail wave.
+uint32_t ms_chunk(const zn_ctx* c, uint32_t batch) {
+  const size_t per = (size_t)c->n * (27 + (c->prm.log_n == 15 ? 16 : 0));
+  size_t k = (128ull << 20) / per;
+  if (k < 1) k = 1;
+  if (k > 65535) k = 65535;
+  const size_t chunks = (batch + k - 1) / k;
+  return (uint32_t)((batch + chunks - 1) / chunks);
+}
+
+// ct_index == nullptr: ciphertext b takes index b.
+int ms_common(zn_ctx* c, const zn_pk* pk, const double* slots, uint32_t n_slots, uint32_t batch, uint64_t seed,
+              unsigned domain, const uint64_t* ct_index, uint64_t* ct, cudaStream_t st) {
+  const uint32_t chunk = ms_chunk(c, batch);
+  const uint32_t first = batch < chunk ? batch : chunk;
+  const size_t n = c->n;
+  const size_t m_b = sizeof(i64) * first * n, d_b = 2 * m_b;
+  const size_t t_b = c->prm.log_n == 15 ? 2 * sizeof(u64) * first * n : 0, s_b = 3 * (size_t)first * n;
+  Scratch scratch(c, st);
+  if (!scratch.alloc(m_b + d_b + t_b + s_b)) return ZN_ENOMEM;
+  unsigned char* base = (unsigned char*)scratch.p;
+  zn::MsArgs A = ms_args(c, pk);
+  A.swap = 0;
+  A.m = (const i64*)base;
+  A.d = (i64*)(base + m_b);
+  A.tmp = t_b ? (u64*)(base + m_b + d_b) : nullptr;
+  A.small = (const int8_t*)(base + m_b + d_b + t_b);
+  const size_t ct_words = 2 * (size_t)(c->L - 1) * n;
+  for (uint32_t b0 = 0; b0 < batch; b0 += chunk) {
+    const uint32_t nb = (batch - b0) < chunk ? (batch - b0) : chunk;
+    zn::PrepArgs pa;
+    pa.slots = n_slots ? slots + (size_t)b0 * n_slots : nullptr;
+    pa.n_slots = n_slots;
+    pa.ct_index = ct_index ? ct_index + b0 : nullptr;
+    pa.ct_index0 = b0;
+    pa.seed = seed;
+    pa.domain = domain;
+    pa.me = (i64*)A.m;
+    pa.small = (int8_t*)A.small;
+    A.out = ct + (size_t)b0 * ct_words;
+    {
+      TimedLaunch t(c, ZN_TIME_ENCODE, st);
+      ZN_CUDA(zn::launch_prep_ms(c->dp, pa, nb, st));
+    }
+    {
+      TimedLaunch t(c, ZN_TIME_MS_SPECIAL, st);
+      ZN_CUDA(zn::launch_ms_special(c->dp, A, nb, st));
+    }
+    TimedLaunch t(c, ZN_TIME_MS_DATA, st);
+    ZN_CUDA(zn::launch_ms_data(c->dp, A, nb, st));
+  }
+  return ZN_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -295,6 +390,10 @@ int zn_ctx_create(const zn_params* p, int device, zn_ctx** out) {
     dp.ninvs[i] = zn::shoup(dp.ninv[i], q);
   }
   dp.q0inv_mod_q1 = L > 1 ? zn::powmod(c->q[0] % c->q[1], c->q[1] - 2, c->q[1]) : 0;
+  for (uint32_t i = 0; i + 1 < L; ++i) {
+    c->pinv[i] = zn::powmod(c->q[L - 1] % c->q[i], c->q[i] - 2, c->q[i]);
+    c->pinvs[i] = zn::shoup(c->pinv[i], c->q[i]);
+  }
   zn::cdt_thresholds(dp.cdt);
 
   DeviceGuard g(device);
@@ -452,6 +551,7 @@ int ckks_keygen(zn_ctx* c, uint64_t seed, zn_sk** sk, zn_pk** pk) {
     for (uint32_t j = 0; j < c->n; ++j) s->s[j] = (int8_t)tmp[j];
   }
   cudaFree(d_s);
+  if (!rc) rc = ms_key_forms(c, k);
   if (rc) {
     cudaGetLastError();
     zn_sk_destroy(s);
@@ -476,6 +576,7 @@ void zn_pk_destroy(zn_pk* k) {
   k->tag = kTagDead;
   DeviceGuard g(k->ctx->device);
   cudaFree(k->d);
+  cudaFree(k->ms);
   delete k;
 }
 
@@ -508,6 +609,11 @@ int zn_pk_import(zn_ctx* c, const uint64_t* host_in, zn_pk** out) {
     cudaGetLastError();
     zn_pk_destroy(k);
     return ZN_ECUDA;
+  }
+  const int rc = ms_key_forms(c, k);
+  if (rc) {
+    zn_pk_destroy(k);
+    return rc;
   }
   *out = k;
   return ZN_OK;
@@ -672,6 +778,46 @@ int zinc_encrypt(zn_ctx* c, const zn_zcache* z, const double* slots, uint32_t n_
                  const uint64_t* ct_index, uint64_t* ct, void* stream) {
   if (!c || !zc_of(z, c)) return ZN_EINVAL;
   return encrypt_common(c, true, z->d, nullptr, slots, n_slots, batch, seed, ct_index, ct, stream);
+}
+
+// ------------------------------------- special prime and modulus switching
+
+int ckks_encrypt_ms(zn_ctx* c, const zn_pk* pk, const double* slots, uint32_t n_slots, uint32_t batch,
+                    uint64_t seed, const uint64_t* ct_index, uint64_t* ct, void* stream) {
+  if (!c || !pk_of(pk, c) || c->L < 2 || !pk->ms || n_slots > c->n / 2) return ZN_EINVAL;
+  if (batch == 0) return ZN_OK;
+  if (!ct || !ct_index || (n_slots && !slots)) return ZN_EINVAL;
+  DeviceGuard g(c->device);
+  return ms_common(c, pk, slots, n_slots, batch, seed, 0u, ct_index, ct, S(stream));
+}
+
+int zinc_precompute_ms(zn_ctx* c, const zn_pk* pk, uint64_t seed, zn_ctx* dc, zn_zcache** out) {
+  if (!c || !pk_of(pk, c) || c->L < 2 || !pk->ms || !dc || !out) return ZN_EINVAL;
+  *out = nullptr;
+  if (dc->device != c->device || dc->L != c->L - 1 || dc->prm.log_n != c->prm.log_n ||
+      dc->prm.log2_delta != c->prm.log2_delta)
+    return ZN_EINVAL;
+  for (uint32_t i = 0; i < dc->L; ++i)
+    if (dc->q[i] != c->q[i]) return ZN_EINVAL;
+  DeviceGuard g(c->device);
+  zn_zcache* z = new (std::nothrow) zn_zcache();
+  if (!z) return ZN_ENOMEM;
+  z->ctx = dc;
+  if (cudaMalloc(&z->d, sizeof(u64) * 2 * ring_words(dc)) != cudaSuccess) {
+    cudaGetLastError();
+    delete z;
+    return ZN_ENOMEM;
+  }
+  // modulus-switched Enc of the zero plaintext, sampling domain 3, ct_index 0
+  int rc = ms_common(c, pk, nullptr, 0, 1, seed, 3u, nullptr, z->d, 0);
+  if (!rc && cudaDeviceSynchronize() != cudaSuccess) rc = ZN_ECUDA;
+  if (rc) {
+    cudaGetLastError();
+    zn_zcache_destroy(z);
+    return rc;
+  }
+  *out = z;
+  return ZN_OK;
 }
 
 // -------------------------------------------------------------- decrypt

@@ -109,16 +109,19 @@ __global__ void k_encode_smem(DevParams P, const double* __restrict__ slots, uin
 // for all q_i):
 //   vanilla (Eq. 8):    me = m + e0 (poly 1), small = [u (poly 0), e1 (poly 2)]
 //   Zinc (Algorithm 1): me = m + e1' (poly 0), small = [e2' (poly 1)]
+//   modulus-switched vanilla (MS): me = m, small = [u, e0, e1] (polys 0, 1, 2;
+//     the noise enters before the division by the special prime, m after it)
 // chi block k yields coefficients k and k + N/2 -- the pair that the
 // encoder's last loop produces at k.
 // cdt: the chi thresholds staged in shared memory by the calling kernel.
-template <bool ZINC>
+template <bool ZINC, bool MS = false>
 __device__ __forceinline__ void prep_one(const DevParams& P, const PrepArgs& A, size_t b, i64* re, i64* im,
                                          const u64* cdt) {
+  static_assert(!(ZINC && MS), "the modulus-switched form is a vanilla encryption");
   const int N = 1 << P.log_n, n = N >> 1;
   const u64 ct = A.ct_index ? A.ct_index[b] : A.ct_index0 + b;
   i64* me = A.me + b * N;
-  int8_t* sp = A.small + b * 2 * (size_t)N;
+  int8_t* sp = A.small + b * (MS ? 3 : 2) * (size_t)N;
   const unsigned tag_e = rand_tag(A.domain, ZINC ? 0 : 1, 0);
   // m first (kept apart from the sampler, which would otherwise share the
   // encoder's registers), then m + e once the block's stores are visible
@@ -133,11 +136,21 @@ __device__ __forceinline__ void prep_one(const DevParams& P, const PrepArgs& A, 
 #pragma unroll 1
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
     const uint4 w = zn_rand(A.seed, (unsigned)k, tag_e, ct);
-    const i64 a = A.n_slots ? me[k] : 0, c = A.n_slots ? me[k + n] : 0;
-    me[k] = a + cdt_search(w.x, w.y, cdt);
-    me[k + n] = c + cdt_search(w.z, w.w, cdt);
+    if constexpr (MS) {
+      if (!A.n_slots) {
+        me[k] = 0;
+        me[k + n] = 0;
+      }
+      sp[N + k] = (int8_t)cdt_search(w.x, w.y, cdt);
+      sp[N + k + n] = (int8_t)cdt_search(w.z, w.w, cdt);
+    } else {
+      const i64 a = A.n_slots ? me[k] : 0, c = A.n_slots ? me[k + n] : 0;
+      me[k] = a + cdt_search(w.x, w.y, cdt);
+      me[k + n] = c + cdt_search(w.z, w.w, cdt);
+    }
   }
   if constexpr (!ZINC) {
+    int8_t* e1p = sp + (MS ? 2 : 1) * (size_t)N;
     const unsigned tag_u = rand_tag(A.domain, 0, 0), tag_1 = rand_tag(A.domain, 2, 0);
 #pragma unroll 1
     for (int blk = threadIdx.x; blk < N / 4; blk += blockDim.x) {
@@ -150,8 +163,8 @@ __device__ __forceinline__ void prep_one(const DevParams& P, const PrepArgs& A, 
 #pragma unroll 1
     for (int blk = threadIdx.x; blk < n; blk += blockDim.x) {
       const uint4 w = zn_rand(A.seed, (unsigned)blk, tag_1, ct);
-      sp[N + blk] = (int8_t)cdt_search(w.x, w.y, cdt);
-      sp[N + blk + n] = (int8_t)cdt_search(w.z, w.w, cdt);
+      e1p[blk] = (int8_t)cdt_search(w.x, w.y, cdt);
+      e1p[blk + n] = (int8_t)cdt_search(w.z, w.w, cdt);
     }
   } else {
     const unsigned tag_2 = rand_tag(A.domain, 1, 0);
@@ -169,13 +182,13 @@ __device__ __forceinline__ void stage_cdt(const DevParams& P, u64* s_cdt) {
   __syncthreads();
 }
 
-template <bool ZINC>
+template <bool ZINC, bool MS = false>
 __global__ void __launch_bounds__(512, 2) k_prep_smem(DevParams P, PrepArgs A) {
   extern __shared__ i64 smi[];
   __shared__ u64 s_cdt[kCdt];
   stage_cdt(P, s_cdt);
   const int h = 1 << (P.log_n - 2);
-  prep_one<ZINC>(P, A, blockIdx.x, smi, smi + h, s_cdt);
+  prep_one<ZINC, MS>(P, A, blockIdx.x, smi, smi + h, s_cdt);
 }
 
 // Persistent prep over a mixed work list: one 512-thread block per SM takes
@@ -360,20 +373,26 @@ cudaError_t launch_encode(const DevParams& P, const double* slots, uint32_t n_sl
   return cudaGetLastError();
 }
 
-template <bool ZINC>
+template <bool ZINC, bool MS = false>
 static cudaError_t prep_launch(const DevParams& P, const PrepArgs& A, uint32_t batch, cudaStream_t st) {
   const int h = 1 << (P.log_n - 2);
   const int block = h / 2 < 512 ? (h / 2 < 32 ? 32 : h / 2) : 512;
   const size_t smem = A.n_slots ? 2 * sizeof(i64) * (size_t)h : 0;
-  cudaError_t e = cudaFuncSetAttribute(k_prep_smem<ZINC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = k_prep_smem<ZINC, MS>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_prep_smem<ZINC><<<batch, block, smem, st>>>(P, A);
+  kern<<<batch, block, smem, st>>>(P, A);
   return cudaGetLastError();
 }
 
 cudaError_t launch_prep(const DevParams& P, const PrepArgs& A, bool zinc, uint32_t batch, cudaStream_t st) {
   if (batch == 0) return cudaSuccess;
   return zinc ? prep_launch<true>(P, A, batch, st) : prep_launch<false>(P, A, batch, st);
+}
+
+cudaError_t launch_prep_ms(const DevParams& P, const PrepArgs& A, uint32_t batch, cudaStream_t st) {
+  if (batch == 0) return cudaSuccess;
+  return prep_launch<false, true>(P, A, batch, st);
 }
 
 cudaError_t launch_batch_prep(const JobDesc* jobs, const PrepUnit* units, int n_units, int* counter, int grid,
