@@ -189,8 +189,13 @@ zn::MsArgs ms_args(const zn_ctx* c, const zn_pk* pk) {
   A.keyms = pk->ms;
   A.keyn = pk->ms + 4 * (size_t)(c->L - 1) * c->n;
   for (uint32_t i = 0; i + 1 < c->L; ++i) {
+    const u64 q = c->q[i];
     A.pinv[i] = c->pinv[i];
     A.pinvs[i] = c->pinvs[i];
+    const u64 off = zn::powmod(2, 62, q);                                  // 2^62 mod q
+    const u64 op = (u64)(((unsigned __int128)off * c->pinv[i]) % q);       // 2^62 p^-1 mod q
+    A.kc1[i] = (q - op) % q;
+    A.kc0[i] = (q - (op + off) % q) % q;
   }
   return A;
 }
@@ -242,8 +247,8 @@ int ms_common(zn_ctx* c, const zn_pk* pk, const double* slots, uint32_t n_slots,
   unsigned char* base = (unsigned char*)scratch.p;
   zn::MsArgs A = ms_args(c, pk);
   A.swap = 0;
-  A.m = (const i64*)base;
-  A.d = (i64*)(base + m_b);
+  A.m = (const u64*)base;
+  A.d = (u64*)(base + m_b);
   A.tmp = t_b ? (u64*)(base + m_b + d_b) : nullptr;
   A.small = (const int8_t*)(base + m_b + d_b + t_b);
   const size_t ct_words = 2 * (size_t)(c->L - 1) * n;

@@ -109,8 +109,9 @@ __global__ void k_encode_smem(DevParams P, const double* __restrict__ slots, uin
 // for all q_i):
 //   vanilla (Eq. 8):    me = m + e0 (poly 1), small = [u (poly 0), e1 (poly 2)]
 //   Zinc (Algorithm 1): me = m + e1' (poly 0), small = [e2' (poly 1)]
-//   modulus-switched vanilla (MS): me = m, small = [u, e0, e1] (polys 0, 1, 2;
-//     the noise enters before the division by the special prime, m after it)
+//   modulus-switched vanilla (MS): me = m + 2^62, small = [u, e0, e1] (polys
+//     0, 1, 2; the noise enters before the division by the special prime, m
+//     after it)
 // chi block k yields coefficients k and k + N/2 -- the pair that the
 // encoder's last loop produces at k.
 // cdt: the chi thresholds staged in shared memory by the calling kernel.
@@ -126,9 +127,11 @@ __device__ __forceinline__ void prep_one(const DevParams& P, const PrepArgs& A, 
   // m first (kept apart from the sampler, which would otherwise share the
   // encoder's registers), then m + e once the block's stores are visible
   if (A.n_slots) {
+    // MS: stored as m + 2^62 (non-negative), read back by the data primes as unsigned
+    constexpr i64 off = MS ? (i64)kMsOffset : 0;
     auto st = [&](int k, i64 a, i64 c) {
-      me[k] = a;
-      me[k + n] = c;
+      me[k] = a + off;
+      me[k + n] = c + off;
     };
     encode_core(P, A.slots + b * A.n_slots, A.n_slots, re, im, st);
     __syncthreads();
@@ -138,8 +141,8 @@ __device__ __forceinline__ void prep_one(const DevParams& P, const PrepArgs& A, 
     const uint4 w = zn_rand(A.seed, (unsigned)k, tag_e, ct);
     if constexpr (MS) {
       if (!A.n_slots) {
-        me[k] = 0;
-        me[k + n] = 0;
+        me[k] = (i64)kMsOffset;
+        me[k + n] = (i64)kMsOffset;
       }
       sp[N + k] = (int8_t)cdt_search(w.x, w.y, cdt);
       sp[N + k + n] = (int8_t)cdt_search(w.z, w.w, cdt);

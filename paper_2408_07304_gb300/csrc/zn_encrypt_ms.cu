@@ -85,14 +85,15 @@ __device__ __forceinline__ void intt_chain(u64* sm, int t, const u64* itw, const
 }
 
 // ------------------------------------------------------ the special prime
-// d_j[k] = e_j[k] + h - r, r = (c + e_j[k] + h) mod p for c = (pk_j u)_p[k] in [0, p).
-__device__ __forceinline__ i64 ms_digit(u64 c, int e, u64 p) {
+// D_j[k] = d_j[k] + 2^62, d_j[k] = e_j[k] + h - r, r = (c + e_j[k] + h) mod p
+// for c = (pk_j u)_p[k] in [0, p); |d_j| <= p/2 + 19 < 2^61.
+__device__ __forceinline__ u64 ms_digit(u64 c, int e, u64 p) {
   const u64 h = p >> 1;
   u64 x = c + small_res(e, p);
   if (x >= p) x -= p;
   u64 r = x + h;
   if (r >= p) r -= p;
-  return (i64)e + (i64)h - (i64)r;
+  return kMsOffset + (u64)((i64)e + (i64)h - (i64)r);
 }
 
 // Component j of ciphertext b, N = 2^LOGN <= 2^14: u -> NTT -> times
@@ -114,7 +115,7 @@ __global__ void __launch_bounds__(NttShape<LOGN, 5>::T) k_ms_special(DevParams P
   auto st_u = [&](int idx, u64 uh) { sm[swz<LOGN>(idx)] = mul_shoup(uh, __ldg(kn + idx), __ldg(kns + idx), p); };
   ntt_chain<LOGN, 5, LOGN, false, decltype(st_u)>(sm, t, P.twp + (size_t)ip * N, 1, p, st_u);
   const int8_t* e = sp + (size_t)(1 + j) * N;
-  i64* d = A.d + (b * 2 + j) * N;
+  u64* d = A.d + (b * 2 + j) * N;
   auto st_c = [&](int idx, u64 c) { d[idx] = ms_digit(c, __ldg(e + idx), p); };
   intt_chain<LOGN, 5, LOGN, decltype(st_c)>(sm, t, P.itw + (size_t)ip * N, P.itws + (size_t)ip * N, 1, p, st_c);
 }
@@ -165,7 +166,7 @@ __global__ void k_ms_special_top(DevParams P, MsArgs A, uint32_t batch) {
     const size_t b = bj >> 1;
     const int j = (int)(bj & 1);
     const int8_t* e = A.small + b * 3 * N + (size_t)(1 + j) * N;
-    i64* d = A.d + bj * N;
+    u64* d = A.d + bj * N;
     d[k] = ms_digit(a, __ldg(e + k), p);
     d[k + HALF] = ms_digit(c, __ldg(e + k + HALF), p);
   }
@@ -208,18 +209,23 @@ __device__ __forceinline__ void gen_val_half2(u64* sm, int t, int nt, int h, V& 
   }
 }
 
-// (d p^-1 + m) mod q and d p^-1 mod q for the data prime's two polynomials.
+// The data prime's transform inputs, in [0, 2q):
+//   first component   d_0 p^-1 + m = D_0 p^-1 + M + kc0   (mod q)
+//   second component  d_1 p^-1     = D_1 p^-1 + kc1       (mod q)
+// with D_j p^-1 one Shoup product (any 64-bit input, result in [0, 2q)) and
+// M one Barrett step (floor(2^64/q) = mu; result in [0, 2q)).
 struct MsVal {
-  const i64* d;
-  const i64* m;   // nullptr: second component
-  u64 q, mu, pv, pvs;
+  const u64* d;
+  const u64* m;   // nullptr: second component
+  u64 q, mu, pv, pvs, kc;
   __device__ __forceinline__ u64 operator()(int k) const {
-    u64 x = mul_shoup(reduce_signed(__ldg(d + k), q, mu), pv, pvs, q);
-    if (x >= q) x -= q;
+    u64 x = mul_shoup(__ldg(d + k), pv, pvs, q) + kc;         // [0, 3q)
     if (m) {
-      x += reduce_signed(__ldg(m + k), q, mu);
-      if (x >= q) x -= q;
+      const u64 a = __ldg(m + k);
+      x += a - __umul64hi(a, mu) * q;                         // [0, 5q)
+      if (x >= 4 * q) x -= 4 * q;
     }
+    if (x >= 2 * q) x -= (m ? 2 : 1) * q;
     return x;
   }
 };
@@ -231,7 +237,8 @@ struct MsVal {
 template <int LOGN, int LOGPER, bool RELAX, int KM>
 __device__ __forceinline__ void ms_unit_q(const DevParams& P, const MsArgs& A, int i, size_t b, u64* sm, int t) {
   using S = NttShape<LOGN, LOGPER>;
-  static_assert(!RELAX || 1 + 2 * LOGN + 2 <= 32, "relaxed sums must stay below 32q");
+  // inputs below 2q, 2q per relaxed stage, 2q from the key product
+  static_assert(!RELAX || 2 + 2 * LOGN + 2 <= 32, "relaxed sums must stay below 32q");
   constexpr int N = S::N;
   constexpr bool TOP = KM == 3 && LOGN % 3 == 1;
   constexpr int HI = TOP ? LOGN - 1 : LOGN;
@@ -245,8 +252,8 @@ __device__ __forceinline__ void ms_unit_q(const DevParams& P, const MsArgs& A, i
   const u64* k1 = k0 + (size_t)Ld * N;
   const u64* k0s = k0 + 2 * (size_t)Ld * N;
   const u64* k1s = k1 + 2 * (size_t)Ld * N;
-  const MsVal v0{A.d + b * 2 * N, A.m + b * N, q, mu, A.pinv[i], A.pinvs[i]};
-  const MsVal v1{A.d + b * 2 * N + N, nullptr, q, mu, A.pinv[i], A.pinvs[i]};
+  const MsVal v0{A.d + b * 2 * N, A.m + b * N, q, mu, A.pinv[i], A.pinvs[i], A.kc0[i]};
+  const MsVal v1{A.d + b * 2 * N + N, nullptr, q, mu, A.pinv[i], A.pinvs[i], A.kc1[i]};
   if constexpr (TOP) gen_i8_top<LOGN, KM, RELAX>(sm, t, S::T, sp, q, __ldg(tw + 1));
   else gen_i8<LOGN, KM>(sm, t, S::T, sp, q);
   auto st_u = [&](int idx, u64 uh) {
@@ -287,8 +294,8 @@ __device__ __forceinline__ void ms_half_unit_q(const DevParams& P, const MsArgs&
   const u64* k1 = k0 + (size_t)Ld * N;
   const u64* k0s = k0 + 2 * (size_t)Ld * N;
   const u64* k1s = k1 + 2 * (size_t)Ld * N;
-  const MsVal v0{A.d + b * 2 * N, A.m + b * N, q, mu, A.pinv[i], A.pinvs[i]};
-  const MsVal v1{A.d + b * 2 * N + N, nullptr, q, mu, A.pinv[i], A.pinvs[i]};
+  const MsVal v0{A.d + b * 2 * N, A.m + b * N, q, mu, A.pinv[i], A.pinvs[i], A.kc0[i]};
+  const MsVal v1{A.d + b * 2 * N + N, nullptr, q, mu, A.pinv[i], A.pinvs[i], A.kc1[i]};
   const int tmul = 2 + h;
   auto sum = [&](u64 a, u64 x) { return RAW ? reduce_sum<RELAX>(a + x, q) : reduce4(a + x, q); };
   if constexpr (TOP) gen_i8_half2<LOGH, KM, RELAX>(sm, t, S::T, h, sp, q, w1p, __ldg(tw + tmul));

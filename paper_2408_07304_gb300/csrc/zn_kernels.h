@@ -89,22 +89,29 @@ cudaError_t launch_sk_residues(const DevParams& P, const int8_t* s, u64* out, cu
 // ------------------------------------------------ modulus-switched encryption
 // The key-level chain q_0..q_{L-1} of P ends in the special prime p = q_{L-1};
 // the ciphertext has the L-1 data primes.  Per ciphertext:
-//   prep (prep_ms):   m [N] int64, small = [u, e0, e1] int8 [3][N]
-//   special (p):      d_j = e_j + h - ((pk_j u + e_j)_p + h) mod p, h = floor(p/2)
+//   prep (prep_ms):   M = m + 2^62 [N], small = [u, e0, e1] int8 [3][N]
+//   special (p):      D_j = d_j + 2^62, d_j = e_j + h - ((pk_j u + e_j)_p + h) mod p,
+//                     h = floor(p/2)
 //   data primes q_i:  c'_0 = (pk0 p^-1) u^ + NTT(d_0 p^-1 + m),
 //                     c'_1 = (pk1 p^-1) u^ + NTT(d_1 p^-1)
+// The 2^62 offsets make M and D_j unsigned, so that a data prime reduces
+// them with one Shoup product (D_j p^-1) or one Barrett step (M) and removes
+// the offsets with the constants kc0, kc1.
 struct MsArgs {
   int swap;             // grid order of the data-prime kernel, as EncArgs
   const u64* keyms;     // [2][L-1][N] pk_j p^-1 mod q_i (NTT form), then Shoup companions [2][L-1][N]
   const u64* keyn;      // [2][N] pk_{j,p} N^-1 mod p (NTT form), then Shoup companions [2][N]
-  const i64* m;         // [B][N] encoded message
+  const u64* m;         // [B][N] encoded message + 2^62
   const int8_t* small;  // [B][3][N] u, e0, e1
-  i64* d;               // [B][2][N] d_0, d_1
+  u64* d;               // [B][2][N] d_0 + 2^62, d_1 + 2^62
   u64* tmp;             // [B][2][N] inverse-transform halves (N = 2^15 only)
   u64* out;             // [B][2][L-1][N]
   u64 pinv[kMaxL];      // p^-1 mod q_i
   u64 pinvs[kMaxL];     // Shoup companions
+  u64 kc1[kMaxL];       // -2^62 p^-1 mod q_i
+  u64 kc0[kMaxL];       // -2^62 (p^-1 + 1) mod q_i
 };
+constexpr u64 kMsOffset = 1ull << 62;
 cudaError_t launch_prep_ms(const DevParams& P, const PrepArgs& A, uint32_t batch, cudaStream_t st);
 // keyms / keyn (and companions) of MsArgs from a key-level public key [2][L][N].
 cudaError_t launch_ms_keys(const DevParams& P, const MsArgs& A, const u64* pk, u64* keyms, u64* keyn,
