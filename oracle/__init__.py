@@ -16,7 +16,9 @@ sampler    R_2 (ternary), chi (rounded Gaussian, sigma = 3.2, CDT), R_q (uniform
            -- Section "Polynomials and Distributions"
 encoder    CKKS canonical-embedding encoder / decoder (FP64)
 ring       definitional negacyclic NTT and schoolbook products (C, via ctypes)
-ckks       Gen (Eq. 7), Enc (Eq. 8), Enc_z (Algorithm 1, Eq. 9), Dec (Eq. 10)
+ckks       Gen (Eq. 7), Enc (Eq. 8), Enc_z (Algorithm 1, Eq. 9), Dec (Eq. 10),
+           the modulus-switched (special-prime) Enc
+bfvbgv     BFV (Eq. 12) and BGV (Eq. 13) encryption, their Zinc forms, Dec
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test against a
 closed form, brute force, an invariant, or an independent library routine,
