@@ -206,6 +206,47 @@ int ckks_encrypt_ms(zn_ctx* ctx, const zn_pk* pk, const double* slots, uint32_t 
  * Algorithm 1 at the data level.  Synchronous. */
 int zinc_precompute_ms(zn_ctx* ctx, const zn_pk* pk, uint64_t seed, zn_ctx* data_ctx, zn_zcache** out);
 
+/* ------------------------------------------- BFV and BGV (Section "Scheme Flexibility")
+ *
+ * The paper notes that Zinc carries over to BFV (Eq. 12) and BGV (Eq. 13).
+ * Plaintexts are polynomials of R_t = Z_t[X]/(X^N + 1) given by their N
+ * coefficients: device int64 [batch][N], each taken mod t (coefficient
+ * encoding; the paper leaves encoding to the schemes' own papers).  Q is the
+ * product of the context's primes; the second component uses pk1 (as read
+ * in Eq. 8).  t must satisfy 2 <= t <= 2^58 and t < q_i for every prime;
+ * ring degrees 2^10 .. 2^15.  Sampling tags are the CKKS ones (vanilla:
+ * domain 0, u / e0 / e1 = polys 0 / 1 / 2; Zinc: domain 1, e1' / e2' =
+ * polys 0 / 1; caches: domain 3, ct_index 0).  Ciphertexts: device uint64
+ * [batch][2][L][N], NTT form.  Decryption is exact while the noise is below
+ * Delta/2 (BFV) or Q/(2t) (BGV).  ZN_EINVAL for an invalid t or ring.
+ *
+ * BFV, Eq. 12: Delta = floor(Q/t); c0 = pk0*u + e0 + Delta*m, c1 = pk1*u + e1
+ * under Gen's key (ckks_keygen).  Its Zinc form adds Delta*m + e1' and e2' to
+ * the cache of zinc_precompute (CKKS's Enc(0), unchanged, as the paper says). */
+int bfv_encrypt(zn_ctx* ctx, const zn_pk* pk, uint64_t t, const int64_t* m, uint32_t batch, uint64_t seed,
+                const uint64_t* ct_index, uint64_t* ct, void* stream);
+int bfv_zinc_encrypt(zn_ctx* ctx, const zn_zcache* zc, uint64_t t, const int64_t* m, uint32_t batch,
+                     uint64_t seed, const uint64_t* ct_index, uint64_t* ct, void* stream);
+/* m = round(t [c0 + c1 s]_Q / Q) mod t, out: device int64 [batch][N] in [0, t). */
+int bfv_decrypt(zn_ctx* ctx, const zn_sk* sk, uint64_t t, const uint64_t* ct, uint32_t batch, int64_t* m,
+                void* stream);
+
+/* BGV, Eq. 13: the errors carry the factor t.  bgv_keygen: Gen's samples with
+ * pk0 = -a*s + t*e (the key records t; zn_pk_import and zn_zcache_import
+ * rebuild Gen-type handles, not BGV ones).  bgv_encrypt:
+ * c0 = pk0*u + t*e0 + m, c1 = pk1*u + t*e1.  bgv_zinc_precompute caches a BGV
+ * encryption of zero; bgv_zinc_encrypt adds m + t*e1' and t*e2' to it.
+ * Synchronous: keygen, precompute. */
+int bgv_keygen(zn_ctx* ctx, uint64_t t, uint64_t seed, zn_sk** sk, zn_pk** pk);
+int bgv_zinc_precompute(zn_ctx* ctx, const zn_pk* pk, uint64_t seed, zn_zcache** out);
+int bgv_encrypt(zn_ctx* ctx, const zn_pk* pk, const int64_t* m, uint32_t batch, uint64_t seed,
+                const uint64_t* ct_index, uint64_t* ct, void* stream);
+int bgv_zinc_encrypt(zn_ctx* ctx, const zn_zcache* zc, const int64_t* m, uint32_t batch, uint64_t seed,
+                     const uint64_t* ct_index, uint64_t* ct, void* stream);
+/* m = ([c0 + c1 s]_Q centred) mod t, out: device int64 [batch][N] in [0, t). */
+int bgv_decrypt(zn_ctx* ctx, const zn_sk* sk, uint64_t t, const uint64_t* ct, uint32_t batch, int64_t* m,
+                void* stream);
+
 /* Host memory in, host memory out: copies slot vectors and ct indices to the
  * device, encrypts -- vanilla (Eq. 8) under pk when zc is NULL, Zinc
  * (Algorithm 1) under zc otherwise (pass exactly one) -- and copies the

@@ -65,6 +65,14 @@ _SIGS = {
     "zinc_encrypt_noalloc": (_i32, [_vp, _vp, _vp, _u32, _u32, _u64, _vp, _vp, _vp]),
     "ckks_encrypt_ms": (_i32, [_vp, _vp, _vp, _u32, _u32, _u64, _vp, _vp, _vp]),
     "zinc_precompute_ms": (_i32, [_vp, _vp, _u64, _vp, _pp]),
+    "bfv_encrypt": (_i32, [_vp, _vp, _u64, _vp, _u32, _u64, _vp, _vp, _vp]),
+    "bfv_zinc_encrypt": (_i32, [_vp, _vp, _u64, _vp, _u32, _u64, _vp, _vp, _vp]),
+    "bfv_decrypt": (_i32, [_vp, _vp, _u64, _vp, _u32, _vp, _vp]),
+    "bgv_keygen": (_i32, [_vp, _u64, _u64, _pp, _pp]),
+    "bgv_zinc_precompute": (_i32, [_vp, _vp, _u64, _pp]),
+    "bgv_encrypt": (_i32, [_vp, _vp, _vp, _u32, _u64, _vp, _vp, _vp]),
+    "bgv_zinc_encrypt": (_i32, [_vp, _vp, _vp, _u32, _u64, _vp, _vp, _vp]),
+    "bgv_decrypt": (_i32, [_vp, _vp, _u64, _vp, _u32, _vp, _vp]),
     "ckks_decrypt": (_i32, [_vp, _vp, _vp, _u32, _vp, _vp]),
     "ckks_decrypt_decode": (_i32, [_vp, _vp, _vp, _u32, _u32, _vp, _vp]),
     "ckks_add": (_i32, [_vp, _vp, _vp, _u32, _vp, _vp]),
@@ -366,6 +374,72 @@ def zinc_precompute_ms(ctx, pk, seed, data_ctx):
     _check(lib().zinc_precompute_ms(ctx.handle, pk.handle, seed, data_ctx.handle, ctypes.byref(h)),
            "zinc_precompute_ms")
     return ZincCache(data_ctx, h)
+
+
+# ------------------------------------------------ BFV (Eq. 12), BGV (Eq. 13)
+
+def _int_enc(fn, ctx, key, t, m, seed, ct_index, out, stream, name):
+    """m: CUDA int64 [B, N] plaintext coefficients (taken mod t) -> int64 [B, 2, L, N]."""
+    import torch
+    B = m.shape[0]
+    out = _out(out, (B, 2, ctx.L, ctx.n), torch.int64, m.device)
+    _dev(m, torch.int64, (B, ctx.n), "m")
+    _dev(ct_index, torch.int64, (B,), "ct_index")
+    _dev(out, torch.int64, (B, 2, ctx.L, ctx.n), "out")
+    args = [ctx.handle, key.handle] + ([t] if t is not None else []) + [m.data_ptr(), B, seed, ct_index.data_ptr(),
+                                                                       out.data_ptr(), _stream(stream)]
+    _check(fn(*args), name)
+    return out
+
+
+def bfv_encrypt(ctx, pk, t, m, seed, ct_index, out=None, stream=None):
+    """BFV encryption (Eq. 12) under Gen's key."""
+    return _int_enc(lib().bfv_encrypt, ctx, pk, t, m, seed, ct_index, out, stream, "bfv_encrypt")
+
+
+def bfv_zinc_encrypt(ctx, zc, t, m, seed, ct_index, out=None, stream=None):
+    """BFV Zinc encryption over the CKKS cache of zinc_precompute."""
+    return _int_enc(lib().bfv_zinc_encrypt, ctx, zc, t, m, seed, ct_index, out, stream, "bfv_zinc_encrypt")
+
+
+def bgv_keygen(ctx, t, seed):
+    sk, pk = ctypes.c_void_p(), ctypes.c_void_p()
+    _check(lib().bgv_keygen(ctx.handle, t, seed, ctypes.byref(sk), ctypes.byref(pk)), "bgv_keygen")
+    return SecretKey(ctx, sk), PublicKey(ctx, pk)
+
+
+def bgv_zinc_precompute(ctx, pk, seed):
+    h = ctypes.c_void_p()
+    _check(lib().bgv_zinc_precompute(ctx.handle, pk.handle, seed, ctypes.byref(h)), "bgv_zinc_precompute")
+    return ZincCache(ctx, h)
+
+
+def bgv_encrypt(ctx, pk, m, seed, ct_index, out=None, stream=None):
+    """BGV encryption (Eq. 13) under a bgv_keygen key (t recorded in the key)."""
+    return _int_enc(lib().bgv_encrypt, ctx, pk, None, m, seed, ct_index, out, stream, "bgv_encrypt")
+
+
+def bgv_zinc_encrypt(ctx, zc, m, seed, ct_index, out=None, stream=None):
+    """BGV Zinc encryption over a bgv_zinc_precompute cache."""
+    return _int_enc(lib().bgv_zinc_encrypt, ctx, zc, None, m, seed, ct_index, out, stream, "bgv_zinc_encrypt")
+
+
+def _int_dec(fn, ctx, sk, t, ct, stream, name):
+    import torch
+    B = ct.shape[0]
+    _dev(ct, torch.int64, (B, 2, ctx.L, ctx.n), "ct")
+    out = torch.empty((B, ctx.n), dtype=torch.int64, device=ct.device)
+    _check(fn(ctx.handle, sk.handle, t, ct.data_ptr(), B, out.data_ptr(), _stream(stream)), name)
+    return out
+
+
+def bfv_decrypt(ctx, sk, t, ct, stream=None):
+    """int64 [B, 2, L, N] -> plaintext coefficients int64 [B, N] in [0, t)."""
+    return _int_dec(lib().bfv_decrypt, ctx, sk, t, ct, stream, "bfv_decrypt")
+
+
+def bgv_decrypt(ctx, sk, t, ct, stream=None):
+    return _int_dec(lib().bgv_decrypt, ctx, sk, t, ct, stream, "bgv_decrypt")
 
 
 def zn_encrypt_host(ctx, key, slots, seed, ct_index, out, chunk=0):

@@ -47,6 +47,7 @@ struct zn_pk {
   // L >= 2: the modulus-switched encryption's key forms -- pk_j p^-1 mod q_i
   // [2][L-1][N] + companions, then pk_{j,p} N^-1 mod p [2][N] + companions
   u64* ms = nullptr;
+  uint64_t t = 0;   // 0: Gen's key (CKKS, BFV); t >= 2: BGV key (error scaled by t)
 };
 struct zn_sk {
   uint32_t tag = kTagSk;
@@ -58,11 +59,18 @@ struct zn_zcache {
   uint32_t tag = kTagZc;
   zn_ctx* ctx;
   u64* d;    // [2][L][N]
+  uint64_t t = 0;   // 0: a CKKS / BFV encryption of zero; t >= 2: a BGV one
 };
 
-static inline bool pk_of(const zn_pk* k, const zn_ctx* c) { return k && k->tag == kTagPk && k->ctx == c; }
+// pk_of / zc_of: Gen's key and caches made with it (CKKS, BFV);
+// bgv_pk_of / bgv_zc_of: BGV keys and caches (error scaled by t >= 2).
+static inline bool pk_of(const zn_pk* k, const zn_ctx* c) { return k && k->tag == kTagPk && k->ctx == c && !k->t; }
+static inline bool bgv_pk_of(const zn_pk* k, const zn_ctx* c) { return k && k->tag == kTagPk && k->ctx == c && k->t; }
 static inline bool sk_of(const zn_sk* k, const zn_ctx* c) { return k && k->tag == kTagSk && k->ctx == c; }
-static inline bool zc_of(const zn_zcache* z, const zn_ctx* c) { return z && z->tag == kTagZc && z->ctx == c; }
+static inline bool zc_of(const zn_zcache* z, const zn_ctx* c) { return z && z->tag == kTagZc && z->ctx == c && !z->t; }
+static inline bool bgv_zc_of(const zn_zcache* z, const zn_ctx* c) {
+  return z && z->tag == kTagZc && z->ctx == c && z->t;
+}
 
 namespace {
 
@@ -277,6 +285,135 @@ int ms_common(zn_ctx* c, const zn_pk* pk, const double* slots, uint32_t n_slots,
   }
   return ZN_OK;
 }
+
+// ------------------------------------------------ BFV / BGV host constants
+// t is valid for a context when 2 <= t <= 2^58 (BGV's m + t e stays an
+// int64) and t < q_i for every prime (t is then invertible mod each q_i).
+bool t_ok(const zn_ctx* c, uint64_t t) {
+  if (t < 2 || t > (1ull << 58)) return false;
+  for (uint32_t i = 0; i < c->L; ++i)
+    if (t >= c->q[i]) return false;
+  return true;
+}
+
+inline u64 mulmod_h(u64 a, u64 b, u64 m) { return (u64)(((unsigned __int128)a * b) % m); }
+
+// Encryption constants: BFV Delta mod q_i with Delta = floor(Q/t) -- from
+// Q = Delta t + (Q mod t) and Q = 0 mod q_i, Delta = -(Q mod t) t^-1 mod q_i
+// -- or BGV t mod q_i; with Shoup companions.
+void int_enc_consts(const zn_ctx* c, uint64_t t, bool bgv, zn::IntArgs& A) {
+  u64 Qt = 1 % t;
+  for (uint32_t j = 0; j < c->L; ++j) Qt = mulmod_h(Qt, c->q[j] % t, t);
+  for (uint32_t i = 0; i < c->L; ++i) {
+    const u64 q = c->q[i];
+    u64 f;
+    if (bgv) {
+      f = t % q;
+    } else {
+      const u64 tinv = zn::powmod(t % q, q - 2, q);
+      f = (q - mulmod_h(Qt % q, tinv, q)) % q;
+    }
+    A.f[i] = f;
+    A.fs[i] = zn::shoup(f, q);
+  }
+}
+
+// Decryption constants (see zn::IntDec).
+void int_dec_consts(const zn_ctx* c, uint64_t t, zn::IntDec& D) {
+  std::memset(&D, 0, sizeof(D));
+  D.t = t;
+  u64 Qt = 1 % t;
+  for (uint32_t j = 0; j < c->L; ++j) Qt = mulmod_h(Qt, c->q[j] % t, t);
+  D.Qt = Qt;
+  for (uint32_t i = 0; i < c->L; ++i) {
+    const u64 q = c->q[i];
+    u64 rest = 1 % q, rest_t = 1 % t;
+    for (uint32_t j = 0; j < c->L; ++j) {
+      if (j == i) continue;
+      rest = mulmod_h(rest, c->q[j] % q, q);
+      rest_t = mulmod_h(rest_t, c->q[j] % t, t);
+    }
+    const u64 y = zn::powmod(rest, q - 2, q);
+    const unsigned __int128 ty = (unsigned __int128)t * y;
+    D.y[i] = y;
+    D.It[i] = (u64)((ty / q) % t);
+    D.r[i] = (u64)(ty % q);
+    D.Qit[i] = rest_t;
+  }
+}
+
+// Ciphertexts per prep/encrypt launch pair: me (8N) + small (3N) within ~48 MiB,
+// in equal chunks.
+uint32_t int_chunk(const zn_ctx* c, uint32_t batch) {
+  size_t k = (48ull << 20) / (11 * (size_t)c->n);
+  if (k < 1) k = 1;
+  if (k > 65535) k = 65535;
+  const size_t chunks = (batch + k - 1) / k;
+  return (uint32_t)((batch + chunks - 1) / chunks);
+}
+
+// BFV / BGV encryption (vanilla under key/keys, Zinc over the cache `key`).
+// m == nullptr: the zero plaintext; ct_index == nullptr: index b.
+int int_common(zn_ctx* c, bool bgv, bool zinc, const u64* key, const u64* keys, uint64_t t, const int64_t* m,
+               uint32_t batch, uint64_t seed, unsigned domain, const uint64_t* ct_index, uint64_t* ct,
+               cudaStream_t st) {
+  const uint32_t chunk = int_chunk(c, batch);
+  const uint32_t first = batch < chunk ? batch : chunk;
+  const size_t n = c->n;
+  const size_t me_b = sizeof(i64) * first * n, sm_b = (zinc ? 2 : 3) * (size_t)first * n;
+  Scratch scratch(c, st);
+  if (!scratch.alloc(me_b + sm_b)) return ZN_ENOMEM;
+  zn::IntArgs A;
+  std::memset(&A, 0, sizeof(A));
+  int_enc_consts(c, t, bgv, A);
+  A.swap = 0;
+  A.key = key;
+  A.keys = keys;
+  A.me = (const i64*)scratch.p;
+  A.small = (const int8_t*)scratch.p + me_b;
+  for (uint32_t b0 = 0; b0 < batch; b0 += chunk) {
+    const uint32_t nb = (batch - b0) < chunk ? (batch - b0) : chunk;
+    zn::IntPrepArgs pa;
+    pa.m = m ? m + (size_t)b0 * n : nullptr;
+    pa.t = t;
+    pa.seed = seed;
+    pa.domain = domain;
+    pa.ct_index = ct_index ? ct_index + b0 : nullptr;
+    pa.ct_index0 = b0;
+    pa.me = (i64*)A.me;
+    pa.small = (int8_t*)A.small;
+    A.out = ct + (size_t)b0 * 2 * ring_words(c);
+    {
+      TimedLaunch tl(c, ZN_TIME_ENCODE, st);
+      ZN_CUDA(zn::launch_prep_int(c->dp, pa, bgv, zinc, nb, st));
+    }
+    TimedLaunch tl(c, zinc ? ZN_TIME_ZINC : ZN_TIME_ENCRYPT, st);
+    ZN_CUDA(zn::launch_encrypt_int(c->dp, A, bgv, zinc, nb, st));
+  }
+  return ZN_OK;
+}
+
+int int_decrypt(zn_ctx* c, const zn_sk* sk, uint64_t t, bool bgv, const uint64_t* ct, uint32_t batch, int64_t* m,
+                cudaStream_t st) {
+  zn::IntDec D;
+  int_dec_consts(c, t, D);
+  const size_t per = sizeof(u64) * ring_words(c);
+  size_t k = (256ull << 20) / per;
+  if (k < 1) k = 1;
+  const uint32_t chunk = (uint32_t)(k < batch ? k : batch);
+  Scratch scratch(c, st);
+  if (!scratch.alloc(per * chunk)) return ZN_ENOMEM;
+  u64* x = (u64*)scratch.p;
+  for (uint32_t b0 = 0; b0 < batch; b0 += chunk) {
+    const uint32_t nb = (batch - b0) < chunk ? (batch - b0) : chunk;
+    ZN_CUDA(zn::launch_dec_mul(c->dp, ct + (size_t)b0 * 2 * ring_words(c), sk->d, nb, x, st));
+    ZN_CUDA(zn::launch_ntt_inv(c->dp, x, nb, st));
+    ZN_CUDA(zn::launch_int_decode(c->dp, D, bgv, x, nb, m + (size_t)b0 * c->n, st));
+  }
+  return ZN_OK;
+}
+
+inline bool int_ring(const zn_ctx* c) { return c->prm.log_n >= 10 && c->prm.log_n <= 15; }
 
 }  // namespace
 
@@ -823,6 +960,127 @@ int zinc_precompute_ms(zn_ctx* c, const zn_pk* pk, uint64_t seed, zn_ctx* dc, zn
   }
   *out = z;
   return ZN_OK;
+}
+
+// ------------------------------------------------------------ BFV / BGV
+
+int bfv_encrypt(zn_ctx* c, const zn_pk* pk, uint64_t t, const int64_t* m, uint32_t batch, uint64_t seed,
+                const uint64_t* ct_index, uint64_t* ct, void* stream) {
+  if (!c || !pk_of(pk, c) || !int_ring(c) || !t_ok(c, t)) return ZN_EINVAL;
+  if (batch == 0) return ZN_OK;
+  if (!m || !ct_index || !ct) return ZN_EINVAL;
+  DeviceGuard g(c->device);
+  return int_common(c, false, false, pk->d, pk->d + 2 * ring_words(c), t, m, batch, seed, 0u, ct_index, ct,
+                    S(stream));
+}
+
+int bfv_zinc_encrypt(zn_ctx* c, const zn_zcache* z, uint64_t t, const int64_t* m, uint32_t batch, uint64_t seed,
+                     const uint64_t* ct_index, uint64_t* ct, void* stream) {
+  if (!c || !zc_of(z, c) || !int_ring(c) || !t_ok(c, t)) return ZN_EINVAL;
+  if (batch == 0) return ZN_OK;
+  if (!m || !ct_index || !ct) return ZN_EINVAL;
+  DeviceGuard g(c->device);
+  return int_common(c, false, true, z->d, nullptr, t, m, batch, seed, 1u, ct_index, ct, S(stream));
+}
+
+int bgv_keygen(zn_ctx* c, uint64_t t, uint64_t seed, zn_sk** sk, zn_pk** pk) {
+  if (!c || !sk || !pk || !int_ring(c) || !t_ok(c, t)) return ZN_EINVAL;
+  int rc = ckks_keygen(c, seed, sk, pk);
+  if (rc) return rc;
+  DeviceGuard g(c->device);
+  zn_pk* k = *pk;
+  const size_t rw = ring_words(c);
+  i64* e = nullptr;
+  u64* eh = nullptr;
+  u64* tmp = nullptr;
+  if (cudaMalloc(&e, sizeof(i64) * c->n) != cudaSuccess || cudaMalloc(&eh, sizeof(u64) * rw) != cudaSuccess ||
+      cudaMalloc(&tmp, sizeof(u64) * rw) != cudaSuccess) {
+    rc = ZN_ENOMEM;
+  } else if (zn::launch_sample(c->dp, 1, seed, 2, 2, 0, 0, 1, e, 0) != cudaSuccess ||   // Gen's e (domain 2, poly 2)
+             zn::launch_residues(c->dp, e, eh, 0) != cudaSuccess ||
+             zn::launch_ntt_fwd(c->dp, eh, 1, tmp, 0) != cudaSuccess ||
+             zn::launch_bgv_key(c->dp, t, eh, k->d, k->d + 2 * rw, 0) != cudaSuccess ||
+             cudaDeviceSynchronize() != cudaSuccess) {
+    rc = ZN_ECUDA;
+  }
+  cudaGetLastError();
+  cudaFree(e);
+  cudaFree(eh);
+  cudaFree(tmp);
+  if (rc) {
+    zn_sk_destroy(*sk);
+    zn_pk_destroy(k);
+    *sk = nullptr;
+    *pk = nullptr;
+    return rc;
+  }
+  cudaFree(k->ms);          // the SEAL-ordered key forms belong to Gen's key
+  k->ms = nullptr;
+  k->t = t;
+  return ZN_OK;
+}
+
+int bgv_zinc_precompute(zn_ctx* c, const zn_pk* pk, uint64_t seed, zn_zcache** out) {
+  if (!c || !bgv_pk_of(pk, c) || !out) return ZN_EINVAL;
+  *out = nullptr;
+  DeviceGuard g(c->device);
+  zn_zcache* z = new (std::nothrow) zn_zcache();
+  if (!z) return ZN_ENOMEM;
+  z->ctx = c;
+  z->t = pk->t;
+  if (cudaMalloc(&z->d, sizeof(u64) * 2 * ring_words(c)) != cudaSuccess) {
+    cudaGetLastError();
+    delete z;
+    return ZN_ENOMEM;
+  }
+  // a BGV encryption of the zero plaintext, sampling domain 3, ct_index 0
+  int rc = int_common(c, true, false, pk->d, pk->d + 2 * ring_words(c), pk->t, nullptr, 1, seed, 3u, nullptr, z->d,
+                      0);
+  if (!rc && cudaDeviceSynchronize() != cudaSuccess) rc = ZN_ECUDA;
+  if (rc) {
+    cudaGetLastError();
+    zn_zcache_destroy(z);
+    return rc;
+  }
+  *out = z;
+  return ZN_OK;
+}
+
+int bgv_encrypt(zn_ctx* c, const zn_pk* pk, const int64_t* m, uint32_t batch, uint64_t seed,
+                const uint64_t* ct_index, uint64_t* ct, void* stream) {
+  if (!c || !bgv_pk_of(pk, c)) return ZN_EINVAL;
+  if (batch == 0) return ZN_OK;
+  if (!m || !ct_index || !ct) return ZN_EINVAL;
+  DeviceGuard g(c->device);
+  return int_common(c, true, false, pk->d, pk->d + 2 * ring_words(c), pk->t, m, batch, seed, 0u, ct_index, ct,
+                    S(stream));
+}
+
+int bgv_zinc_encrypt(zn_ctx* c, const zn_zcache* z, const int64_t* m, uint32_t batch, uint64_t seed,
+                     const uint64_t* ct_index, uint64_t* ct, void* stream) {
+  if (!c || !bgv_zc_of(z, c)) return ZN_EINVAL;
+  if (batch == 0) return ZN_OK;
+  if (!m || !ct_index || !ct) return ZN_EINVAL;
+  DeviceGuard g(c->device);
+  return int_common(c, true, true, z->d, nullptr, z->t, m, batch, seed, 1u, ct_index, ct, S(stream));
+}
+
+int bfv_decrypt(zn_ctx* c, const zn_sk* sk, uint64_t t, const uint64_t* ct, uint32_t batch, int64_t* m,
+                void* stream) {
+  if (!c || !sk_of(sk, c) || !int_ring(c) || !t_ok(c, t)) return ZN_EINVAL;
+  if (batch == 0) return ZN_OK;
+  if (!ct || !m) return ZN_EINVAL;
+  DeviceGuard g(c->device);
+  return int_decrypt(c, sk, t, false, ct, batch, m, S(stream));
+}
+
+int bgv_decrypt(zn_ctx* c, const zn_sk* sk, uint64_t t, const uint64_t* ct, uint32_t batch, int64_t* m,
+                void* stream) {
+  if (!c || !sk_of(sk, c) || !int_ring(c) || !t_ok(c, t)) return ZN_EINVAL;
+  if (batch == 0) return ZN_OK;
+  if (!ct || !m) return ZN_EINVAL;
+  DeviceGuard g(c->device);
+  return int_decrypt(c, sk, t, true, ct, batch, m, S(stream));
 }
 
 // -------------------------------------------------------------- decrypt

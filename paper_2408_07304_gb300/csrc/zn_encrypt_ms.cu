@@ -16,7 +16,7 @@
 // Kernels: k_ms_special (one block per component and ciphertext; N = 2^15 as
 // two half blocks plus k_ms_special_top), then k_encrypt_ms (the data primes,
 // in the launch shapes of the plain encryption's radix-8 kernels).
-#include "zn_kernels.h"
+#include "zn_encrypt_fn.cuh"
 
 namespace zn {
 
@@ -172,43 +172,6 @@ __global__ void k_ms_special_top(DevParams P, MsArgs A, uint32_t batch) {
   }
 }
 
-// --------------------------------------------------- generators from values
-// As gen_i64 and its variants, for a coefficient given by v(k) in [0, q).
-template <int LOGN, int KM, class V>
-__device__ __forceinline__ void gen_val(u64* sm, int t, int nt, V& v) {
-  for (int k = t; k < (1 << LOGN); k += nt) sm[swz<LOGN, KM>(k)] = v(k);
-}
-
-template <int LOGN, int KM, bool RELAX, class V>
-__device__ __forceinline__ void gen_val_top(u64* sm, int t, int nt, V& v, u64 q, ulonglong2 w1) {
-  constexpr int H = (1 << LOGN) / 2;
-  for (int k = t; k < H; k += nt) {
-    u64 x = v(k), y = v(k + H);
-    bfly<RELAX>(x, y, w1, q);
-    sm[swz<LOGN, KM>(k)] = x;
-    sm[swz<LOGN, KM>(k + H)] = y;
-  }
-}
-
-template <int LOGH, int KM, class V>
-__device__ __forceinline__ void gen_val_half(u64* sm, int t, int nt, int h, V& v, u64 q, u64 w1, u64 w1s) {
-  constexpr int HALF = 1 << LOGH;
-  for (int k = t; k < HALF; k += nt) sm[swz<LOGH, KM>(k)] = first_stage(v(k), v(k + HALF), h, w1, w1s, q);
-}
-
-template <int LOGH, int KM, bool RELAX, class V>
-__device__ __forceinline__ void gen_val_half2(u64* sm, int t, int nt, int h, V& v, u64 q, ulonglong2 w1,
-                                              ulonglong2 w2) {
-  constexpr int HALF = 1 << LOGH, Q2 = HALF / 2;
-  for (int k = t; k < Q2; k += nt) {
-    u64 x = first_stage(v(k), v(k + HALF), h, w1.x, w1.y, q);
-    u64 y = first_stage(v(k + Q2), v(k + Q2 + HALF), h, w1.x, w1.y, q);
-    bfly<RELAX>(x, y, w2, q);
-    sm[swz<LOGH, KM>(k)] = x;
-    sm[swz<LOGH, KM>(k + Q2)] = y;
-  }
-}
-
 // The data prime's transform inputs, in [0, 2q):
 //   first component   d_0 p^-1 + m = D_0 p^-1 + M + kc0   (mod q)
 //   second component  d_1 p^-1     = D_1 p^-1 + kc1       (mod q)
@@ -231,90 +194,45 @@ struct MsVal {
 };
 
 // ------------------------------------------------------------ data primes
-// Data prime i of ciphertext b, N = 2^LOGN <= 2^14, in the schedules of
-// encrypt_unit_q (radix 2^KM, top stage in the generator for radix-8 chains
-// with LOGN = 1 mod 3, staged last pass for radix 8).
+// Data prime i of ciphertext b: the vanilla-shaped generic unit with the
+// p^-1-scaled keys and the MsVal inputs.
 template <int LOGN, int LOGPER, bool RELAX, int KM>
 __device__ __forceinline__ void ms_unit_q(const DevParams& P, const MsArgs& A, int i, size_t b, u64* sm, int t) {
-  using S = NttShape<LOGN, LOGPER>;
-  // inputs below 2q, 2q per relaxed stage, 2q from the key product
-  static_assert(!RELAX || 2 + 2 * LOGN + 2 <= 32, "relaxed sums must stay below 32q");
-  constexpr int N = S::N;
-  constexpr bool TOP = KM == 3 && LOGN % 3 == 1;
-  constexpr int HI = TOP ? LOGN - 1 : LOGN;
+  constexpr int N = 1 << LOGN;
   const int Ld = P.L - 1;
-  const u64 q = P.q[i], mu = P.mu[i];
-  const ulonglong2* tw = P.twp + (size_t)i * N;
-  u64* c0 = A.out + (b * 2 * Ld + i) * N;
-  u64* c1 = c0 + (size_t)Ld * N;
-  const int8_t* sp = A.small + b * 3 * N;
-  const u64* k0 = A.keyms + (size_t)i * N;
-  const u64* k1 = k0 + (size_t)Ld * N;
-  const u64* k0s = k0 + 2 * (size_t)Ld * N;
-  const u64* k1s = k1 + 2 * (size_t)Ld * N;
-  const MsVal v0{A.d + b * 2 * N, A.m + b * N, q, mu, A.pinv[i], A.pinvs[i], A.kc0[i]};
-  const MsVal v1{A.d + b * 2 * N + N, nullptr, q, mu, A.pinv[i], A.pinvs[i], A.kc1[i]};
-  if constexpr (TOP) gen_i8_top<LOGN, KM, RELAX>(sm, t, S::T, sp, q, __ldg(tw + 1));
-  else gen_i8<LOGN, KM>(sm, t, S::T, sp, q);
-  auto st_u = [&](int idx, u64 uh) {
-    c0[idx] = mul_shoup(uh, __ldg(k0 + idx), __ldg(k0s + idx), q);
-    c1[idx] = mul_shoup(uh, __ldg(k1 + idx), __ldg(k1s + idx), q);
-  };
-  ntt_chain<LOGN, LOGPER, HI, RELAX, decltype(st_u), KM, true, KM == 3>(sm, t, tw, 1, q, st_u);
-  __syncthreads();
-  if constexpr (TOP) gen_val_top<LOGN, KM, RELAX>(sm, t, S::T, v0, q, __ldg(tw + 1));
-  else gen_val<LOGN, KM>(sm, t, S::T, v0);
-  auto st_0 = [&](int idx, u64 x) { c0[idx] = reduce_sum<RELAX>(c0[idx] + x, q); };
-  ntt_chain<LOGN, LOGPER, HI, RELAX, decltype(st_0), KM, true, KM == 3>(sm, t, tw, 1, q, st_0);
-  __syncthreads();
-  if constexpr (TOP) gen_val_top<LOGN, KM, RELAX>(sm, t, S::T, v1, q, __ldg(tw + 1));
-  else gen_val<LOGN, KM>(sm, t, S::T, v1);
-  auto st_1 = [&](int idx, u64 x) { c1[idx] = reduce_sum<RELAX>(c1[idx] + x, q); };
-  ntt_chain<LOGN, LOGPER, HI, RELAX, decltype(st_1), KM, true, KM == 3>(sm, t, tw, 1, q, st_1);
+  const u64 q = P.q[i];
+  FnLimb o;
+  o.c0 = A.out + (b * 2 * Ld + i) * N;
+  o.c1 = o.c0 + (size_t)Ld * N;
+  o.k0 = A.keyms + (size_t)i * N;
+  o.k1 = o.k0 + (size_t)Ld * N;
+  o.k0s = o.k0 + 2 * (size_t)Ld * N;
+  o.k1s = o.k1 + 2 * (size_t)Ld * N;
+  o.u = A.small + b * 3 * N;
+  const MsVal v0{A.d + b * 2 * N, A.m + b * N, q, P.mu[i], A.pinv[i], A.pinvs[i], A.kc0[i]};
+  const MsVal v1{A.d + b * 2 * N + N, nullptr, q, P.mu[i], A.pinv[i], A.pinvs[i], A.kc1[i]};
+  fn_unit_q<LOGN, LOGPER, RELAX, KM, false>(P.twp + (size_t)i * N, q, o, v0, v1, sm, t);
 }
 
-// Output half h of data prime i, N = 2^(LOGH+1) (encrypt_half_unit_q's schedule).
+// Output half h of data prime i, N = 2^(LOGH+1).
 template <int LOGH, int LOGPER, bool RELAX, int KM>
 __device__ __forceinline__ void ms_half_unit_q(const DevParams& P, const MsArgs& A, int i, int h, size_t b, u64* sm,
                                                int t) {
-  using S = NttShape<LOGH, LOGPER>;
   constexpr int N = 2 << LOGH, HALF = 1 << LOGH;
-  constexpr bool RAW = !RELAX || 4 + 2 * LOGH + 2 <= 32;
-  constexpr bool TOP = KM == 3 && LOGH % 3 == 1;
-  constexpr int HI = TOP ? LOGH - 1 : LOGH;
   const int Ld = P.L - 1;
-  const u64 q = P.q[i], mu = P.mu[i];
-  const ulonglong2* tw = P.twp + (size_t)i * N;
-  const ulonglong2 w1p = __ldg(tw + 1);
+  const u64 q = P.q[i];
   const size_t off = (size_t)h * HALF;
-  u64* c0 = A.out + (b * 2 * Ld + i) * N + off;
-  u64* c1 = c0 + (size_t)Ld * N;
-  const int8_t* sp = A.small + b * 3 * N;
-  const u64* k0 = A.keyms + (size_t)i * N + off;
-  const u64* k1 = k0 + (size_t)Ld * N;
-  const u64* k0s = k0 + 2 * (size_t)Ld * N;
-  const u64* k1s = k1 + 2 * (size_t)Ld * N;
-  const MsVal v0{A.d + b * 2 * N, A.m + b * N, q, mu, A.pinv[i], A.pinvs[i], A.kc0[i]};
-  const MsVal v1{A.d + b * 2 * N + N, nullptr, q, mu, A.pinv[i], A.pinvs[i], A.kc1[i]};
-  const int tmul = 2 + h;
-  auto sum = [&](u64 a, u64 x) { return RAW ? reduce_sum<RELAX>(a + x, q) : reduce4(a + x, q); };
-  if constexpr (TOP) gen_i8_half2<LOGH, KM, RELAX>(sm, t, S::T, h, sp, q, w1p, __ldg(tw + tmul));
-  else gen_i8_half<LOGH, KM>(sm, t, S::T, h, sp, q, w1p.x, w1p.y);
-  auto st_u = [&](int idx, u64 uh) {
-    c0[idx] = mul_shoup(uh, __ldg(k0 + idx), __ldg(k0s + idx), q);
-    c1[idx] = mul_shoup(uh, __ldg(k1 + idx), __ldg(k1s + idx), q);
-  };
-  ntt_chain<LOGH, LOGPER, HI, RELAX, decltype(st_u), KM, true, KM == 3>(sm, t, tw, tmul, q, st_u);
-  __syncthreads();
-  if constexpr (TOP) gen_val_half2<LOGH, KM, RELAX>(sm, t, S::T, h, v0, q, w1p, __ldg(tw + tmul));
-  else gen_val_half<LOGH, KM>(sm, t, S::T, h, v0, q, w1p.x, w1p.y);
-  auto st_0 = [&](int idx, u64 x) { c0[idx] = sum(c0[idx], x); };
-  ntt_chain<LOGH, LOGPER, HI, RELAX, decltype(st_0), KM, RAW, KM == 3>(sm, t, tw, tmul, q, st_0);
-  __syncthreads();
-  if constexpr (TOP) gen_val_half2<LOGH, KM, RELAX>(sm, t, S::T, h, v1, q, w1p, __ldg(tw + tmul));
-  else gen_val_half<LOGH, KM>(sm, t, S::T, h, v1, q, w1p.x, w1p.y);
-  auto st_1 = [&](int idx, u64 x) { c1[idx] = sum(c1[idx], x); };
-  ntt_chain<LOGH, LOGPER, HI, RELAX, decltype(st_1), KM, RAW, KM == 3>(sm, t, tw, tmul, q, st_1);
+  FnLimb o;
+  o.c0 = A.out + (b * 2 * Ld + i) * N + off;
+  o.c1 = o.c0 + (size_t)Ld * N;
+  o.k0 = A.keyms + (size_t)i * N + off;
+  o.k1 = o.k0 + (size_t)Ld * N;
+  o.k0s = o.k0 + 2 * (size_t)Ld * N;
+  o.k1s = o.k1 + 2 * (size_t)Ld * N;
+  o.u = A.small + b * 3 * N;
+  const MsVal v0{A.d + b * 2 * N, A.m + b * N, q, P.mu[i], A.pinv[i], A.pinvs[i], A.kc0[i]};
+  const MsVal v1{A.d + b * 2 * N + N, nullptr, q, P.mu[i], A.pinv[i], A.pinvs[i], A.kc1[i]};
+  fn_half_unit_q<LOGH, LOGPER, RELAX, KM, false>(P.twp + (size_t)i * N, q, h, o, v0, v1, sm, t);
 }
 
 // grid (L-1, B), or (B, L-1) when A.swap

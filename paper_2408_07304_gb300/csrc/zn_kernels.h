@@ -119,4 +119,52 @@ cudaError_t launch_ms_keys(const DevParams& P, const MsArgs& A, const u64* pk, u
 cudaError_t launch_ms_special(const DevParams& P, const MsArgs& A, uint32_t batch, cudaStream_t st);
 cudaError_t launch_ms_data(const DevParams& P, const MsArgs& A, uint32_t batch, cudaStream_t st);
 
+// ------------------------------------------- BFV (Eq. 12) and BGV (Eq. 13)
+// Coefficient plaintexts m in Z_t (int64, taken mod t).  The prep kernel
+// draws the randomness once per ciphertext (same tags as the CKKS path) and
+// writes me = m mod t (BFV) or m mod t + t e_a (BGV), e_a = e0 (vanilla) or
+// e1' (Zinc), with small = [u, e0, e1] (vanilla) or [e1', e2'] (Zinc).
+struct IntPrepArgs {
+  const i64* m;         // [B][N] plaintext coefficients, or nullptr (zero plaintext)
+  u64 t;
+  u64 seed;
+  unsigned domain;
+  const u64* ct_index;  // [B] or nullptr (then ct_index0 + b)
+  u64 ct_index0;
+  i64* me;              // [B][N]
+  int8_t* small;        // [B][3][N] vanilla, [B][2][N] Zinc
+};
+struct IntArgs {
+  int swap;             // grid order, as EncArgs
+  const u64* key;       // vanilla: pk [2][L][N]; Zinc: cache [2][L][N]
+  const u64* keys;      // vanilla: Shoup companions [2][L][N]
+  const i64* me;        // [B][N] from the prep kernel
+  const int8_t* small;  // [B][3 or 2][N] from the prep kernel
+  u64* out;             // [B][2][L][N]
+  u64 f[kMaxL];         // BFV: Delta mod q_i (Delta = floor(Q/t)); BGV: t mod q_i
+  u64 fs[kMaxL];        // Shoup companions
+};
+// Decryption constants for the chain q_0..q_{L-1} (Q their product):
+//   y_i = (Q/q_i)^-1 mod q_i;  BFV: t y_i = I_i q_i + r_i, It_i = I_i mod t;
+//   BGV: Qi_t = (Q/q_i) mod t, Q_t = Q mod t.
+struct IntDec {
+  u64 t;
+  u64 y[kMaxL];
+  u64 It[kMaxL];
+  u64 r[kMaxL];
+  u64 Qit[kMaxL];
+  u64 Qt;
+};
+cudaError_t launch_prep_int(const DevParams& P, const IntPrepArgs& A, bool bgv, bool zinc, uint32_t batch,
+                            cudaStream_t st);
+cudaError_t launch_encrypt_int(const DevParams& P, const IntArgs& A, bool bgv, bool zinc, uint32_t batch,
+                               cudaStream_t st);
+// x: [B][L][N] coefficient residues of c0 + c1 s (Dec, Eq. 10) -> m [B][N] in [0, t).
+cudaError_t launch_int_decode(const DevParams& P, const IntDec& D, bool bgv, const u64* x, uint32_t batch, i64* m,
+                              cudaStream_t st);
+// pk0 += (t - 1) e-hat (per prime, NTT form) and its Shoup companions: Gen's key becomes BGV's.
+cudaError_t launch_bgv_key(const DevParams& P, u64 t, const u64* ehat, u64* pk, u64* pks, cudaStream_t st);
+// residues [L][N] of a signed int64 polynomial [N]
+cudaError_t launch_residues(const DevParams& P, const i64* v, u64* out, cudaStream_t st);
+
 }  // namespace zn

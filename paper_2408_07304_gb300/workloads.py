@@ -74,6 +74,18 @@ def slots(w: Workload, batch: int = None, first: int = 0, n_slots: int = None, s
     return out
 
 
+def int_plaintexts(w: Workload, t: int, batch: int = None, first: int = 0, seed: int = None):
+    """Coefficient plaintexts for BFV / BGV: int64 [batch, N] uniform in [0, t),
+    vector b drawn from its own stream (seed, first + b, t)."""
+    batch = w.batch if batch is None else batch
+    seed = w.seed if seed is None else seed
+    out = np.empty((batch, w.n), dtype=np.int64)
+    for b in range(batch):
+        rng = np.random.Generator(np.random.PCG64([seed, first + b, t]))
+        out[b] = rng.integers(0, t, w.n, dtype=np.int64)
+    return out
+
+
 def small(log_n, bits, log2_delta, batch, n_slots, seed=0, lo=-1.0, hi=1.0):
     """An ad-hoc uniform workload (tests)."""
     return Workload(f"n{1 << log_n}", log_n, tuple(bits), log2_delta, batch, n_slots, "uniform", lo, hi, seed)
