@@ -19,6 +19,8 @@ ring       definitional negacyclic NTT and schoolbook products (C, via ctypes)
 ckks       Gen (Eq. 7), Enc (Eq. 8), Enc_z (Algorithm 1, Eq. 9), Dec (Eq. 10),
            the modulus-switched (special-prime) Enc
 bfvbgv     BFV (Eq. 12) and BGV (Eq. 13) encryption, their Zinc forms, Dec
+nttrand    Zinc with its errors generated in the NTT domain (a reading of the
+           Conclusion's O(N) remark): rotations of a cached error basis
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test against a
 closed form, brute force, an invariant, or an independent library routine,
