@@ -345,6 +345,43 @@ def run_ours(args, w):
                 "paper_speedup_context": "Table 2 totals, CKKS over Zinc: 2.34x, 2.51x, 2.44x (SEAL, one EPYC 7302P thread, N=32768)"}
         del out_m, out_mz, zc_d, dctx
 
+    # ---- BFV (Eq. 12) and BGV (Eq. 13), vanilla and Zinc, on the same ring
+    # and chain: coefficient plaintexts uniform in [0, t), t = 65537
+    intl = None
+    if not args.no_int and 10 <= w.log_n <= 15:
+        t_pt = 65537
+        m_int = torch.tensor(workloads.int_plaintexts(w, t_pt, batch=B, first=rank * B), device=dev)
+        out_i = torch.empty((B, 2, w.L, w.n), dtype=torch.int64, device=dev)
+        gsk, gpk = api.bgv_keygen(ctx, t_pt, workloads.KEYGEN_SEED)
+        gzc = api.bgv_zinc_precompute(ctx, gpk, workloads.CACHE_SEED)
+        legs = {"bfv": lambda: api.bfv_encrypt(ctx, pk, t_pt, m_int, w.seed, idx, out=out_i, stream=stream),
+                "bfv_zinc": lambda: api.bfv_zinc_encrypt(ctx, zc, t_pt, m_int, w.seed, idx, out=out_i, stream=stream),
+                "bgv": lambda: api.bgv_encrypt(ctx, gpk, m_int, w.seed, idx, out=out_i, stream=stream),
+                "bgv_zinc": lambda: api.bgv_zinc_encrypt(ctx, gzc, m_int, w.seed, idx, out=out_i, stream=stream)}
+        rates = {}
+        for name, fn in legs.items():
+            for _ in range(args.warmup):
+                fn()
+            torch.cuda.synchronize(dev)
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            t_ms = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
+            if world > 1:
+                dist.all_reduce(t_ms, op=dist.ReduceOp.MAX)
+            rates[name + "_enc_s"] = B * world * args.steps / (float(t_ms.item()) / 1e3)
+        api.zn_sync_status(ctx, stream)
+        # every plaintext of the last (BGV Zinc) batch decrypts exactly
+        ok = bool(torch.equal(api.bgv_decrypt(ctx, gsk, t_pt, out_i), m_int))
+        intl = dict(rates, t=t_pt, plaintext="coefficients uniform in [0, t)",
+                    bfv_zinc_speedup=rates["bfv_zinc_enc_s"] / rates["bfv_enc_s"],
+                    bgv_zinc_speedup=rates["bgv_zinc_enc_s"] / rates["bgv_enc_s"], decrypt_exact=ok)
+        del out_i, m_int, gzc, gpk, gsk
+
     # ---- end to end through the host-buffer entry point: every step copies
     # the slot vectors and ct indices in (once per mode) and every ciphertext
     # out, pipelined in chunks over three streams
@@ -398,7 +435,7 @@ def run_ours(args, w):
             "vanilla_enc_s": van_rate, "zinc_enc_s": zin_rate, "zinc_speedup": zin_rate / van_rate,
             "hbm_roofline_frac": value * per_ct_bytes / (hbm_peak * 1e9),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-            "serving": serving, "persistent_graph": persistent, "special_prime": seal,
+            "serving": serving, "persistent_graph": persistent, "special_prime": seal, "bfv_bgv": intl,
             "kernel_ms_per_launch": {"prep": enc_ms / max(enc_n, 1), "encrypt_vanilla": kv_avg,
                                      "encrypt_zinc": kz_avg},
             "autotune": {"variant": tune[0], "ms_per_variant": tune[1]},
@@ -423,6 +460,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving (p50/p99) run")
     ap.add_argument("--no-persistent", action="store_true", help="skip the persistent-graph path")
     ap.add_argument("--no-special", action="store_true", help="skip the special-prime (SEAL-ordered) leg")
+    ap.add_argument("--no-int", action="store_true", help="skip the BFV / BGV leg")
     ap.add_argument("--serve-requests", type=int, default=20000)
     args = ap.parse_args()
     w = workloads.WORKLOADS[args.workload]

@@ -54,6 +54,7 @@ typedef struct zn_ctx zn_ctx;
 typedef struct zn_sk zn_sk;
 typedef struct zn_pk zn_pk;
 typedef struct zn_zcache zn_zcache;
+typedef struct zn_nbasis zn_nbasis;
 
 /* Parameter set.  log_n in [4, 15]; n_primes in [1, ZN_MAX_PRIMES];
  * prime_bits[i] in [20, 61]; log2_delta in [1, 62].  The error distribution
@@ -247,6 +248,35 @@ int bgv_zinc_encrypt(zn_ctx* ctx, const zn_zcache* zc, const int64_t* m, uint32_
 int bgv_decrypt(zn_ctx* ctx, const zn_sk* sk, uint64_t t, const uint64_t* ct, uint32_t batch, int64_t* m,
                 void* stream);
 
+/* ------------------------------- Zinc with NTT-domain errors (O(N) encryption)
+ *
+ * The paper's Conclusion names a further optimisation: generating the random
+ * error polynomials directly in the Fourier (NTT) space, which removes Zinc's
+ * two transforms per prime.  The paper gives no construction; this library's
+ * reading, a change of the error distribution with no security claim:
+ *   - a basis of K cached chi polynomials per component, E_{c,j} (domain 4,
+ *     poly 16c + j, ct_index 0, the basis seed), kept in NTT form;
+ *   - per ciphertext, rotations r_{c,j} uniform in [0, 2N) (Philox block j of
+ *     domain 5, poly c, the ciphertext's seed and ct_index, word 0);
+ *   - e'_c = sum_j X^{r_{c,j}} E_{c,j} (X^N = -1): each coefficient is a sum
+ *     of K chi values (variance K sigma^2, |e'| <= 19 K);
+ *   - over a plaintext already encoded in NTT form (the paper's Construction
+ *     assumes an encoded m): c' = (z0 + m + e'_0, z1 + e'_1).
+ * In NTT form X^r multiplies output i by psi^((2 brv(i) + 1) r mod 2N), so
+ * the encryption is pointwise: per prime and coefficient 2K table lookups
+ * and 4K Shoup products.  Ring degrees 2^10..2^15.
+ *
+ * zinc_nbasis_create: K in [1, 16]; synchronous.  ckks_encode_ntt: the CKKS
+ * encoding (as ckks_encode) reduced mod each q_i and transformed: out device
+ * uint64 [batch][L][N].  zinc_encrypt_ntt: zc from zinc_precompute; m_hat
+ * device uint64 [batch][L][N] (from ckks_encode_ntt); ct as zinc_encrypt. */
+int zinc_nbasis_create(zn_ctx* ctx, uint32_t K, uint64_t seed, zn_nbasis** out);
+void zn_nbasis_destroy(zn_nbasis* nb);
+int ckks_encode_ntt(zn_ctx* ctx, const double* slots, uint32_t n_slots, uint32_t batch, uint64_t* out,
+                    void* stream);
+int zinc_encrypt_ntt(zn_ctx* ctx, const zn_zcache* zc, const zn_nbasis* nb, const uint64_t* m_hat,
+                     uint32_t batch, uint64_t seed, const uint64_t* ct_index, uint64_t* ct, void* stream);
+
 /* Host memory in, host memory out: copies slot vectors and ct indices to the
  * device, encrypts -- vanilla (Eq. 8) under pk when zc is NULL, Zinc
  * (Algorithm 1) under zc otherwise (pass exactly one) -- and copies the
@@ -377,7 +407,8 @@ enum {
   ZN_TIME_ZINC = 2,        /* Zinc encryption kernel                           */
   ZN_TIME_MS_SPECIAL = 3,  /* modulus-switched vanilla: special-prime kernels  */
   ZN_TIME_MS_DATA = 4,     /* modulus-switched vanilla: data-prime kernel      */
-  ZN_TIME_KINDS = 5
+  ZN_TIME_ZINC_NTT = 5,    /* Zinc with NTT-domain errors                      */
+  ZN_TIME_KINDS = 6
 };
 
 /* on != 0: every later kernel launch of the kinds above in this context is

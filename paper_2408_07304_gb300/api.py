@@ -65,6 +65,10 @@ _SIGS = {
     "zinc_encrypt_noalloc": (_i32, [_vp, _vp, _vp, _u32, _u32, _u64, _vp, _vp, _vp]),
     "ckks_encrypt_ms": (_i32, [_vp, _vp, _vp, _u32, _u32, _u64, _vp, _vp, _vp]),
     "zinc_precompute_ms": (_i32, [_vp, _vp, _u64, _vp, _pp]),
+    "zinc_nbasis_create": (_i32, [_vp, _u32, _u64, _pp]),
+    "zn_nbasis_destroy": (None, [_vp]),
+    "ckks_encode_ntt": (_i32, [_vp, _vp, _u32, _u32, _vp, _vp]),
+    "zinc_encrypt_ntt": (_i32, [_vp, _vp, _vp, _vp, _u32, _u64, _vp, _vp, _vp]),
     "bfv_encrypt": (_i32, [_vp, _vp, _u64, _vp, _u32, _u64, _vp, _vp, _vp]),
     "bfv_zinc_encrypt": (_i32, [_vp, _vp, _u64, _vp, _u32, _u64, _vp, _vp, _vp]),
     "bfv_decrypt": (_i32, [_vp, _vp, _u64, _vp, _u32, _vp, _vp]),
@@ -226,6 +230,10 @@ class ZincCache(_Handle):
     _destroy = "zn_zcache_destroy"
 
 
+class NttBasis(_Handle):
+    _destroy = "zn_nbasis_destroy"
+
+
 # ------------------------------------------------------------ entry points
 
 def zn_ctx_create(log_n, prime_bits, log2_delta, device=0):
@@ -374,6 +382,42 @@ def zinc_precompute_ms(ctx, pk, seed, data_ctx):
     _check(lib().zinc_precompute_ms(ctx.handle, pk.handle, seed, data_ctx.handle, ctypes.byref(h)),
            "zinc_precompute_ms")
     return ZincCache(data_ctx, h)
+
+
+# ------------------------------------------- Zinc with NTT-domain errors
+
+def zinc_nbasis_create(ctx, K, seed):
+    """Cached error basis (K chi polynomials per component, NTT form) and rotation tables."""
+    h = ctypes.c_void_p()
+    _check(lib().zinc_nbasis_create(ctx.handle, K, seed, ctypes.byref(h)), "zinc_nbasis_create")
+    nb = NttBasis(ctx, h)
+    nb.K = K
+    return nb
+
+
+def ckks_encode_ntt(ctx, slots, out=None, stream=None):
+    """slots: CUDA float64 [B, n_slots] -> pre-encoded plaintexts int64 [B, L, N] (uint64 residues, NTT form)."""
+    import torch
+    B, ns = slots.shape
+    out = _out(out, (B, ctx.L, ctx.n), torch.int64, slots.device)
+    _dev(slots, torch.float64, None, "slots")
+    _dev(out, torch.int64, (B, ctx.L, ctx.n), "out")
+    _check(lib().ckks_encode_ntt(ctx.handle, slots.data_ptr(), ns, B, out.data_ptr(), _stream(stream)),
+           "ckks_encode_ntt")
+    return out
+
+
+def zinc_encrypt_ntt(ctx, zc, nb, m_hat, seed, ct_index, out=None, stream=None):
+    """Zinc with NTT-domain errors: m_hat int64 [B, L, N] (from ckks_encode_ntt) -> int64 [B, 2, L, N]."""
+    import torch
+    B = m_hat.shape[0]
+    out = _out(out, (B, 2, ctx.L, ctx.n), torch.int64, m_hat.device)
+    _dev(m_hat, torch.int64, (B, ctx.L, ctx.n), "m_hat")
+    _dev(ct_index, torch.int64, (B,), "ct_index")
+    _dev(out, torch.int64, (B, 2, ctx.L, ctx.n), "out")
+    _check(lib().zinc_encrypt_ntt(ctx.handle, zc.handle, nb.handle, m_hat.data_ptr(), B, seed, ct_index.data_ptr(),
+                                  out.data_ptr(), _stream(stream)), "zinc_encrypt_ntt")
+    return out
 
 
 # ------------------------------------------------ BFV (Eq. 12), BGV (Eq. 13)
@@ -621,7 +665,7 @@ def zn_probe_butterfly(device=0):
     return r.value
 
 
-TIME_ENCODE, TIME_ENCRYPT, TIME_ZINC, TIME_MS_SPECIAL, TIME_MS_DATA = 0, 1, 2, 3, 4
+TIME_ENCODE, TIME_ENCRYPT, TIME_ZINC, TIME_MS_SPECIAL, TIME_MS_DATA, TIME_ZINC_NTT = 0, 1, 2, 3, 4, 5
 
 
 def zn_timing_enable(ctx, on=True):

@@ -38,7 +38,17 @@ struct zn_ctx {
 };
 
 // Handle type tags: an opaque pointer of the wrong kind is rejected (ZN_EINVAL).
-enum : uint32_t { kTagPk = 0x6b70u, kTagSk = 0x6b73u, kTagZc = 0x637au, kTagDead = 0u };
+enum : uint32_t { kTagPk = 0x6b70u, kTagSk = 0x6b73u, kTagZc = 0x637au, kTagNb = 0x626eu, kTagDead = 0u };
+
+// Cached error basis of the NTT-domain Zinc randomiser, and the rotation tables.
+struct zn_nbasis {
+  uint32_t tag = kTagNb;
+  zn_ctx* ctx;
+  uint32_t K;
+  u64* E;                  // [2][K][L][N] NTT form
+  ulonglong2* thi;         // [L][N/32] (psi^(64 h), Shoup companion)
+  ulonglong2* tlo;         // [L][64]   (psi^l, Shoup companion)
+};
 
 struct zn_pk {
   uint32_t tag = kTagPk;
@@ -1081,6 +1091,119 @@ int bgv_decrypt(zn_ctx* c, const zn_sk* sk, uint64_t t, const uint64_t* ct, uint
   if (!ct || !m) return ZN_EINVAL;
   DeviceGuard g(c->device);
   return int_decrypt(c, sk, t, true, ct, batch, m, S(stream));
+}
+
+// ------------------------------------------- Zinc with NTT-domain errors
+
+void zn_nbasis_destroy(zn_nbasis* nb) {
+  if (!nb || nb->tag != kTagNb) return;
+  nb->tag = kTagDead;
+  DeviceGuard g(nb->ctx->device);
+  cudaFree(nb->E);
+  cudaFree(nb->thi);
+  cudaFree(nb->tlo);
+  delete nb;
+}
+
+int zinc_nbasis_create(zn_ctx* c, uint32_t K, uint64_t seed, zn_nbasis** out) {
+  if (!c || !out || K < 1 || K > 16 || !int_ring(c)) return ZN_EINVAL;
+  *out = nullptr;
+  DeviceGuard g(c->device);
+  zn_nbasis* nb = new (std::nothrow) zn_nbasis();
+  if (!nb) return ZN_ENOMEM;
+  nb->ctx = c;
+  nb->K = K;
+  const size_t n = c->n, rw = ring_words(c), nhi = n / 32;
+  // power tables on the host: psi^(64 h), h < 2N/64, and psi^l, l < 64, per prime
+  std::vector<ulonglong2> hi(c->L * nhi), lo(c->L * 64);
+  for (uint32_t i = 0; i < c->L; ++i) {
+    const u64 q = c->q[i], psi = c->psi[i], p64 = zn::powmod(psi, 64, q);
+    u64 v = 1;
+    for (size_t h = 0; h < nhi; ++h, v = mulmod_h(v, p64, q)) hi[i * nhi + h] = make_ulonglong2(v, zn::shoup(v, q));
+    v = 1;
+    for (int l = 0; l < 64; ++l, v = mulmod_h(v, psi, q)) lo[i * 64 + l] = make_ulonglong2(v, zn::shoup(v, q));
+  }
+  i64* e = nullptr;
+  u64* tmp = nullptr;
+  int rc = ZN_OK;
+  if (cudaMalloc(&nb->E, sizeof(u64) * 2 * K * rw) != cudaSuccess ||
+      cudaMalloc(&nb->thi, sizeof(ulonglong2) * hi.size()) != cudaSuccess ||
+      cudaMalloc(&nb->tlo, sizeof(ulonglong2) * lo.size()) != cudaSuccess ||
+      cudaMalloc(&e, sizeof(i64) * n) != cudaSuccess || cudaMalloc(&tmp, sizeof(u64) * rw) != cudaSuccess) {
+    rc = ZN_ENOMEM;
+  } else if (cudaMemcpy(nb->thi, hi.data(), sizeof(ulonglong2) * hi.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+             cudaMemcpy(nb->tlo, lo.data(), sizeof(ulonglong2) * lo.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+    rc = ZN_ECUDA;
+  } else {
+    // E_{c,j} <- chi (domain 4, poly 16 c + j, ct_index 0), residues, forward NTT
+    for (uint32_t cj = 0; cj < 2 * K && !rc; ++cj) {
+      const uint32_t cc = cj / K, j = cj % K;
+      u64* slot = nb->E + (size_t)cj * rw;
+      if (zn::launch_sample(c->dp, 1, seed, 4, 16 * cc + j, 0, 0, 1, e, 0) != cudaSuccess ||
+          zn::launch_residues(c->dp, e, slot, 0) != cudaSuccess ||
+          zn::launch_ntt_fwd(c->dp, slot, 1, tmp, 0) != cudaSuccess)
+        rc = ZN_ECUDA;
+    }
+    if (!rc && cudaDeviceSynchronize() != cudaSuccess) rc = ZN_ECUDA;
+  }
+  cudaGetLastError();
+  cudaFree(e);
+  cudaFree(tmp);
+  if (rc) {
+    zn_nbasis_destroy(nb);
+    return rc;
+  }
+  *out = nb;
+  return ZN_OK;
+}
+
+int ckks_encode_ntt(zn_ctx* c, const double* slots, uint32_t n_slots, uint32_t batch, uint64_t* out, void* stream) {
+  if (!c || n_slots > c->n / 2) return ZN_EINVAL;
+  if (batch == 0) return ZN_OK;
+  if (!out || (n_slots && !slots)) return ZN_EINVAL;
+  DeviceGuard g(c->device);
+  const size_t n = c->n, rw = ring_words(c);
+  size_t k = (256ull << 20) / (sizeof(u64) * rw);
+  if (k < 1) k = 1;
+  const uint32_t chunk = (uint32_t)(k < batch ? k : batch);
+  const bool big = c->prm.log_n == 15;    // the 2^15 forward transform goes through a copy
+  Scratch scratch(c, S(stream));
+  if (!scratch.alloc(sizeof(i64) * chunk * n + (big ? sizeof(u64) * chunk * rw : 0))) return ZN_ENOMEM;
+  i64* coef = (i64*)scratch.p;
+  u64* tmp = big ? (u64*)((unsigned char*)scratch.p + sizeof(i64) * chunk * n) : nullptr;
+  for (uint32_t b0 = 0; b0 < batch; b0 += chunk) {
+    const uint32_t nb = (batch - b0) < chunk ? (batch - b0) : chunk;
+    u64* o = out + (size_t)b0 * rw;
+    ZN_CUDA(zn::launch_encode(c->dp, n_slots ? slots + (size_t)b0 * n_slots : nullptr, n_slots, nb, coef, S(stream)));
+    ZN_CUDA(zn::launch_residues_batch(c->dp, coef, nb, o, S(stream)));
+    ZN_CUDA(zn::launch_ntt_fwd(c->dp, o, nb, tmp, S(stream)));
+  }
+  return ZN_OK;
+}
+
+int zinc_encrypt_ntt(zn_ctx* c, const zn_zcache* z, const zn_nbasis* nb, const uint64_t* m_hat, uint32_t batch,
+                     uint64_t seed, const uint64_t* ct_index, uint64_t* ct, void* stream) {
+  if (!c || !zc_of(z, c) || !nb || nb->tag != kTagNb || nb->ctx != c) return ZN_EINVAL;
+  if (batch == 0) return ZN_OK;
+  if (!m_hat || !ct_index || !ct) return ZN_EINVAL;
+  DeviceGuard g(c->device);
+  zn::NttZincArgs A;
+  A.z = z->d;
+  A.E = nb->E;
+  A.thi = nb->thi;
+  A.tlo = nb->tlo;
+  A.seed = seed;
+  A.K = (int)nb->K;
+  const size_t rw = ring_words(c);
+  for (uint32_t b0 = 0; b0 < batch; b0 += 65535) {
+    const uint32_t n_b = (batch - b0) < 65535 ? (batch - b0) : 65535;
+    A.m = m_hat + (size_t)b0 * rw;
+    A.ct_index = ct_index + b0;
+    A.out = ct + (size_t)b0 * 2 * rw;
+    TimedLaunch t(c, ZN_TIME_ZINC_NTT, S(stream));
+    ZN_CUDA(zn::launch_zinc_ntt(c->dp, A, n_b, S(stream)));
+  }
+  return ZN_OK;
 }
 
 // -------------------------------------------------------------- decrypt

@@ -162,6 +162,25 @@ cudaError_t launch_encrypt_int(const DevParams& P, const IntArgs& A, bool bgv, b
 // x: [B][L][N] coefficient residues of c0 + c1 s (Dec, Eq. 10) -> m [B][N] in [0, t).
 cudaError_t launch_int_decode(const DevParams& P, const IntDec& D, bool bgv, const u64* x, uint32_t batch, i64* m,
                               cudaStream_t st);
+// ------------------------------------- Zinc with NTT-domain errors (O(N))
+// e'_c = sum_{j<K} X^{r_{c,j}} E_{c,j}: in NTT form the rotation X^r is the
+// pointwise factor psi^((2 brv(i) + 1) r mod 2N) at output i, taken as
+// thi[e >> 6] * tlo[e & 63] (psi^(64 h) and psi^l, Shoup pairs).
+struct NttZincArgs {
+  const u64* z;           // cached zero [2][L][N]
+  const u64* E;           // basis [2][K][L][N], NTT form
+  const ulonglong2* thi;  // [L][N/32] (psi^(64 h), Shoup companion)
+  const ulonglong2* tlo;  // [L][64]   (psi^l, Shoup companion)
+  const u64* m;           // [B][L][N] pre-encoded plaintexts, NTT form
+  const u64* ct_index;    // [B]
+  u64 seed;
+  u64* out;               // [B][2][L][N]
+  int K;
+};
+cudaError_t launch_zinc_ntt(const DevParams& P, const NttZincArgs& A, uint32_t batch, cudaStream_t st);
+// int64 coefficients [B][N] -> residues [B][L][N]
+cudaError_t launch_residues_batch(const DevParams& P, const i64* v, uint32_t batch, u64* out, cudaStream_t st);
+
 // pk0 += (t - 1) e-hat (per prime, NTT form) and its Shoup companions: Gen's key becomes BGV's.
 cudaError_t launch_bgv_key(const DevParams& P, u64 t, const u64* ehat, u64* pk, u64* pks, cudaStream_t st);
 // residues [L][N] of a signed int64 polynomial [N]

@@ -20,6 +20,7 @@ import numpy as np
 
 KEYGEN_SEED = 1     # Gen
 CACHE_SEED = 2      # the cached Enc(0)
+NBASIS_SEED = 3     # the cached error basis of the NTT-domain Zinc randomiser
 
 
 @dataclass(frozen=True)
