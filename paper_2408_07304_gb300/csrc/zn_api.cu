@@ -46,8 +46,8 @@ struct zn_nbasis {
   zn_ctx* ctx;
   uint32_t K;
   u64* E;                  // [2][K][L][N] NTT form
-  ulonglong2* thi;         // [L][N/32] (psi^(64 h), Shoup companion)
-  ulonglong2* tlo;         // [L][64]   (psi^l, Shoup companion)
+  u64* thi;                // [L][N/32] psi^(64 h) mod q
+  u64* tlo;                // [L][64]   psi^l 2^64 mod q (Montgomery form)
 };
 
 struct zn_pk {
@@ -1114,25 +1114,27 @@ int zinc_nbasis_create(zn_ctx* c, uint32_t K, uint64_t seed, zn_nbasis** out) {
   nb->ctx = c;
   nb->K = K;
   const size_t n = c->n, rw = ring_words(c), nhi = n / 32;
-  // power tables on the host: psi^(64 h), h < 2N/64, and psi^l, l < 64, per prime
-  std::vector<ulonglong2> hi(c->L * nhi), lo(c->L * 64);
+  // power tables on the host: psi^(64 h), h < 2N/64, and psi^l 2^64 (the
+  // Montgomery form, so that one Montgomery product of the two is psi^e), per prime
+  std::vector<u64> hi(c->L * nhi), lo(c->L * 64);
   for (uint32_t i = 0; i < c->L; ++i) {
     const u64 q = c->q[i], psi = c->psi[i], p64 = zn::powmod(psi, 64, q);
+    const u64 r64 = (u64)((((unsigned __int128)1) << 64) % q);
     u64 v = 1;
-    for (size_t h = 0; h < nhi; ++h, v = mulmod_h(v, p64, q)) hi[i * nhi + h] = make_ulonglong2(v, zn::shoup(v, q));
-    v = 1;
-    for (int l = 0; l < 64; ++l, v = mulmod_h(v, psi, q)) lo[i * 64 + l] = make_ulonglong2(v, zn::shoup(v, q));
+    for (size_t h = 0; h < nhi; ++h, v = mulmod_h(v, p64, q)) hi[i * nhi + h] = v;
+    v = r64;
+    for (int l = 0; l < 64; ++l, v = mulmod_h(v, psi, q)) lo[i * 64 + l] = v;
   }
   i64* e = nullptr;
   u64* tmp = nullptr;
   int rc = ZN_OK;
   if (cudaMalloc(&nb->E, sizeof(u64) * 2 * K * rw) != cudaSuccess ||
-      cudaMalloc(&nb->thi, sizeof(ulonglong2) * hi.size()) != cudaSuccess ||
-      cudaMalloc(&nb->tlo, sizeof(ulonglong2) * lo.size()) != cudaSuccess ||
+      cudaMalloc(&nb->thi, sizeof(u64) * hi.size()) != cudaSuccess ||
+      cudaMalloc(&nb->tlo, sizeof(u64) * lo.size()) != cudaSuccess ||
       cudaMalloc(&e, sizeof(i64) * n) != cudaSuccess || cudaMalloc(&tmp, sizeof(u64) * rw) != cudaSuccess) {
     rc = ZN_ENOMEM;
-  } else if (cudaMemcpy(nb->thi, hi.data(), sizeof(ulonglong2) * hi.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-             cudaMemcpy(nb->tlo, lo.data(), sizeof(ulonglong2) * lo.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+  } else if (cudaMemcpy(nb->thi, hi.data(), sizeof(u64) * hi.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+             cudaMemcpy(nb->tlo, lo.data(), sizeof(u64) * lo.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
     rc = ZN_ECUDA;
   } else {
     // E_{c,j} <- chi (domain 4, poly 16 c + j, ct_index 0), residues, forward NTT
@@ -1188,6 +1190,12 @@ int zinc_encrypt_ntt(zn_ctx* c, const zn_zcache* z, const zn_nbasis* nb, const u
   if (!m_hat || !ct_index || !ct) return ZN_EINVAL;
   DeviceGuard g(c->device);
   zn::NttZincArgs A;
+  std::memset(&A, 0, sizeof(A));
+  for (uint32_t i = 0; i < c->L; ++i) {
+    u64 inv = 1;                          // q^-1 mod 2^64 by Newton's iteration (q odd)
+    for (int it = 0; it < 6; ++it) inv *= 2 - c->q[i] * inv;
+    A.qneg[i] = (u64)0 - inv;
+  }
   A.z = z->d;
   A.E = nb->E;
   A.thi = nb->thi;

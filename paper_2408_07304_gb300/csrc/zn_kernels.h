@@ -164,18 +164,22 @@ cudaError_t launch_int_decode(const DevParams& P, const IntDec& D, bool bgv, con
                               cudaStream_t st);
 // ------------------------------------- Zinc with NTT-domain errors (O(N))
 // e'_c = sum_{j<K} X^{r_{c,j}} E_{c,j}: in NTT form the rotation X^r is the
-// pointwise factor psi^((2 brv(i) + 1) r mod 2N) at output i, taken as
-// thi[e >> 6] * tlo[e & 63] (psi^(64 h) and psi^l, Shoup pairs).
+// pointwise factor psi^(a r mod 2N) at output i, a = 2 brv(i) + 1.  With
+// i = t + 256 k (t < 256), a = 2^(n-7) brv_8(t) + 2 brv_(n-8)(k) + 1, so the
+// factor splits into flo[t] * fhi[k]; a block builds both tables per
+// rotation (with Shoup companions) from psi^(64 h) and psi^l 2^64 (one
+// Montgomery product each) and multiplies by Shoup products.
 struct NttZincArgs {
   const u64* z;           // cached zero [2][L][N]
   const u64* E;           // basis [2][K][L][N], NTT form
-  const ulonglong2* thi;  // [L][N/32] (psi^(64 h), Shoup companion)
-  const ulonglong2* tlo;  // [L][64]   (psi^l, Shoup companion)
+  const u64* thi;         // [L][N/32] psi^(64 h) mod q
+  const u64* tlo;         // [L][64]   psi^l 2^64 mod q (Montgomery form)
   const u64* m;           // [B][L][N] pre-encoded plaintexts, NTT form
   const u64* ct_index;    // [B]
   u64 seed;
   u64* out;               // [B][2][L][N]
   int K;
+  u64 qneg[kMaxL];        // -q_i^-1 mod 2^64 (Montgomery)
 };
 cudaError_t launch_zinc_ntt(const DevParams& P, const NttZincArgs& A, uint32_t batch, cudaStream_t st);
 // int64 coefficients [B][N] -> residues [B][L][N]
