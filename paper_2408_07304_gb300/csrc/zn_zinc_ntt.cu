@@ -29,12 +29,15 @@ __device__ __forceinline__ u64 mont_mul(u64 a, u64 b, u64 q, u64 qneg) {
 // (mod q, from psi^(64 h) and psi^l), each with its Shoup companion, so that
 // a basis value times its factor is two Shoup products; fhi[k] is read by
 // the whole warp at once (broadcast), flo[t] by each thread at its own slot.
+// K is a template parameter so that the term loop unrolls and each
+// thread's flo entries stay in registers across its trips.
+template <int K>
 __global__ void __launch_bounds__(256, 4) k_zinc_ntt(DevParams P, NttZincArgs A) {
   extern __shared__ ulonglong2 s_tab[];   // [2][K][N/256] fhi, then [2][K][256] flo
   __shared__ unsigned s_r[32];            // [2][16]
   const int i = blockIdx.x;
   const size_t b = blockIdx.y;
-  const int log_n = P.log_n, N = 1 << log_n, L = P.L, K = A.K, NK = N >> 8;
+  const int log_n = P.log_n, N = 1 << log_n, L = P.L, NK = N >> 8;
   const unsigned mask2n = 2u * N - 1;
   const u64 q = P.q[i], qn = A.qneg[i];
   const int t = threadIdx.x;
@@ -73,14 +76,23 @@ __global__ void __launch_bounds__(256, 4) k_zinc_ntt(DevParams P, NttZincArgs A)
   const size_t estride = (size_t)L * N;          // between basis polynomials of one prime
   const u64* E0 = A.E + (size_t)i * N + t;       // E_{0,0} at prime i, this thread's column
   const u64* E1 = E0 + (size_t)K * estride;      // E_{1,0}
-#pragma unroll 2
+  constexpr bool REG = K <= 4;                   // flo in registers (no spills up to K = 4)
+  constexpr int UNJ = REG ? K : 1;               // term loop unrolled only then
+  constexpr int UNK = K <= 2 ? 2 : 1;
+  ulonglong2 lo[REG ? 2 * K : 1];
+  if constexpr (REG) {
+#pragma unroll
+    for (int cj = 0; cj < 2 * K; ++cj) lo[cj] = flo[cj * 256 + t];
+  }
+#pragma unroll UNK
   for (int k = 0; k < NK; ++k) {
     const int idx = t + (k << 8);
     u64 acc0 = __ldg(z0 + idx) + __ldg(m + idx);  // [0, 2q)
     u64 acc1 = __ldg(z1 + idx);
+#pragma unroll UNJ
     for (int j = 0; j < K; ++j) {
-      const ulonglong2 h0 = fhi[j * NK + k], l0 = flo[j * 256 + t];
-      const ulonglong2 h1 = fhi[(K + j) * NK + k], l1 = flo[(K + j) * 256 + t];
+      const ulonglong2 h0 = fhi[j * NK + k], l0 = REG ? lo[REG ? j : 0] : flo[j * 256 + t];
+      const ulonglong2 h1 = fhi[(K + j) * NK + k], l1 = REG ? lo[REG ? K + j : 0] : flo[(K + j) * 256 + t];
       const u64 x = mul_shoup(mul_shoup(__ldg(E0 + j * estride + (k << 8)), h0.x, h0.y, q), l0.x, l0.y, q);
       const u64 y = mul_shoup(mul_shoup(__ldg(E1 + j * estride + (k << 8)), h1.x, h1.y, q), l1.x, l1.y, q);
       acc0 += x;
@@ -103,14 +115,36 @@ __global__ void k_residues_batch(DevParams P, const i64* __restrict__ v, uint32_
   }
 }
 
+template <int K>
+static cudaError_t zinc_ntt_k(const DevParams& P, const NttZincArgs& A, uint32_t batch, cudaStream_t st) {
+  const size_t smem = sizeof(ulonglong2) * 2 * K * ((1u << (P.log_n - 8)) + 256);
+  cudaError_t e = cudaFuncSetAttribute(k_zinc_ntt<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_zinc_ntt<K><<<dim3(P.L, batch), 256, smem, st>>>(P, A);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_zinc_ntt(const DevParams& P, const NttZincArgs& A, uint32_t batch, cudaStream_t st) {
   if (batch == 0) return cudaSuccess;
   if (P.log_n < 10 || P.log_n > 15 || A.K < 1 || A.K > 16) return cudaErrorInvalidValue;
-  const size_t smem = sizeof(ulonglong2) * 2 * A.K * ((1u << (P.log_n - 8)) + 256);
-  cudaError_t e = cudaFuncSetAttribute(k_zinc_ntt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  k_zinc_ntt<<<dim3(P.L, batch), 256, smem, st>>>(P, A);
-  return cudaGetLastError();
+  switch (A.K) {
+    case 1: return zinc_ntt_k<1>(P, A, batch, st);
+    case 2: return zinc_ntt_k<2>(P, A, batch, st);
+    case 3: return zinc_ntt_k<3>(P, A, batch, st);
+    case 4: return zinc_ntt_k<4>(P, A, batch, st);
+    case 5: return zinc_ntt_k<5>(P, A, batch, st);
+    case 6: return zinc_ntt_k<6>(P, A, batch, st);
+    case 7: return zinc_ntt_k<7>(P, A, batch, st);
+    case 8: return zinc_ntt_k<8>(P, A, batch, st);
+    case 9: return zinc_ntt_k<9>(P, A, batch, st);
+    case 10: return zinc_ntt_k<10>(P, A, batch, st);
+    case 11: return zinc_ntt_k<11>(P, A, batch, st);
+    case 12: return zinc_ntt_k<12>(P, A, batch, st);
+    case 13: return zinc_ntt_k<13>(P, A, batch, st);
+    case 14: return zinc_ntt_k<14>(P, A, batch, st);
+    case 15: return zinc_ntt_k<15>(P, A, batch, st);
+    default: return zinc_ntt_k<16>(P, A, batch, st);
+  }
 }
 
 cudaError_t launch_residues_batch(const DevParams& P, const i64* v, uint32_t batch, u64* out, cudaStream_t st) {
