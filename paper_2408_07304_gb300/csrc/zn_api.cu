@@ -538,6 +538,7 @@ int zn_ctx_create(const zn_params* p, int device, zn_ctx** out) {
     const u64 q = c->q[i];
     dp.q[i] = q;
     dp.mu[i] = (u64)((((unsigned __int128)1) << 64) / q);
+    dp.moff[i] = (q - zn::powmod(2, 62, q)) % q;
     dp.ninv[i] = zn::powmod(n % q, q - 2, q);
     dp.ninvs[i] = zn::shoup(dp.ninv[i], q);
   }

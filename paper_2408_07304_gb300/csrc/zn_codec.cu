@@ -109,6 +109,7 @@ __global__ void k_encode_smem(DevParams P, const double* __restrict__ slots, uin
 // for all q_i):
 //   vanilla (Eq. 8):    me = m + e0 (poly 1), small = [u (poly 0), e1 (poly 2)]
 //   Zinc (Algorithm 1): me = m + e1' (poly 0), small = [e2' (poly 1)]
+//   (me stored with the offset 2^62)
 //   modulus-switched vanilla (MS): me = m + 2^62, small = [u, e0, e1] (polys
 //     0, 1, 2; the noise enters before the division by the special prime, m
 //     after it)
@@ -147,9 +148,11 @@ __device__ __forceinline__ void prep_one(const DevParams& P, const PrepArgs& A, 
       sp[N + k] = (int8_t)cdt_search(w.x, w.y, cdt);
       sp[N + k + n] = (int8_t)cdt_search(w.z, w.w, cdt);
     } else {
+      // m + e with the offset 2^62 (non-negative as an unsigned word; the
+      // encryption units remove it with reduce_biased)
       const i64 a = A.n_slots ? me[k] : 0, c = A.n_slots ? me[k + n] : 0;
-      me[k] = a + cdt_search(w.x, w.y, cdt);
-      me[k + n] = c + cdt_search(w.z, w.w, cdt);
+      me[k] = (i64)((u64)(a + cdt_search(w.x, w.y, cdt)) + kMsOffset);
+      me[k + n] = (i64)((u64)(c + cdt_search(w.z, w.w, cdt)) + kMsOffset);
     }
   }
   if constexpr (!ZINC) {

@@ -24,6 +24,7 @@ struct DevParams {
   int log_n, L, log2_delta, pad;
   u64 q[kMaxL];
   u64 mu[kMaxL];             // floor(2^64 / q): Barrett reduction
+  u64 moff[kMaxL];           // -2^62 mod q: removes the offset of the prepared int64 polynomials
   u64 ninv[kMaxL];           // N^-1 mod q
   u64 ninvs[kMaxL];          // its Shoup companion
   u64 q0inv_mod_q1;          // CRT (decode)
@@ -66,6 +67,14 @@ __device__ __forceinline__ u64 reduce_signed(i64 x, u64 q, u64 mu) {
   u64 r = a - __umul64hi(a, mu) * q;       // [0, 2q)
   if (r >= q) r -= q;
   return (x < 0 && r) ? q - r : r;
+}
+
+// x = v + 2^62 (stored unsigned) for a signed v with |v| < 2^62 + 2^5 ->
+// v mod q in [0, 2q): one Barrett step leaves x mod q in [0, 2q), moff =
+// -2^62 mod q removes the offset.
+__device__ __forceinline__ u64 reduce_biased(u64 x, u64 q, u64 mu, u64 moff) {
+  const u64 r = x - __umul64hi(x, mu) * q + moff;   // [0, 3q)
+  return r >= 2 * q ? r - q : r;
 }
 
 // small signed integer (|v| < q) -> residue
@@ -360,11 +369,12 @@ __device__ __forceinline__ void gen_copy(u64* sm, const u64* __restrict__ a) {
   for (int k = threadIdx.x; k < (1 << LOGN); k += blockDim.x) sm[swz<LOGN>(k)] = a[k];
 }
 
-// Encoded message plus noise (int64) from the per-ciphertext scratch; thread t
-// of nt.
+// Encoded message plus noise from the per-ciphertext scratch, stored with the
+// offset 2^62 (see reduce_biased), into [0, 2q); thread t of nt.
 template <int LOGN, int KM = 4>
-__device__ __forceinline__ void gen_i64(u64* sm, int t, int nt, const i64* __restrict__ a, u64 q, u64 mu) {
-  for (int k = t; k < (1 << LOGN); k += nt) sm[swz<LOGN, KM>(k)] = reduce_signed(__ldg(a + k), q, mu);
+__device__ __forceinline__ void gen_i64(u64* sm, int t, int nt, const i64* __restrict__ a, u64 q, u64 mu,
+                                        u64 moff) {
+  for (int k = t; k < (1 << LOGN); k += nt) sm[swz<LOGN, KM>(k)] = reduce_biased((u64)__ldg(a + k), q, mu, moff);
 }
 
 // Small signed polynomial (int8) from the per-ciphertext scratch.
@@ -384,10 +394,10 @@ __device__ __forceinline__ void bfly(u64& x, u64& y, ulonglong2 w, u64 q) {
 
 template <int LOGN, int KM, bool RELAX>
 __device__ __forceinline__ void gen_i64_top(u64* sm, int t, int nt, const i64* __restrict__ a, u64 q, u64 mu,
-                                            ulonglong2 w1) {
+                                            u64 moff, ulonglong2 w1) {
   constexpr int H = (1 << LOGN) / 2;
   for (int k = t; k < H; k += nt) {
-    u64 x = reduce_signed(__ldg(a + k), q, mu), y = reduce_signed(__ldg(a + k + H), q, mu);
+    u64 x = reduce_biased((u64)__ldg(a + k), q, mu, moff), y = reduce_biased((u64)__ldg(a + k + H), q, mu, moff);
     bfly<RELAX>(x, y, w1, q);
     sm[swz<LOGN, KM>(k)] = x;
     sm[swz<LOGN, KM>(k + H)] = y;
@@ -464,11 +474,11 @@ __device__ __forceinline__ void gen_uniform_half(u64* sm, int h, u64 seed, unsig
 
 template <int LOGH, int KM = 4>
 __device__ __forceinline__ void gen_i64_half(u64* sm, int t, int nt, int h, const i64* __restrict__ a, u64 q, u64 mu,
-                                             u64 w1, u64 w1s) {
+                                             u64 moff, u64 w1, u64 w1s) {
   constexpr int HALF = 1 << LOGH;
   for (int k = t; k < HALF; k += nt)
-    sm[swz<LOGH, KM>(k)] = first_stage(reduce_signed(__ldg(a + k), q, mu), reduce_signed(__ldg(a + k + HALF), q, mu),
-                                       h, w1, w1s, q);
+    sm[swz<LOGH, KM>(k)] = first_stage(reduce_biased((u64)__ldg(a + k), q, mu, moff),
+                                       reduce_biased((u64)__ldg(a + k + HALF), q, mu, moff), h, w1, w1s, q);
 }
 
 template <int LOGH, int KM = 4>
@@ -484,13 +494,13 @@ __device__ __forceinline__ void gen_i8_half(u64* sm, int t, int nt, int h, const
 // per loop trip.  Outputs below 4q (Harvey) or 6q (relaxed).
 template <int LOGH, int KM, bool RELAX>
 __device__ __forceinline__ void gen_i64_half2(u64* sm, int t, int nt, int h, const i64* __restrict__ a, u64 q, u64 mu,
-                                              ulonglong2 w1, ulonglong2 w2) {
+                                              u64 moff, ulonglong2 w1, ulonglong2 w2) {
   constexpr int HALF = 1 << LOGH, Q2 = HALF / 2;
   for (int k = t; k < Q2; k += nt) {
-    u64 x = first_stage(reduce_signed(__ldg(a + k), q, mu), reduce_signed(__ldg(a + k + HALF), q, mu), h, w1.x,
-                        w1.y, q);
-    u64 y = first_stage(reduce_signed(__ldg(a + k + Q2), q, mu), reduce_signed(__ldg(a + k + Q2 + HALF), q, mu), h,
-                        w1.x, w1.y, q);
+    u64 x = first_stage(reduce_biased((u64)__ldg(a + k), q, mu, moff),
+                        reduce_biased((u64)__ldg(a + k + HALF), q, mu, moff), h, w1.x, w1.y, q);
+    u64 y = first_stage(reduce_biased((u64)__ldg(a + k + Q2), q, mu, moff),
+                        reduce_biased((u64)__ldg(a + k + Q2 + HALF), q, mu, moff), h, w1.x, w1.y, q);
     bfly<RELAX>(x, y, w2, q);
     sm[swz<LOGH, KM>(k)] = x;
     sm[swz<LOGH, KM>(k + Q2)] = y;

@@ -19,7 +19,8 @@ namespace zn {
 // runs the same barriers but touches no global memory.  The last NTT pass
 // hands its outputs over unreduced where the epilogue can absorb them: the
 // Shoup product pk*u-hat takes any 64-bit input, and a sum below 32q (relaxed:
-// 2q or q plus q + 2q*LOGN) or 8q (Harvey) is reduced once (reduce_sum).
+// 2q plus 2q + 2q*LOGN, the inputs being below 2q) or 8q (Harvey) is reduced
+// once (reduce_sum).
 // Radix-8 schedules (KM = 3) with LOGN = 1 mod 3 run the top stage in the
 // generator and 3-bit passes over the rest, and stage the last pass through
 // shared memory (its threads own 8 adjacent outputs each).
@@ -27,11 +28,12 @@ template <int LOGN, bool ZINC, int LOGPER, bool RELAX, int KM = 4>
 __device__ __forceinline__ void encrypt_unit_q(const DevParams& P, const EncArgs& A, int i, size_t b, u64* sm, int t,
                                                bool active) {
   using S = NttShape<LOGN, LOGPER>;
-  static_assert(!RELAX || 1 + 2 * LOGN + 2 <= 32, "relaxed sums must stay below 32q");
+  // inputs below 2q (reduce_biased), 2q per relaxed stage, 2q from the key product
+  static_assert(!RELAX || 2 + 2 * LOGN + 2 <= 32, "relaxed sums must stay below 32q");
   constexpr bool TOP = KM == 3 && LOGN % 3 == 1;
   constexpr int HI = TOP ? LOGN - 1 : LOGN;
   const int L = P.L;
-  const u64 q = P.q[i], mu = P.mu[i];
+  const u64 q = P.q[i], mu = P.mu[i], moff = P.moff[i];
   const ulonglong2* tw = P.twp + (size_t)i * S::N;
   u64* c0 = A.out + (b * 2 * L + i) * S::N;
   u64* c1 = c0 + (size_t)L * S::N;
@@ -46,8 +48,8 @@ __device__ __forceinline__ void encrypt_unit_q(const DevParams& P, const EncArgs
   };
   auto load_me = [&]() {
     if (!active) return;
-    if constexpr (TOP) gen_i64_top<LOGN, KM, RELAX>(sm, t, S::T, me, q, mu, __ldg(tw + 1));
-    else gen_i64<LOGN, KM>(sm, t, S::T, me, q, mu);
+    if constexpr (TOP) gen_i64_top<LOGN, KM, RELAX>(sm, t, S::T, me, q, mu, moff, __ldg(tw + 1));
+    else gen_i64<LOGN, KM>(sm, t, S::T, me, q, mu, moff);
   };
   if constexpr (!ZINC) {
     const u64* k0s = A.keys + (size_t)i * S::N;
@@ -102,7 +104,7 @@ __device__ __forceinline__ void encrypt_half_unit_q(const DevParams& P, const En
   constexpr bool TOP = KM == 3 && LOGH % 3 == 1;
   constexpr int HI = TOP ? LOGH - 1 : LOGH;
   const int L = P.L;
-  const u64 q = P.q[i], mu = P.mu[i];
+  const u64 q = P.q[i], mu = P.mu[i], moff = P.moff[i];
   const ulonglong2* tw = P.twp + (size_t)i * N;
   const ulonglong2 w1p = __ldg(tw + 1);
   const u64 w1 = w1p.x, w1s = w1p.y;
@@ -120,8 +122,8 @@ __device__ __forceinline__ void encrypt_half_unit_q(const DevParams& P, const En
     else gen_i8_half<LOGH, KM>(sm, t, S::T, h, src, q, w1, w1s);
   };
   auto load_me = [&]() {
-    if constexpr (TOP) gen_i64_half2<LOGH, KM, RELAX>(sm, t, S::T, h, me, q, mu, w1p, __ldg(tw + tmul));
-    else gen_i64_half<LOGH, KM>(sm, t, S::T, h, me, q, mu, w1, w1s);
+    if constexpr (TOP) gen_i64_half2<LOGH, KM, RELAX>(sm, t, S::T, h, me, q, mu, moff, w1p, __ldg(tw + tmul));
+    else gen_i64_half<LOGH, KM>(sm, t, S::T, h, me, q, mu, moff, w1, w1s);
   };
   if constexpr (!ZINC) {
     const u64* k0s = A.keys + (size_t)i * N + off;
@@ -280,7 +282,7 @@ __device__ __forceinline__ void encrypt_mp_unit_q(const DevParams& P, const EncA
   constexpr int NP = ZINC ? 2 : 3;
   constexpr int T = MpShape<LOGM>::T;
   const int L = P.L;
-  const u64 q = P.q[i], mu = P.mu[i];
+  const u64 q = P.q[i], mu = P.mu[i], moff = P.moff[i];
   const ulonglong2* tw = P.twp + (size_t)i * N;
   const size_t off = (size_t)h * M;
   ulonglong2* c0 = reinterpret_cast<ulonglong2*>(A.out + (b * 2 * L + i) * N + off);
@@ -293,20 +295,20 @@ __device__ __forceinline__ void encrypt_mp_unit_q(const DevParams& P, const EncA
   if constexpr (S == 0) {
     if constexpr (!ZINC) {
       gen_i8<LOGM>(sm, t, T, sp, q);
-      gen_i64<LOGM>(sm + M, t, T, me, q, mu);
+      gen_i64<LOGM>(sm + M, t, T, me, q, mu, moff);
       gen_i8<LOGM>(sm + 2 * M, t, T, sp + N, q);
     } else {
-      gen_i64<LOGM>(sm, t, T, me, q, mu);
+      gen_i64<LOGM>(sm, t, T, me, q, mu, moff);
       gen_i8<LOGM>(sm + M, t, T, sp, q);
     }
   } else {
     const ulonglong2 w1 = __ldg(tw + 1);
     if constexpr (!ZINC) {
       gen_i8_half<LOGM>(sm, t, T, h, sp, q, w1.x, w1.y);
-      gen_i64_half<LOGM>(sm + M, t, T, h, me, q, mu, w1.x, w1.y);
+      gen_i64_half<LOGM>(sm + M, t, T, h, me, q, mu, moff, w1.x, w1.y);
       gen_i8_half<LOGM>(sm + 2 * M, t, T, h, sp + N, q, w1.x, w1.y);
     } else {
-      gen_i64_half<LOGM>(sm, t, T, h, me, q, mu, w1.x, w1.y);
+      gen_i64_half<LOGM>(sm, t, T, h, me, q, mu, moff, w1.x, w1.y);
       gen_i8_half<LOGM>(sm + M, t, T, h, sp, q, w1.x, w1.y);
     }
   }
