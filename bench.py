@@ -310,6 +310,14 @@ def run_ours(args, w):
         host_z = torch.empty(out_z.shape, dtype=torch.int64, pin_memory=True)
         api.zn_encrypt_host(ctx, pk, host_slots, w.seed, host_idx, host_v)      # warm-up
         torch.cuda.synchronize(dev)
+        # the device-to-host link of this machine: one plain copy of the ciphertexts
+        # into the same pinned buffer (the end-to-end rate cannot exceed it)
+        l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0.record(stream)
+        host_v.copy_(out_v, non_blocking=True)
+        l1.record(stream)
+        torch.cuda.synchronize(dev)
+        link_gbs = host_v.numel() * 8 / (l0.elapsed_time(l1) / 1e3) / 1e9
         barrier()
         t_start = time.perf_counter()
         for _ in range(e2e_steps):
@@ -319,7 +327,10 @@ def run_ours(args, w):
         if world > 1:
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
+        link_bound = link_gbs * 1e9 / (2 * w.L * w.n * 8)
         e2e = {"value": 2 * B * world * e2e_steps / e2e_s, "unit": UNIT,
+               "d2h_link_gbs": link_gbs, "link_bound_enc_s": link_bound * world,
+               "of_link_bound": 2 * B * e2e_steps / e2e_s / link_bound,
                "h2d_bytes_per_step": int(2 * (host_slots.numel() * 8 + host_idx.numel() * 8)),
                "d2h_bytes_per_step": int(2 * host_v.numel() * 8),
                "steps": e2e_steps, "api": "zn_encrypt_host (pinned host buffers, chunks of 256 over 3 streams)"}
