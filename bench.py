@@ -154,6 +154,23 @@ def run_reference(args, w):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------ replicas
+def replica_range(rank, batch):
+    """ct_index range [rank * batch, (rank + 1) * batch) of one replica.
+    Encryptions are independent and their randomness is keyed by ct_index,
+    so the ranks share no data and no collective runs on the data path."""
+    return rank * batch, (rank + 1) * batch
+
+
+def max_over_ranks(values, world, device, dist=None):
+    """Element-wise maximum of per-rank timings (all_reduce MAX when world > 1)."""
+    import torch
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
 # ------------------------------------------------------------------ GPU arm
 def modmuls_per_ct(w, zinc):
     """Butterfly-equivalents (Shoup multiplications) per ciphertext: (N/2) log2 N
@@ -180,9 +197,10 @@ def run_ours(args, w):
     sk, pk = api.ckks_keygen(ctx, workloads.KEYGEN_SEED)
     zc = api.zinc_precompute(ctx, pk, workloads.CACHE_SEED)
     B = w.batch
-    z = workloads.slots(w, batch=B, first=rank * B)
+    lo, hi = replica_range(rank, B)
+    z = workloads.slots(w, batch=B, first=lo)
     slots = torch.tensor(z, dtype=torch.float64, device=dev)
-    idx = torch.arange(rank * B, (rank + 1) * B, dtype=torch.int64, device=dev)
+    idx = torch.arange(lo, hi, dtype=torch.int64, device=dev)
     out_v = torch.empty((B, 2, w.L, w.n), dtype=torch.int64, device=dev)
     out_z = torch.empty_like(out_v)
     stream = torch.cuda.current_stream(dev)
@@ -232,10 +250,7 @@ def run_ours(args, w):
     api.zn_sync_status(ctx, stream)
     launches = enc_n + kv_n + kz_n
 
-    t = torch.tensor([total_ms, van_ms, zin_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms, van_ms, zin_ms = [float(x) for x in t.tolist()]
+    total_ms, van_ms, zin_ms = max_over_ranks([total_ms, van_ms, zin_ms], world, dev, dist)
     cts = 2 * B * world * args.steps
     value = cts / (total_ms / 1e3)
     van_rate = B * world * args.steps / (van_ms / 1e3)
@@ -323,10 +338,7 @@ def run_ours(args, w):
         for _ in range(e2e_steps):
             api.zn_encrypt_host(ctx, pk, host_slots, w.seed, host_idx, host_v)
             api.zn_encrypt_host(ctx, zc, host_slots, w.seed, host_idx, host_z)
-        t = torch.tensor([time.perf_counter() - t_start], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+        e2e_s = max_over_ranks([time.perf_counter() - t_start], world, dev, dist)[0]
         link_bound = link_gbs * 1e9 / (2 * w.L * w.n * 8)
         e2e = {"value": 2 * B * world * e2e_steps / e2e_s, "unit": UNIT,
                "d2h_link_gbs": link_gbs, "link_bound_enc_s": link_bound * world,
@@ -369,10 +381,7 @@ def run_ours(args, w):
         api.zn_timing_enable(ctx, False)
         api.zn_sync_status(ctx, stream)
         api.zn_sync_status(dctx, stream)
-        t = torch.tensor([ms_ms, mz_ms], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_ms, mz_ms = [float(x) for x in t.tolist()]
+        ms_ms, mz_ms = max_over_ranks([ms_ms, mz_ms], world, dev, dist)
         ms_rate = B * world * args.steps / (ms_ms / 1e3)
         mz_rate = B * world * args.steps / (mz_ms / 1e3)
         seal = {"vanilla_ms_enc_s": ms_rate, "zinc_data_level_enc_s": mz_rate, "zinc_speedup": mz_rate / ms_rate,
@@ -388,7 +397,7 @@ def run_ours(args, w):
     intl = None
     if not args.no_int and 10 <= w.log_n <= 15:
         t_pt = 65537
-        m_int = torch.tensor(workloads.int_plaintexts(w, t_pt, batch=B, first=rank * B), device=dev)
+        m_int = torch.tensor(workloads.int_plaintexts(w, t_pt, batch=B, first=lo), device=dev)
         out_i = torch.empty((B, 2, w.L, w.n), dtype=torch.int64, device=dev)
         gsk, gpk = api.bgv_keygen(ctx, t_pt, workloads.KEYGEN_SEED)
         gzc = api.bgv_zinc_precompute(ctx, gpk, workloads.CACHE_SEED)
@@ -408,10 +417,8 @@ def run_ours(args, w):
                 fn()
             e1.record(stream)
             torch.cuda.synchronize(dev)
-            t_ms = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
-            if world > 1:
-                dist.all_reduce(t_ms, op=dist.ReduceOp.MAX)
-            rates[name + "_enc_s"] = B * world * args.steps / (float(t_ms.item()) / 1e3)
+            t_ms = max_over_ranks([e0.elapsed_time(e1)], world, dev, dist)[0]
+            rates[name + "_enc_s"] = B * world * args.steps / (t_ms / 1e3)
         api.zn_sync_status(ctx, stream)
         # every plaintext of the last (BGV Zinc) batch decrypts exactly
         ok = bool(torch.equal(api.bgv_decrypt(ctx, gsk, t_pt, out_i), m_int))
@@ -440,10 +447,7 @@ def run_ours(args, w):
                 api.zinc_encrypt_ntt(ctx, zc, nb, m_hat, w.seed, idx, out=out_n, stream=stream)
             e1.record(stream)
             torch.cuda.synchronize(dev)
-            t_ms = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
-            if world > 1:
-                dist.all_reduce(t_ms, op=dist.ReduceOp.MAX)
-            t_ms = float(t_ms.item())
+            t_ms = max_over_ranks([e0.elapsed_time(e1)], world, dev, dist)[0]
             rate = B * world * args.steps / (t_ms / 1e3)
             # algorithmic HBM bytes per ciphertext: the plaintext read and the ciphertext written
             per = 3 * w.L * w.n * 8
