@@ -178,7 +178,6 @@ def test_ms_full_size_sampled(name):
 
 def test_ms_encode_overflow_latched_on_the_key_level_context():
     # an encoded coefficient of 2^62 or more is an overflow: latched, context usable
-    ctx, dctx, pk, _, _ = gpu_model(10, (40, 40, 41), 30, 1, 2)
     bad = gpu_ctx(10, (50, 50, 51), 60)
     _, bpk = api.ckks_keygen(bad, 1)
     api.ckks_encrypt_ms(bad, bpk, dev(np.full((1, 8), 1e6), torch.float64), 0, dev(np.array([0]), torch.int64))
