@@ -426,6 +426,10 @@ int zn_timing_read(zn_ctx* ctx, int kind, double* ms, uint64_t* launches);
  * registers alone (no memory traffic) -- the practical ALU ceiling of every
  * transform in this library.  Synchronous; ~30 ms. */
 int zn_probe_butterfly(int device, double* butterflies_per_s);
+/* The same for the relaxed butterfly (no correction step; the transforms use
+ * it for primes below 2^59), with one fold back to [0, 4q) every 12 stages as
+ * a transform's final reduction would do. */
+int zn_probe_butterfly_relaxed(int device, double* butterflies_per_s);
 
 /* ------------------------------------------------ host-side tables (no GPU) */
 

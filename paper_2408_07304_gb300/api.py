@@ -93,6 +93,7 @@ _SIGS = {
     "zn_get_variant": (_i32, [_vp]),
     "zn_autotune": (_i32, [_vp, _vp, _vp, _u32, _vp, _vp]),
     "zn_probe_butterfly": (_i32, [_i32, _vp]),
+    "zn_probe_butterfly_relaxed": (_i32, [_i32, _vp]),
     "zn_timing_enable": (_i32, [_vp, _i32]),
     "zn_timing_read": (_i32, [_vp, _i32, _vp, _vp]),
     "zn_host_primes": (_i32, [_u32, _vp, _u32, _vp]),
@@ -656,6 +657,13 @@ def zn_autotune(ctx, pk, zc, batch):
     chosen = ctypes.c_int()
     _check(lib().zn_autotune(ctx.handle, pk.handle, zc.handle, batch, ms, ctypes.byref(chosen)), "zn_autotune")
     return chosen.value, [float(x) for x in ms]
+
+
+def zn_probe_butterfly_relaxed(device=0):
+    """Register-only butterflies/s of the relaxed butterfly (primes below 2^59)."""
+    r = ctypes.c_double()
+    _check(lib().zn_probe_butterfly_relaxed(device, ctypes.byref(r)), "zn_probe_butterfly_relaxed")
+    return r.value
 
 
 def zn_probe_butterfly(device=0):

@@ -1561,7 +1561,18 @@ int zn_probe_butterfly(int device, double* per_s) {
     cudaGetLastError();
     return ZN_ECUDA;
   }
-  return zn::probe_butterfly(sms, per_s) == cudaSuccess ? ZN_OK : ZN_ECUDA;
+  return zn::probe_butterfly(sms, per_s, false) == cudaSuccess ? ZN_OK : ZN_ECUDA;
+}
+
+int zn_probe_butterfly_relaxed(int device, double* per_s) {
+  if (!per_s) return ZN_EINVAL;
+  DeviceGuard g(device);
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    cudaGetLastError();
+    return ZN_ECUDA;
+  }
+  return zn::probe_butterfly(sms, per_s, true) == cudaSuccess ? ZN_OK : ZN_ECUDA;
 }
 
 // ------------------------------------------------------------ building blocks

@@ -82,8 +82,9 @@ cudaError_t launch_sample(const DevParams& P, int kind, u64 seed, unsigned domai
                           u64 ct_index0, uint32_t count, i64* out, cudaStream_t st);
 cudaError_t launch_chi_eval(const DevParams& P, const u64* u, uint32_t n, int* out, cudaStream_t st);
 cudaError_t launch_shoup(const DevParams& P, const u64* w, u64* ws, uint32_t polys, cudaStream_t st);
-// Butterflies per second of k_probe_butterfly (register-only ceiling).
-cudaError_t probe_butterfly(int sms, double* per_s);
+// Butterflies per second of k_probe_butterfly (register-only ceiling),
+// corrected (Harvey) or relaxed form.
+cudaError_t probe_butterfly(int sms, double* per_s, bool relaxed);
 cudaError_t launch_sk_residues(const DevParams& P, const int8_t* s, u64* out, cudaStream_t st);
 
 // ------------------------------------------------ modulus-switched encryption
