@@ -172,3 +172,42 @@ def bgv_decrypt(P, K: Keys, c0, c1, t):
     """m = ([c0 + c1 s]_Q centred) mod t."""
     xs, _ = dec_poly(P, K, c0, c1)
     return [x % t for x in xs]
+
+
+# ------------------------------------------------------- batching (slots)
+# Plaintext slots for BFV / BGV (a reading; the paper defers encoding to the
+# schemes' papers): for a prime t = 1 mod 2N with psi_t its minimal primitive
+# 2N-th root, R_t is isomorphic to Z_t^N by evaluation at the odd powers of
+# psi_t.  Slot s < N/2 is the value at psi_t^(5^s mod 2N), slot N/2 + s the
+# value at psi_t^(-5^s mod 2N) (the slot order of the CKKS encoder, both
+# conjugate halves).
+
+def slot_exponents(log_n):
+    """a_s with slot s <-> evaluation at psi_t^(a_s)."""
+    n = 1 << log_n
+    out, g = [], 1
+    for _ in range(n // 2):
+        out.append(g)
+        g = g * 5 % (2 * n)
+    return out + [(2 * n - a) % (2 * n) for a in out]
+
+
+def batch_encode(slots, t, log_n):
+    """The m in R_t with m(psi_t^(a_s)) = slots[s] mod t (coefficients in [0, t))."""
+    from . import numtheory
+    n = 1 << log_n
+    psi = numtheory.find_psi(t, log_n)
+    # the definitional NTT evaluates at psi^(2 brv(i) + 1): place slot s at
+    # the output index i with 2 brv(i) + 1 = a_s
+    y = np.zeros(n, dtype=np.uint64)
+    for s, a in enumerate(slot_exponents(log_n)):
+        y[numtheory.brv((a - 1) // 2, log_n)] = int(slots[s]) % t
+    return [int(v) for v in ring.intt(y, t, psi)]
+
+
+def batch_decode(m, t, log_n):
+    """slots[s] = m(psi_t^(a_s)) mod t."""
+    from . import numtheory
+    psi = numtheory.find_psi(t, log_n)
+    y = ring.ntt(np.array([int(v) % t for v in m], dtype=np.uint64), t, psi)
+    return [int(y[numtheory.brv((a - 1) // 2, log_n)]) for a in slot_exponents(log_n)]
