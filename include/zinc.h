@@ -55,6 +55,7 @@ typedef struct zn_sk zn_sk;
 typedef struct zn_pk zn_pk;
 typedef struct zn_zcache zn_zcache;
 typedef struct zn_nbasis zn_nbasis;
+typedef struct zn_slot_encoder zn_slot_encoder;
 
 /* Parameter set.  log_n in [4, 15]; n_primes in [1, ZN_MAX_PRIMES];
  * prime_bits[i] in [20, 61]; log2_delta in [1, 62].  The error distribution
@@ -231,6 +232,23 @@ int bfv_zinc_encrypt(zn_ctx* ctx, const zn_zcache* zc, uint64_t t, const int64_t
 /* m = round(t [c0 + c1 s]_Q / Q) mod t, out: device int64 [batch][N] in [0, t). */
 int bfv_decrypt(zn_ctx* ctx, const zn_sk* sk, uint64_t t, const uint64_t* ct, uint32_t batch, int64_t* m,
                 void* stream);
+
+/* Slot batching for BFV / BGV plaintexts (the paper leaves plaintext
+ * encoding to the schemes' papers; this is the usual one).  For a prime
+ * t = 1 mod 2N, R_t is isomorphic to Z_t^N by evaluation at the odd powers of
+ * psi_t, the minimal primitive 2N-th root of unity mod t: slot s < N/2 holds
+ * m(psi_t^(5^s mod 2N)) and slot N/2 + s holds m(psi_t^(-5^s mod 2N)) (the
+ * CKKS encoder's slot order), so slot-wise sums and products of vectors are
+ * sums and products in R_t.  zn_slot_encoder_create: t prime, t = 1 mod 2N,
+ * and valid for ctx as above (ZN_EINVAL otherwise); synchronous.
+ * zn_slots_encode: slots device int64 [batch][N] (each taken mod t) -> m
+ * device int64 [batch][N] in [0, t), the plaintext for bfv_* / bgv_*.
+ * zn_slots_decode: the inverse (input taken mod t).  Stream-ordered; not
+ * tuned (one block per vector, radix-2 stages in global memory). */
+int zn_slot_encoder_create(zn_ctx* ctx, uint64_t t, zn_slot_encoder** out);
+void zn_slot_encoder_destroy(zn_slot_encoder* se);
+int zn_slots_encode(zn_slot_encoder* se, const int64_t* slots, uint32_t batch, int64_t* m, void* stream);
+int zn_slots_decode(zn_slot_encoder* se, const int64_t* m, uint32_t batch, int64_t* slots, void* stream);
 
 /* BGV, Eq. 13: the errors carry the factor t.  bgv_keygen: Gen's samples with
  * pk0 = -a*s + t*e (the key records t; zn_pk_import and zn_zcache_import

@@ -65,6 +65,10 @@ _SIGS = {
     "zinc_encrypt_noalloc": (_i32, [_vp, _vp, _vp, _u32, _u32, _u64, _vp, _vp, _vp]),
     "ckks_encrypt_ms": (_i32, [_vp, _vp, _vp, _u32, _u32, _u64, _vp, _vp, _vp]),
     "zinc_precompute_ms": (_i32, [_vp, _vp, _u64, _vp, _pp]),
+    "zn_slot_encoder_create": (_i32, [_vp, _u64, _pp]),
+    "zn_slot_encoder_destroy": (None, [_vp]),
+    "zn_slots_encode": (_i32, [_vp, _vp, _u32, _vp, _vp]),
+    "zn_slots_decode": (_i32, [_vp, _vp, _u32, _vp, _vp]),
     "zinc_nbasis_create": (_i32, [_vp, _u32, _u64, _pp]),
     "zn_nbasis_destroy": (None, [_vp]),
     "ckks_encode_ntt": (_i32, [_vp, _vp, _u32, _u32, _vp, _vp]),
@@ -233,6 +237,10 @@ class ZincCache(_Handle):
 
 class NttBasis(_Handle):
     _destroy = "zn_nbasis_destroy"
+
+
+class SlotEncoder(_Handle):
+    _destroy = "zn_slot_encoder_destroy"
 
 
 # ------------------------------------------------------------ entry points
@@ -434,6 +442,38 @@ def _int_enc(fn, ctx, key, t, m, seed, ct_index, out, stream, name):
     args = [ctx.handle, key.handle] + ([t] if t is not None else []) + [m.data_ptr(), B, seed, ct_index.data_ptr(),
                                                                        out.data_ptr(), _stream(stream)]
     _check(fn(*args), name)
+    return out
+
+
+def zn_slot_encoder_create(ctx, t):
+    """Slot batching tables for the plaintext modulus t (prime, t = 1 mod 2N)."""
+    h = ctypes.c_void_p()
+    _check(lib().zn_slot_encoder_create(ctx.handle, t, ctypes.byref(h)), "zn_slot_encoder_create")
+    se = SlotEncoder(ctx, h)
+    se.t = t
+    return se
+
+
+def zn_slots_encode(se, slots, out=None, stream=None):
+    """CUDA int64 [B, N] slot values (taken mod t) -> plaintext coefficients int64 [B, N] in [0, t)."""
+    import torch
+    ctx = se.ctx
+    B = slots.shape[0]
+    out = _out(out, (B, ctx.n), torch.int64, slots.device)
+    _dev(slots, torch.int64, (B, ctx.n), "slots")
+    _dev(out, torch.int64, (B, ctx.n), "out")
+    _check(lib().zn_slots_encode(se.handle, slots.data_ptr(), B, out.data_ptr(), _stream(stream)), "zn_slots_encode")
+    return out
+
+
+def zn_slots_decode(se, m, out=None, stream=None):
+    import torch
+    ctx = se.ctx
+    B = m.shape[0]
+    out = _out(out, (B, ctx.n), torch.int64, m.device)
+    _dev(m, torch.int64, (B, ctx.n), "m")
+    _dev(out, torch.int64, (B, ctx.n), "out")
+    _check(lib().zn_slots_decode(se.handle, m.data_ptr(), B, out.data_ptr(), _stream(stream)), "zn_slots_decode")
     return out
 
 

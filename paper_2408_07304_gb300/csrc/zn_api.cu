@@ -40,6 +40,14 @@ struct zn_ctx {
 // Handle type tags: an opaque pointer of the wrong kind is rejected (ZN_EINVAL).
 enum : uint32_t { kTagPk = 0x6b70u, kTagSk = 0x6b73u, kTagZc = 0x637au, kTagNb = 0x626eu, kTagDead = 0u };
 
+// Slot batching tables for a plaintext modulus t (BFV / BGV).
+struct zn_slot_encoder {
+  uint32_t tag = 0x7365u;
+  zn_ctx* ctx;
+  zn::BatchEnc E;
+  void* d;                 // one allocation: twp [N], itw [N], itws [N], pos [N]
+};
+
 // Cached error basis of the NTT-domain Zinc randomiser, and the rotation tables.
 struct zn_nbasis {
   uint32_t tag = kTagNb;
@@ -1096,6 +1104,94 @@ int bgv_decrypt(zn_ctx* c, const zn_sk* sk, uint64_t t, const uint64_t* ct, uint
   if (!ct || !m) return ZN_EINVAL;
   DeviceGuard g(c->device);
   return int_decrypt(c, sk, t, true, ct, batch, m, S(stream));
+}
+
+// ------------------------------------------------- slot batching (BFV, BGV)
+
+void zn_slot_encoder_destroy(zn_slot_encoder* se) {
+  if (!se || se->tag != 0x7365u) return;
+  se->tag = kTagDead;
+  DeviceGuard g(se->ctx->device);
+  cudaFree(se->d);
+  delete se;
+}
+
+int zn_slot_encoder_create(zn_ctx* c, uint64_t t, zn_slot_encoder** out) {
+  if (!c || !out || !int_ring(c) || !t_ok(c, t)) return ZN_EINVAL;
+  *out = nullptr;
+  const uint32_t log_n = c->prm.log_n, n = c->n;
+  if (!zn::is_prime(t) || t % (2ull * n) != 1) return ZN_EINVAL;
+  zn_slot_encoder* se = new (std::nothrow) zn_slot_encoder();
+  if (!se) return ZN_ENOMEM;
+  se->ctx = c;
+  const u64 psi = zn::find_psi(t, log_n);
+  std::vector<u64> tw(n), tws(n), itw(n), itws(n);
+  zn::ntt_tables(t, psi, log_n, tw.data(), tws.data(), itw.data(), itws.data());
+  std::vector<ulonglong2> twp(n);
+  for (uint32_t k = 0; k < n; ++k) twp[k] = make_ulonglong2(tw[k], tws[k]);
+  // slot s <-> psi^(a_s), a_s = 5^s (s < N/2) or -5^(s - N/2) mod 2N; NTT index i
+  // evaluates at psi^(2 brv(i) + 1)
+  std::vector<int> pos(n);
+  {
+    u64 g = 1;
+    for (uint32_t s2 = 0; s2 < n / 2; ++s2) {
+      const u64 a[2] = {g, 2ull * n - g};
+      for (int h = 0; h < 2; ++h) {
+        const uint32_t e = (uint32_t)((a[h] - 1) / 2);
+        uint32_t r = 0;
+        for (uint32_t bit = 0; bit < log_n; ++bit) r |= ((e >> bit) & 1u) << (log_n - 1 - bit);
+        pos[h * (n / 2) + s2] = (int)r;
+      }
+      g = g * 5 % (2ull * n);
+    }
+  }
+  const size_t b_tw = sizeof(ulonglong2) * n, b_w = sizeof(u64) * n, b_pos = sizeof(int) * n;
+  DeviceGuard gd(c->device);
+  if (cudaMalloc(&se->d, b_tw + 2 * b_w + b_pos) != cudaSuccess) {
+    cudaGetLastError();
+    delete se;
+    return ZN_ENOMEM;
+  }
+  unsigned char* base = (unsigned char*)se->d;
+  if (cudaMemcpy(base, twp.data(), b_tw, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(base + b_tw, itw.data(), b_w, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(base + b_tw + b_w, itws.data(), b_w, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(base + b_tw + 2 * b_w, pos.data(), b_pos, cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    zn_slot_encoder_destroy(se);
+    return ZN_ECUDA;
+  }
+  zn::BatchEnc& E = se->E;
+  E.log_n = (int)log_n;
+  E.t = t;
+  E.ninv = zn::powmod(n % t, t - 2, t);
+  E.ninvs = zn::shoup(E.ninv, t);
+  E.twp = (const ulonglong2*)base;
+  E.itw = (const u64*)(base + b_tw);
+  E.itws = (const u64*)(base + b_tw + b_w);
+  E.pos = (const int*)(base + b_tw + 2 * b_w);
+  *out = se;
+  return ZN_OK;
+}
+
+int zn_slots_encode(zn_slot_encoder* se, const int64_t* slots, uint32_t batch, int64_t* m, void* stream) {
+  if (!se || se->tag != 0x7365u) return ZN_EINVAL;
+  if (batch == 0) return ZN_OK;
+  if (!slots || !m) return ZN_EINVAL;
+  DeviceGuard g(se->ctx->device);
+  ZN_CUDA(zn::launch_batch_encode(se->E, slots, batch, m, S(stream)));
+  return ZN_OK;
+}
+
+int zn_slots_decode(zn_slot_encoder* se, const int64_t* m, uint32_t batch, int64_t* slots, void* stream) {
+  if (!se || se->tag != 0x7365u) return ZN_EINVAL;
+  if (batch == 0) return ZN_OK;
+  if (!slots || !m) return ZN_EINVAL;
+  DeviceGuard g(se->ctx->device);
+  Scratch scratch(se->ctx, S(stream));
+  if (!scratch.alloc(sizeof(u64) * batch * (size_t)se->ctx->n)) return ZN_ENOMEM;
+  ZN_CUDA(zn::launch_batch_decode(se->E, m, batch, (u64*)scratch.p, slots, S(stream)));
+  return ZN_OK;
 }
 
 // ------------------------------------------- Zinc with NTT-domain errors

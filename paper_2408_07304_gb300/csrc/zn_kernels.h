@@ -186,6 +186,20 @@ cudaError_t launch_zinc_ntt(const DevParams& P, const NttZincArgs& A, uint32_t b
 // int64 coefficients [B][N] -> residues [B][L][N]
 cudaError_t launch_residues_batch(const DevParams& P, const i64* v, uint32_t batch, u64* out, cudaStream_t st);
 
+// Slot batching for BFV / BGV plaintexts (a prime t = 1 mod 2N).
+struct BatchEnc {
+  int log_n;
+  u64 t;
+  u64 ninv, ninvs;          // N^-1 mod t and its Shoup companion
+  const ulonglong2* twp;    // [N] (psi^brv(k), Shoup companion) mod t
+  const u64* itw;           // [N] psi^-brv(k) mod t
+  const u64* itws;          // [N] Shoup companions
+  const int* pos;           // [N] NTT output index of slot s
+};
+cudaError_t launch_batch_encode(const BatchEnc& E, const i64* slots, uint32_t batch, i64* m, cudaStream_t st);
+cudaError_t launch_batch_decode(const BatchEnc& E, const i64* m, uint32_t batch, u64* work, i64* slots,
+                                cudaStream_t st);
+
 // pk0 += (t - 1) e-hat (per prime, NTT form) and its Shoup companions: Gen's key becomes BGV's.
 cudaError_t launch_bgv_key(const DevParams& P, u64 t, const u64* ehat, u64* pk, u64* pks, cudaStream_t st);
 // residues [L][N] of a signed int64 polynomial [N]
