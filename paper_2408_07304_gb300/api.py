@@ -699,6 +699,39 @@ def zn_autotune(ctx, pk, zc, batch):
     return chosen.value, [float(x) for x in ms]
 
 
+def _device_name(device):
+    import torch
+    return torch.cuda.get_device_name(device)
+
+
+def autotune_cached(ctx, pk, zc, batch=512, path=None):
+    """The context's launch shape from a JSON cache keyed by device name, ring
+    degree and prime chain: set from the cache on a hit, else tuned by
+    zn_autotune on `batch` encryptions and stored.  Returns (variant, hit)."""
+    import json
+    path = path or os.path.join(os.path.expanduser("~"), ".cache", "zinc_gb300_autotune.json")
+    key = f"{_device_name(ctx.device)}|{ctx.log_n}|{','.join(str(q) for q in ctx.primes)}"
+    try:
+        with open(path) as f:
+            cache = json.load(f)
+    except (OSError, ValueError):
+        cache = {}
+    v = cache.get(key)
+    if isinstance(v, int) and 0 <= v < VARIANTS:
+        zn_set_variant(ctx, v)
+        return v, True
+    v, ms = zn_autotune(ctx, pk, zc, batch)
+    cache[key] = v
+    d = os.path.dirname(path)
+    if d:
+        os.makedirs(d, exist_ok=True)
+    tmp = f"{path}.tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+    return v, False
+
+
 def zn_probe_butterfly_relaxed(device=0):
     """Register-only butterflies/s of the relaxed butterfly (primes below 2^59)."""
     r = ctypes.c_double()
