@@ -75,7 +75,7 @@ def build(verbose: bool = False) -> str:
                     print(out, file=sys.stderr)
     if jobs or not os.path.exists(LIB):
         tmp = LIB + f".tmp{os.getpid()}"
-        _compile([nvcc, *ARCH, "-shared", "-o", tmp] + objs + ["-lcudart"])
+        _compile([nvcc, *ARCH, "-shared", "-o", tmp] + objs + ["-lcudart", "-ldl"])
         os.replace(tmp, LIB)
     return LIB
 

@@ -9,6 +9,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/zinc.h"
 #include "zn_host.h"
 #include "zn_kernels.h"
@@ -93,6 +95,13 @@ static inline bool bgv_zc_of(const zn_zcache* z, const zn_ctx* c) {
 namespace {
 
 inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// NVTX range around an entry point: names the call in Nsight timelines (a
+// no-op unless a profiling tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 inline size_t limb(const zn_ctx* c) { return (size_t)c->n; }
 inline size_t ring_words(const zn_ctx* c) { return (size_t)c->L * c->n; }
@@ -679,6 +688,7 @@ int zn_timing_read(zn_ctx* c, int kind, double* ms, uint64_t* launches) {
 // ------------------------------------------------------------------ keys
 
 int ckks_keygen(zn_ctx* c, uint64_t seed, zn_sk** sk, zn_pk** pk) {
+  NvtxRange nvtx("ckks_keygen");
   if (!c || !sk || !pk) return ZN_EINVAL;
   *sk = nullptr;
   *pk = nullptr;
@@ -830,6 +840,7 @@ int zn_sk_import(zn_ctx* c, const int8_t* host_in, zn_sk** out) {
 // --------------------------------------------------------------- encode
 
 int ckks_encode(zn_ctx* c, const double* slots, uint32_t n_slots, uint32_t batch, int64_t* out, void* stream) {
+  NvtxRange nvtx("ckks_encode");
   if (!c || n_slots > c->n / 2) return ZN_EINVAL;
   if (batch == 0) return ZN_OK;
   if (!out || (n_slots && !slots)) return ZN_EINVAL;
@@ -842,12 +853,14 @@ int ckks_encode(zn_ctx* c, const double* slots, uint32_t n_slots, uint32_t batch
 
 int ckks_encrypt(zn_ctx* c, const zn_pk* pk, const double* slots, uint32_t n_slots, uint32_t batch, uint64_t seed,
                  const uint64_t* ct_index, uint64_t* ct, void* stream) {
+  NvtxRange nvtx("ckks_encrypt");
   if (!c || !pk_of(pk, c)) return ZN_EINVAL;
   return encrypt_common(c, false, pk->d, pk->d + 2 * ring_words(c), slots, n_slots, batch, seed, ct_index, ct,
                         stream);
 }
 
 int zinc_precompute(zn_ctx* c, const zn_pk* pk, uint64_t seed, zn_zcache** out) {
+  NvtxRange nvtx("zinc_precompute");
   if (!c || !pk_of(pk, c) || !out) return ZN_EINVAL;
   *out = nullptr;
   DeviceGuard g(c->device);
@@ -941,6 +954,7 @@ int zn_zcache_import(zn_ctx* c, const uint64_t* host_in, zn_zcache** out) {
 
 int zinc_encrypt(zn_ctx* c, const zn_zcache* z, const double* slots, uint32_t n_slots, uint32_t batch, uint64_t seed,
                  const uint64_t* ct_index, uint64_t* ct, void* stream) {
+  NvtxRange nvtx("zinc_encrypt");
   if (!c || !zc_of(z, c)) return ZN_EINVAL;
   return encrypt_common(c, true, z->d, nullptr, slots, n_slots, batch, seed, ct_index, ct, stream);
 }
@@ -949,6 +963,7 @@ int zinc_encrypt(zn_ctx* c, const zn_zcache* z, const double* slots, uint32_t n_
 
 int ckks_encrypt_ms(zn_ctx* c, const zn_pk* pk, const double* slots, uint32_t n_slots, uint32_t batch,
                     uint64_t seed, const uint64_t* ct_index, uint64_t* ct, void* stream) {
+  NvtxRange nvtx("ckks_encrypt_ms");
   if (!c || !pk_of(pk, c) || c->L < 2 || !pk->ms || n_slots > c->n / 2) return ZN_EINVAL;
   if (batch == 0) return ZN_OK;
   if (!ct || !ct_index || (n_slots && !slots)) return ZN_EINVAL;
@@ -957,6 +972,7 @@ int ckks_encrypt_ms(zn_ctx* c, const zn_pk* pk, const double* slots, uint32_t n_
 }
 
 int zinc_precompute_ms(zn_ctx* c, const zn_pk* pk, uint64_t seed, zn_ctx* dc, zn_zcache** out) {
+  NvtxRange nvtx("zinc_precompute_ms");
   if (!c || !pk_of(pk, c) || c->L < 2 || !pk->ms || !dc || !out) return ZN_EINVAL;
   *out = nullptr;
   if (dc->device != c->device || dc->L != c->L - 1 || dc->prm.log_n != c->prm.log_n ||
@@ -989,6 +1005,7 @@ int zinc_precompute_ms(zn_ctx* c, const zn_pk* pk, uint64_t seed, zn_ctx* dc, zn
 
 int bfv_encrypt(zn_ctx* c, const zn_pk* pk, uint64_t t, const int64_t* m, uint32_t batch, uint64_t seed,
                 const uint64_t* ct_index, uint64_t* ct, void* stream) {
+  NvtxRange nvtx("bfv_encrypt");
   if (!c || !pk_of(pk, c) || !int_ring(c) || !t_ok(c, t)) return ZN_EINVAL;
   if (batch == 0) return ZN_OK;
   if (!m || !ct_index || !ct) return ZN_EINVAL;
@@ -999,6 +1016,7 @@ int bfv_encrypt(zn_ctx* c, const zn_pk* pk, uint64_t t, const int64_t* m, uint32
 
 int bfv_zinc_encrypt(zn_ctx* c, const zn_zcache* z, uint64_t t, const int64_t* m, uint32_t batch, uint64_t seed,
                      const uint64_t* ct_index, uint64_t* ct, void* stream) {
+  NvtxRange nvtx("bfv_zinc_encrypt");
   if (!c || !zc_of(z, c) || !int_ring(c) || !t_ok(c, t)) return ZN_EINVAL;
   if (batch == 0) return ZN_OK;
   if (!m || !ct_index || !ct) return ZN_EINVAL;
@@ -1007,6 +1025,7 @@ int bfv_zinc_encrypt(zn_ctx* c, const zn_zcache* z, uint64_t t, const int64_t* m
 }
 
 int bgv_keygen(zn_ctx* c, uint64_t t, uint64_t seed, zn_sk** sk, zn_pk** pk) {
+  NvtxRange nvtx("bgv_keygen");
   if (!c || !sk || !pk || !int_ring(c) || !t_ok(c, t)) return ZN_EINVAL;
   int rc = ckks_keygen(c, seed, sk, pk);
   if (rc) return rc;
@@ -1071,6 +1090,7 @@ int bgv_zinc_precompute(zn_ctx* c, const zn_pk* pk, uint64_t seed, zn_zcache** o
 
 int bgv_encrypt(zn_ctx* c, const zn_pk* pk, const int64_t* m, uint32_t batch, uint64_t seed,
                 const uint64_t* ct_index, uint64_t* ct, void* stream) {
+  NvtxRange nvtx("bgv_encrypt");
   if (!c || !bgv_pk_of(pk, c)) return ZN_EINVAL;
   if (batch == 0) return ZN_OK;
   if (!m || !ct_index || !ct) return ZN_EINVAL;
@@ -1081,6 +1101,7 @@ int bgv_encrypt(zn_ctx* c, const zn_pk* pk, const int64_t* m, uint32_t batch, ui
 
 int bgv_zinc_encrypt(zn_ctx* c, const zn_zcache* z, const int64_t* m, uint32_t batch, uint64_t seed,
                      const uint64_t* ct_index, uint64_t* ct, void* stream) {
+  NvtxRange nvtx("bgv_zinc_encrypt");
   if (!c || !bgv_zc_of(z, c)) return ZN_EINVAL;
   if (batch == 0) return ZN_OK;
   if (!m || !ct_index || !ct) return ZN_EINVAL;
@@ -1090,6 +1111,7 @@ int bgv_zinc_encrypt(zn_ctx* c, const zn_zcache* z, const int64_t* m, uint32_t b
 
 int bfv_decrypt(zn_ctx* c, const zn_sk* sk, uint64_t t, const uint64_t* ct, uint32_t batch, int64_t* m,
                 void* stream) {
+  NvtxRange nvtx("bfv_decrypt");
   if (!c || !sk_of(sk, c) || !int_ring(c) || !t_ok(c, t)) return ZN_EINVAL;
   if (batch == 0) return ZN_OK;
   if (!ct || !m) return ZN_EINVAL;
@@ -1099,6 +1121,7 @@ int bfv_decrypt(zn_ctx* c, const zn_sk* sk, uint64_t t, const uint64_t* ct, uint
 
 int bgv_decrypt(zn_ctx* c, const zn_sk* sk, uint64_t t, const uint64_t* ct, uint32_t batch, int64_t* m,
                 void* stream) {
+  NvtxRange nvtx("bgv_decrypt");
   if (!c || !sk_of(sk, c) || !int_ring(c) || !t_ok(c, t)) return ZN_EINVAL;
   if (batch == 0) return ZN_OK;
   if (!ct || !m) return ZN_EINVAL;
@@ -1175,6 +1198,7 @@ int zn_slot_encoder_create(zn_ctx* c, uint64_t t, zn_slot_encoder** out) {
 }
 
 int zn_slots_encode(zn_slot_encoder* se, const int64_t* slots, uint32_t batch, int64_t* m, void* stream) {
+  NvtxRange nvtx("zn_slots_encode");
   if (!se || se->tag != 0x7365u) return ZN_EINVAL;
   if (batch == 0) return ZN_OK;
   if (!slots || !m) return ZN_EINVAL;
@@ -1184,6 +1208,7 @@ int zn_slots_encode(zn_slot_encoder* se, const int64_t* slots, uint32_t batch, i
 }
 
 int zn_slots_decode(zn_slot_encoder* se, const int64_t* m, uint32_t batch, int64_t* slots, void* stream) {
+  NvtxRange nvtx("zn_slots_decode");
   if (!se || se->tag != 0x7365u) return ZN_EINVAL;
   if (batch == 0) return ZN_OK;
   if (!slots || !m) return ZN_EINVAL;
@@ -1261,6 +1286,7 @@ int zinc_nbasis_create(zn_ctx* c, uint32_t K, uint64_t seed, zn_nbasis** out) {
 }
 
 int ckks_encode_ntt(zn_ctx* c, const double* slots, uint32_t n_slots, uint32_t batch, uint64_t* out, void* stream) {
+  NvtxRange nvtx("ckks_encode_ntt");
   if (!c || n_slots > c->n / 2) return ZN_EINVAL;
   if (batch == 0) return ZN_OK;
   if (!out || (n_slots && !slots)) return ZN_EINVAL;
@@ -1286,6 +1312,7 @@ int ckks_encode_ntt(zn_ctx* c, const double* slots, uint32_t n_slots, uint32_t b
 
 int zinc_encrypt_ntt(zn_ctx* c, const zn_zcache* z, const zn_nbasis* nb, const uint64_t* m_hat, uint32_t batch,
                      uint64_t seed, const uint64_t* ct_index, uint64_t* ct, void* stream) {
+  NvtxRange nvtx("zinc_encrypt_ntt");
   if (!c || !zc_of(z, c) || !nb || nb->tag != kTagNb || nb->ctx != c) return ZN_EINVAL;
   if (batch == 0) return ZN_OK;
   if (!m_hat || !ct_index || !ct) return ZN_EINVAL;
@@ -1318,6 +1345,7 @@ int zinc_encrypt_ntt(zn_ctx* c, const zn_zcache* z, const zn_nbasis* nb, const u
 // -------------------------------------------------------------- decrypt
 
 int ckks_decrypt(zn_ctx* c, const zn_sk* sk, const uint64_t* ct, uint32_t batch, uint64_t* out, void* stream) {
+  NvtxRange nvtx("ckks_decrypt");
   if (!c || !sk_of(sk, c)) return ZN_EINVAL;
   if (batch == 0) return ZN_OK;
   if (!ct || !out) return ZN_EINVAL;
@@ -1329,6 +1357,7 @@ int ckks_decrypt(zn_ctx* c, const zn_sk* sk, const uint64_t* ct, uint32_t batch,
 
 int ckks_decrypt_decode(zn_ctx* c, const zn_sk* sk, const uint64_t* ct, uint32_t batch, uint32_t n_slots, double* out,
                         void* stream) {
+  NvtxRange nvtx("ckks_decrypt_decode");
   if (!c || !sk_of(sk, c) || n_slots > c->n / 2) return ZN_EINVAL;
   if (batch == 0 || n_slots == 0) return ZN_OK;
   if (!ct || !out) return ZN_EINVAL;
@@ -1503,6 +1532,7 @@ static int batch_enqueue(zn_batch* b, cudaStream_t st) {
 }
 
 int zn_batch_run(zn_batch* b, void* stream, int graph) {
+  NvtxRange nvtx("zn_batch_run");
   if (!b) return ZN_EINVAL;
   DeviceGuard g(b->device);
   cudaStream_t st = S(stream);
@@ -1540,6 +1570,7 @@ int zn_batch_info(const zn_batch* b, uint32_t* prep_units, uint32_t* packets) {
 int zn_encrypt_host(zn_ctx* c, const zn_pk* pk, const zn_zcache* zc, const double* host_slots, uint32_t n_slots,
                     uint32_t batch, uint64_t seed, const uint64_t* host_ct_index, uint64_t* host_ct,
                     uint32_t chunk) {
+  NvtxRange nvtx("zn_encrypt_host");
   if (!c || (pk && zc) || (!pk && !zc) || (pk && !pk_of(pk, c)) || (zc && !zc_of(zc, c)) || n_slots > c->n / 2)
     return ZN_EINVAL;
   if (batch == 0) return ZN_OK;
@@ -1602,6 +1633,7 @@ int zn_set_variant(zn_ctx* c, int variant) {
 int zn_get_variant(const zn_ctx* c) { return c ? c->variant : ZN_EINVAL; }
 
 int zn_autotune(zn_ctx* c, const zn_pk* pk, const zn_zcache* zc, uint32_t batch, float* ms, int* chosen) {
+  NvtxRange nvtx("zn_autotune");
   if (!c || !pk_of(pk, c) || !zc_of(zc, c) || batch == 0) return ZN_EINVAL;
   DeviceGuard g(c->device);
   u64* ct = nullptr;
