@@ -324,34 +324,48 @@ def run_ours(args, w):
     # out, pipelined in chunks over three streams
     e2e = None
     if not args.no_e2e:
-        e2e_steps = max(1, min(args.steps, 3))
+        e2e_steps = max(1, min(args.steps, 5))
         host_slots = torch.tensor(z, dtype=torch.float64).pin_memory()
         host_idx = idx.cpu().pin_memory()
         host_v = torch.empty(out_v.shape, dtype=torch.int64, pin_memory=True)
         host_z = torch.empty(out_z.shape, dtype=torch.int64, pin_memory=True)
-        api.zn_encrypt_host(ctx, pk, host_slots, w.seed, host_idx, host_v)      # warm-up
+        api.zn_encrypt_host(ctx, pk, host_slots, w.seed, host_idx, host_v)      # warm-up, both modes
+        api.zn_encrypt_host(ctx, zc, host_slots, w.seed, host_idx, host_z)      # (first touch of each buffer)
         torch.cuda.synchronize(dev)
         # the device-to-host link of this machine, copied the way the entry point
         # copies (chunks of 256 ciphertexts over three streams, into the same
         # pinned buffer): the end-to-end rate cannot exceed it
         cstreams = [torch.cuda.Stream(dev) for _ in range(3)]
-        torch.cuda.synchronize(dev)
-        l0 = time.perf_counter()
-        for k, c0 in enumerate(range(0, B, 256)):
-            with torch.cuda.stream(cstreams[k % 3]):
-                host_v[c0:c0 + 256].copy_(out_v[c0:c0 + 256], non_blocking=True)
-        torch.cuda.synchronize(dev)
-        link_gbs = host_v.numel() * 8 / (time.perf_counter() - l0) / 1e9
+
+        def link_probe():
+            torch.cuda.synchronize(dev)
+            l0 = time.perf_counter()
+            for k, c0 in enumerate(range(0, B, 256)):
+                with torch.cuda.stream(cstreams[k % 3]):
+                    host_v[c0:c0 + 256].copy_(out_v[c0:c0 + 256], non_blocking=True)
+            torch.cuda.synchronize(dev)
+            return host_v.numel() * 8 / (time.perf_counter() - l0) / 1e9
+
+        link_before = link_probe()
         barrier()
-        t_start = time.perf_counter()
+        # each step timed on its own: the host link of these boxes is shared
+        # with other tenants and fluctuates, so the value is the median step
+        step_s = []
         for _ in range(e2e_steps):
+            t_start = time.perf_counter()
             api.zn_encrypt_host(ctx, pk, host_slots, w.seed, host_idx, host_v)
             api.zn_encrypt_host(ctx, zc, host_slots, w.seed, host_idx, host_z)
-        e2e_s = max_over_ranks([time.perf_counter() - t_start], world, dev, dist)[0]
+            step_s.append(time.perf_counter() - t_start)
+        step_s = max_over_ranks(step_s, world, dev, dist)
+        link_after = link_probe()
+        link_gbs = max(link_before, link_after)
+        e2e_s = statistics.median(step_s)
         link_bound = link_gbs * 1e9 / (2 * w.L * w.n * 8)
-        e2e = {"value": 2 * B * world * e2e_steps / e2e_s, "unit": UNIT,
-               "d2h_link_gbs": link_gbs, "link_bound_enc_s": link_bound * world,
-               "of_link_bound": 2 * B * e2e_steps / e2e_s / link_bound,
+        e2e = {"value": 2 * B * world / e2e_s, "unit": UNIT, "statistic": f"median of {e2e_steps} timed steps",
+               "step_s": step_s, "mean_enc_s": 2 * B * world * e2e_steps / sum(step_s),
+               "d2h_link_gbs": link_gbs, "d2h_link_gbs_before_after": [link_before, link_after],
+               "link_bound_enc_s": link_bound * world,
+               "of_link_bound": 2 * B / e2e_s / link_bound,
                "h2d_bytes_per_step": int(2 * (host_slots.numel() * 8 + host_idx.numel() * 8)),
                "d2h_bytes_per_step": int(2 * host_v.numel() * 8),
                "steps": e2e_steps, "api": "zn_encrypt_host (pinned host buffers, chunks of 256 over 3 streams)"}

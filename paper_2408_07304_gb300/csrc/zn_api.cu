@@ -175,20 +175,12 @@ uint32_t encode_chunk(const zn_ctx* c) {
   return (uint32_t)k;
 }
 
-int encrypt_common(zn_ctx* c, bool zinc, const u64* key, const u64* keys, const double* slots, uint32_t n_slots,
-                   uint32_t batch, uint64_t seed, const uint64_t* ct_index, uint64_t* ct, void* stream) {
-  if (!c || !key || n_slots > c->n / 2) return ZN_EINVAL;
-  if (batch == 0) return ZN_OK;
-  if (!ct || !ct_index || (n_slots && !slots)) return ZN_EINVAL;
-  DeviceGuard g(c->device);
-  const uint32_t chunk = encode_chunk(c);
-  const uint32_t first = batch < chunk ? batch : chunk;
-  // per chunk: message + noise (int64 [N]) and small polynomials (int8 [2][N])
-  const size_t me_b = sizeof(i64) * first * c->n, sm_b = 2 * (size_t)first * c->n;
-  Scratch scratch(c, S(stream));
-  if (!scratch.alloc(me_b + sm_b)) return ZN_ENOMEM;
-  i64* me = (i64*)scratch.p;
-  int8_t* small = (int8_t*)scratch.p + me_b;
+// Prep + encrypt launch pairs over `batch` ciphertexts in chunks of `chunk`,
+// with caller-provided scratch for one chunk: me int64 [chunk][N], small
+// int8 [chunk][2][N].
+int encrypt_with(zn_ctx* c, bool zinc, const u64* key, const u64* keys, const double* slots, uint32_t n_slots,
+                 uint32_t batch, uint64_t seed, const uint64_t* ct_index, uint64_t* ct, i64* me, int8_t* small,
+                 uint32_t chunk, cudaStream_t st) {
   for (uint32_t b0 = 0; b0 < batch; b0 += chunk) {
     const uint32_t nb = (batch - b0) < chunk ? (batch - b0) : chunk;
     zn::PrepArgs pa;
@@ -201,8 +193,8 @@ int encrypt_common(zn_ctx* c, bool zinc, const u64* key, const u64* keys, const 
     pa.me = me;
     pa.small = small;
     {
-      TimedLaunch t(c, ZN_TIME_ENCODE, S(stream));
-      ZN_CUDA(zn::launch_prep(c->dp, pa, zinc, nb, S(stream)));
+      TimedLaunch t(c, ZN_TIME_ENCODE, st);
+      ZN_CUDA(zn::launch_prep(c->dp, pa, zinc, nb, st));
     }
     zn::EncArgs A;
     A.swap = 0;
@@ -211,10 +203,31 @@ int encrypt_common(zn_ctx* c, bool zinc, const u64* key, const u64* keys, const 
     A.me = me;
     A.small = small;
     A.out = ct + (size_t)b0 * 2 * ring_words(c);
-    TimedLaunch t(c, zinc ? ZN_TIME_ZINC : ZN_TIME_ENCRYPT, S(stream));
-    ZN_CUDA(zn::launch_encrypt(c->dp, A, zinc, nb, c->variant, S(stream)));
+    TimedLaunch t(c, zinc ? ZN_TIME_ZINC : ZN_TIME_ENCRYPT, st);
+    ZN_CUDA(zn::launch_encrypt(c->dp, A, zinc, nb, c->variant, st));
   }
   return ZN_OK;
+}
+
+// Bytes of encrypt_with's scratch for chunks of `chunk` ciphertexts: the
+// message-plus-noise words, then the small polynomials.
+size_t encrypt_scratch_bytes(const zn_ctx* c, uint32_t chunk) {
+  return sizeof(i64) * chunk * (size_t)c->n + 2 * (size_t)chunk * c->n;
+}
+
+int encrypt_common(zn_ctx* c, bool zinc, const u64* key, const u64* keys, const double* slots, uint32_t n_slots,
+                   uint32_t batch, uint64_t seed, const uint64_t* ct_index, uint64_t* ct, void* stream) {
+  if (!c || !key || n_slots > c->n / 2) return ZN_EINVAL;
+  if (batch == 0) return ZN_OK;
+  if (!ct || !ct_index || (n_slots && !slots)) return ZN_EINVAL;
+  DeviceGuard g(c->device);
+  const uint32_t chunk = encode_chunk(c);
+  const uint32_t first = batch < chunk ? batch : chunk;
+  Scratch scratch(c, S(stream));
+  if (!scratch.alloc(encrypt_scratch_bytes(c, first))) return ZN_ENOMEM;
+  i64* me = (i64*)scratch.p;
+  int8_t* small = (int8_t*)scratch.p + sizeof(i64) * first * (size_t)c->n;
+  return encrypt_with(c, zinc, key, keys, slots, n_slots, batch, seed, ct_index, ct, me, small, first, S(stream));
 }
 
 // The modulus-switched encryption's arguments that depend only on the context.
@@ -1587,13 +1600,17 @@ int zn_encrypt_host(zn_ctx* c, const zn_pk* pk, const zn_zcache* zc, const doubl
   const size_t ct_b = sizeof(u64) * 2 * ring_words(c) * chunk;
   const size_t sl_b = (sizeof(double) * n_slots * chunk + 255) / 256 * 256;
   const size_t ix_b = (sizeof(u64) * chunk + 255) / 256 * 256;
+  // each stream also owns its encryption scratch for the whole call, so that
+  // no per-chunk pool allocation can make one stream wait for another's frees
+  const uint32_t ech = chunk < encode_chunk(c) ? chunk : encode_chunk(c);
+  const size_t en_b = (encrypt_scratch_bytes(c, ech) + 255) / 256 * 256;
   const bool zinc = zc != nullptr;
   int rc = ZN_OK;
   {
     Scratch st0(c, c->hs[0]), st1(c, c->hs[1]), st2(c, c->hs[2]);
     Scratch* stage[3] = {&st0, &st1, &st2};
     for (int k = 0; k < 3 && !rc; ++k)
-      if (!stage[k]->alloc(ct_b + sl_b + ix_b)) rc = ZN_ENOMEM;
+      if (!stage[k]->alloc(ct_b + sl_b + ix_b + en_b)) rc = ZN_ENOMEM;
     for (uint32_t b0 = 0, k = 0; b0 < batch && !rc; b0 += chunk, k = (k + 1) % 3) {
       const uint32_t nb = (batch - b0) < chunk ? (batch - b0) : chunk;
       cudaStream_t st = c->hs[k];
@@ -1601,15 +1618,17 @@ int zn_encrypt_host(zn_ctx* c, const zn_pk* pk, const zn_zcache* zc, const doubl
       u64* d_ct = (u64*)base;
       double* d_sl = (double*)(base + ct_b);
       u64* d_ix = (u64*)(base + ct_b + sl_b);
+      i64* d_me = (i64*)(base + ct_b + sl_b + ix_b);
+      int8_t* d_small = (int8_t*)d_me + sizeof(i64) * ech * (size_t)c->n;
       if ((n_slots && cudaMemcpyAsync(d_sl, host_slots + (size_t)b0 * n_slots, sizeof(double) * n_slots * nb,
                                       cudaMemcpyHostToDevice, st) != cudaSuccess) ||
           cudaMemcpyAsync(d_ix, host_ct_index + b0, sizeof(u64) * nb, cudaMemcpyHostToDevice, st) != cudaSuccess) {
         rc = ZN_ECUDA;
         break;
       }
-      rc = zinc ? encrypt_common(c, true, zc->d, nullptr, d_sl, n_slots, nb, seed, d_ix, d_ct, st)
-                : encrypt_common(c, false, pk->d, pk->d + 2 * ring_words(c), d_sl, n_slots, nb, seed, d_ix, d_ct,
-                                 st);
+      rc = zinc ? encrypt_with(c, true, zc->d, nullptr, d_sl, n_slots, nb, seed, d_ix, d_ct, d_me, d_small, ech, st)
+                : encrypt_with(c, false, pk->d, pk->d + 2 * ring_words(c), d_sl, n_slots, nb, seed, d_ix, d_ct, d_me,
+                               d_small, ech, st);
       if (!rc && cudaMemcpyAsync(host_ct + (size_t)b0 * 2 * ring_words(c), d_ct,
                                  sizeof(u64) * 2 * ring_words(c) * nb, cudaMemcpyDeviceToHost, st) != cudaSuccess)
         rc = ZN_ECUDA;
