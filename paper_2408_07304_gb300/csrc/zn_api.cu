@@ -40,11 +40,13 @@ struct zn_ctx {
 };
 
 // Handle type tags: an opaque pointer of the wrong kind is rejected (ZN_EINVAL).
-enum : uint32_t { kTagPk = 0x6b70u, kTagSk = 0x6b73u, kTagZc = 0x637au, kTagNb = 0x626eu, kTagDead = 0u };
+enum : uint32_t {
+  kTagPk = 0x6b70u, kTagSk = 0x6b73u, kTagZc = 0x637au, kTagNb = 0x626eu, kTagSe = 0x7365u, kTagDead = 0u
+};
 
 // Slot batching tables for a plaintext modulus t (BFV / BGV).
 struct zn_slot_encoder {
-  uint32_t tag = 0x7365u;
+  uint32_t tag = kTagSe;
   zn_ctx* ctx;
   zn::BatchEnc E;
   void* d;                 // one allocation: twp [N], itw [N], itws [N], pos [N]
@@ -1145,7 +1147,7 @@ int bgv_decrypt(zn_ctx* c, const zn_sk* sk, uint64_t t, const uint64_t* ct, uint
 // ------------------------------------------------- slot batching (BFV, BGV)
 
 void zn_slot_encoder_destroy(zn_slot_encoder* se) {
-  if (!se || se->tag != 0x7365u) return;
+  if (!se || se->tag != kTagSe) return;
   se->tag = kTagDead;
   DeviceGuard g(se->ctx->device);
   cudaFree(se->d);
@@ -1212,7 +1214,7 @@ int zn_slot_encoder_create(zn_ctx* c, uint64_t t, zn_slot_encoder** out) {
 
 int zn_slots_encode(zn_slot_encoder* se, const int64_t* slots, uint32_t batch, int64_t* m, void* stream) {
   NvtxRange nvtx("zn_slots_encode");
-  if (!se || se->tag != 0x7365u) return ZN_EINVAL;
+  if (!se || se->tag != kTagSe) return ZN_EINVAL;
   if (batch == 0) return ZN_OK;
   if (!slots || !m) return ZN_EINVAL;
   DeviceGuard g(se->ctx->device);
@@ -1222,7 +1224,7 @@ int zn_slots_encode(zn_slot_encoder* se, const int64_t* slots, uint32_t batch, i
 
 int zn_slots_decode(zn_slot_encoder* se, const int64_t* m, uint32_t batch, int64_t* slots, void* stream) {
   NvtxRange nvtx("zn_slots_decode");
-  if (!se || se->tag != 0x7365u) return ZN_EINVAL;
+  if (!se || se->tag != kTagSe) return ZN_EINVAL;
   if (batch == 0) return ZN_OK;
   if (!slots || !m) return ZN_EINVAL;
   DeviceGuard g(se->ctx->device);
