@@ -458,7 +458,7 @@ def run_ours(args, w):
         m_hat = api.ckks_encode_ntt(ctx, slots)
         out_n = torch.empty((B, 2, w.L, w.n), dtype=torch.int64, device=dev)
         nttz = {"plaintext": "pre-encoded in NTT form (ckks_encode_ntt, untimed)"}
-        for K in (2, 4):
+        for K in (1, 2, 4):
             nb = api.zinc_nbasis_create(ctx, K, workloads.NBASIS_SEED)
             for _ in range(args.warmup):
                 api.zinc_encrypt_ntt(ctx, zc, nb, m_hat, w.seed, idx, out=out_n, stream=stream)
