@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(256, 4) k_zinc_ntt(DevParams P, NttZincArgs A)
   const u64* E1 = E0 + (size_t)K * estride;      // E_{1,0}
   constexpr bool REG = K <= 4;                   // flo in registers (no spills up to K = 4)
   constexpr int UNJ = REG ? K : 1;               // term loop unrolled only then
-  constexpr int UNK = K <= 2 ? 2 : 1;
+  constexpr int UNK = K == 1 ? 4 : K == 2 ? 2 : 1;
   ulonglong2 lo[REG ? 2 * K : 1];
   if constexpr (REG) {
 #pragma unroll
