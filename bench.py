@@ -42,6 +42,13 @@ NCU_TRAFFIC = {
     ("throughput", "k_encrypt_half<13,vanilla,radix-8,3 blocks/SM>", 256): 55.511296e6 + 528.509952e6,
     ("throughput", "k_encrypt_half<13,Zinc,radix-8,3 blocks/SM>", 256): 42.093056e6 + 495.656960e6,
 }
+# Busy fraction of the SM's integer multiply-add pipe (ncu
+# sm__pipe_fmaheavy_cycles_active, which is also the kernel's
+# sm__throughput: the busiest unit of the SM) in the same capture.
+NCU_INT_PIPE = {
+    ("throughput", "k_encrypt_half<13,vanilla,radix-8,3 blocks/SM>", 256): 0.7514,
+    ("throughput", "k_encrypt_half<13,Zinc,radix-8,3 blocks/SM>", 256): 0.7167,
+}
 VARIANT_KERNEL = {6: "k_encrypt_half<13,{mode},radix-8,3 blocks/SM>",
                   7: "k_encrypt_half<13,{mode},radix-8,3 blocks/SM,ciphertext-major>"}
 
@@ -284,6 +291,7 @@ def run_ours(args, w):
     kname = VARIANT_KERNEL.get(tune[0], "k_encrypt<{mode}> variant %d" % tune[0]) if w.log_n == 14 else \
         f"k_encrypt<{w.log_n},{{mode}}> variant {tune[0]}"
     traffic = NCU_TRAFFIC.get((w.name, kname.format(mode="vanilla"), int(round(chunk_cts))))
+    int_pipe = NCU_INT_PIPE.get((w.name, kname.format(mode="vanilla"), int(round(chunk_cts))))
     roofline = {"bound": "alu", "achieved": achieved, "peak": derived_peak, "unit": "Gbutterfly/s",
                 "frac": achieved / derived_peak, "traffic": traffic,
                 "traffic_unit": "DRAM bytes per launch (ncu)", "algorithmic_bytes": chunk_cts * ct_bytes,
@@ -292,6 +300,8 @@ def run_ours(args, w):
                 "probe_peak": probe, "probe_frac": achieved / probe,
                 "probe_harvey": probe_h, "probe_relaxed": probe_r, "relaxed_prime_share": f_rel,
                 "zinc_kernel_achieved": bfly_z / (kz_avg / 1e3) / 1e9,
+                "int_pipe": {"pipe": "fmaheavy (32-bit integer multiply-add)", "busy_frac": int_pipe,
+                             "source": "ncu sm__pipe_fmaheavy_cycles_active, 256-ciphertext launch"},
                 "hbm": {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
                         "frac": hbm_achieved / hbm_peak, "peak_source": peak_src}}
 
@@ -337,14 +347,17 @@ def run_ours(args, w):
         # pinned buffer): the end-to-end rate cannot exceed it
         cstreams = [torch.cuda.Stream(dev) for _ in range(3)]
 
-        def link_probe():
-            torch.cuda.synchronize(dev)
-            l0 = time.perf_counter()
-            for k, c0 in enumerate(range(0, B, 256)):
-                with torch.cuda.stream(cstreams[k % 3]):
-                    host_v[c0:c0 + 256].copy_(out_v[c0:c0 + 256], non_blocking=True)
-            torch.cuda.synchronize(dev)
-            return host_v.numel() * 8 / (time.perf_counter() - l0) / 1e9
+        def link_probe(reps=3):
+            best = 0.0
+            for _ in range(reps):   # the best of a few: other tenants' traffic only slows a copy down
+                torch.cuda.synchronize(dev)
+                l0 = time.perf_counter()
+                for k, c0 in enumerate(range(0, B, 256)):
+                    with torch.cuda.stream(cstreams[k % 3]):
+                        host_v[c0:c0 + 256].copy_(out_v[c0:c0 + 256], non_blocking=True)
+                torch.cuda.synchronize(dev)
+                best = max(best, host_v.numel() * 8 / (time.perf_counter() - l0) / 1e9)
+            return best
 
         link_before = link_probe()
         barrier()
@@ -366,6 +379,7 @@ def run_ours(args, w):
                "d2h_link_gbs": link_gbs, "d2h_link_gbs_before_after": [link_before, link_after],
                "link_bound_enc_s": link_bound * world,
                "of_link_bound": 2 * B / e2e_s / link_bound,
+               "d2h_gbs_fastest_step": 2 * host_v.numel() * 8 / min(step_s) / 1e9,
                "h2d_bytes_per_step": int(2 * (host_slots.numel() * 8 + host_idx.numel() * 8)),
                "d2h_bytes_per_step": int(2 * host_v.numel() * 8),
                "steps": e2e_steps, "api": "zn_encrypt_host (pinned host buffers, chunks of 256 over 3 streams)"}
