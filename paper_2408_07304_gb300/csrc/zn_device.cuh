@@ -82,6 +82,12 @@ __device__ __forceinline__ u64 small_res(int v, u64 q) {
   return v < 0 ? q - (u64)(-(i64)v) : (u64)v;
 }
 
+// v w mod q for a ternary v (v in {-1, 0, 1}) and w in [0, q): a selection,
+// in [0, q].
+__device__ __forceinline__ u64 mul_tern(int v, u64 w, u64 q) {
+  return v == 0 ? 0ull : v > 0 ? w : q - w;
+}
+
 // general a*b mod q (slow path: keygen and imports only)
 __device__ __forceinline__ u64 mulmod_slow(u64 a, u64 b, u64 q) {
   return (u64)(((u128)a * b) % q);
@@ -404,10 +410,20 @@ __device__ __forceinline__ void gen_i64_top(u64* sm, int t, int nt, const i64* _
   }
 }
 
-template <int LOGN, int KM, bool RELAX>
+// TERN: the polynomial is ternary, and the top stage's products are
+// selections (outputs below 2q).
+template <int LOGN, int KM, bool RELAX, bool TERN = false>
 __device__ __forceinline__ void gen_i8_top(u64* sm, int t, int nt, const int8_t* __restrict__ a, u64 q,
                                            ulonglong2 w1) {
   constexpr int H = (1 << LOGN) / 2;
+  if constexpr (TERN) {
+    for (int k = t; k < H; k += nt) {
+      const u64 x = small_res(__ldg(a + k), q), p = mul_tern(__ldg(a + k + H), w1.x, q);
+      sm[swz<LOGN, KM>(k)] = x + p;
+      sm[swz<LOGN, KM>(k + H)] = x - p + q;
+    }
+    return;
+  }
   for (int k = t; k < H; k += nt) {
     u64 x = small_res(__ldg(a + k), q), y = small_res(__ldg(a + k + H), q);
     bfly<RELAX>(x, y, w1, q);
@@ -481,10 +497,18 @@ __device__ __forceinline__ void gen_i64_half(u64* sm, int t, int nt, int h, cons
                                        reduce_biased((u64)__ldg(a + k + HALF), q, mu, moff), h, w1, w1s, q);
 }
 
-template <int LOGH, int KM = 4>
+// TERN: ternary polynomial, first-stage products by selection (below 2q).
+template <int LOGH, int KM = 4, bool TERN = false>
 __device__ __forceinline__ void gen_i8_half(u64* sm, int t, int nt, int h, const int8_t* __restrict__ a, u64 q, u64 w1,
                                             u64 w1s) {
   constexpr int HALF = 1 << LOGH;
+  if constexpr (TERN) {
+    for (int k = t; k < HALF; k += nt) {
+      const int b = __ldg(a + k + HALF);
+      sm[swz<LOGH, KM>(k)] = small_res(__ldg(a + k), q) + mul_tern(h ? -b : b, w1, q);
+    }
+    return;
+  }
   for (int k = t; k < HALF; k += nt)
     sm[swz<LOGH, KM>(k)] = first_stage(small_res(__ldg(a + k), q), small_res(__ldg(a + k + HALF), q), h, w1, w1s, q);
 }
@@ -507,10 +531,25 @@ __device__ __forceinline__ void gen_i64_half2(u64* sm, int t, int nt, int h, con
   }
 }
 
-template <int LOGH, int KM, bool RELAX>
+// TERN: ternary polynomial, both stages from selections.  With w1 = tw[1] =
+// psi^(N/2), w2 = tw[2 + h], w3 = tw[3 - h] (psi^(N/4), psi^(3N/4) taken in
+// the order h, 1 - h) and psi^N = -1: w1 w2 = w3 for h = 0 and -w1 w2 = w3
+// for h = 1, so the first-stage output y = a1 +- b1 w1 enters the second
+// stage as y w2 = a1 w2 + b1 w3 (outputs below 4q, no multiplication).
+template <int LOGH, int KM, bool RELAX, bool TERN = false>
 __device__ __forceinline__ void gen_i8_half2(u64* sm, int t, int nt, int h, const int8_t* __restrict__ a, u64 q,
-                                             ulonglong2 w1, ulonglong2 w2) {
+                                             ulonglong2 w1, ulonglong2 w2, ulonglong2 w3) {
   constexpr int HALF = 1 << LOGH, Q2 = HALF / 2;
+  if constexpr (TERN) {
+    for (int k = t; k < Q2; k += nt) {
+      const int b0 = __ldg(a + k + HALF);
+      const u64 x = small_res(__ldg(a + k), q) + mul_tern(h ? -b0 : b0, w1.x, q);                      // [0, 2q)
+      const u64 yw = mul_tern(__ldg(a + k + Q2), w2.x, q) + mul_tern(__ldg(a + k + Q2 + HALF), w3.x, q);  // [0, 2q]
+      sm[swz<LOGH, KM>(k)] = x + yw;
+      sm[swz<LOGH, KM>(k + Q2)] = x - yw + 2 * q;
+    }
+    return;
+  }
   for (int k = t; k < Q2; k += nt) {
     u64 x = first_stage(small_res(__ldg(a + k), q), small_res(__ldg(a + k + HALF), q), h, w1.x, w1.y, q);
     u64 y = first_stage(small_res(__ldg(a + k + Q2), q), small_res(__ldg(a + k + Q2 + HALF), q), h, w1.x, w1.y, q);

@@ -80,7 +80,7 @@ __device__ __forceinline__ void fn_unit_q(const ulonglong2* tw, u64 q, const FnL
   if constexpr (!ZINC) {
     const u64* k0s = o.k0s;
     const u64* k1s = o.k1s;
-    if constexpr (TOP) gen_i8_top<LOGN, KM, RELAX>(sm, t, S::T, o.u, q, __ldg(tw + 1));
+    if constexpr (TOP) gen_i8_top<LOGN, KM, RELAX, true>(sm, t, S::T, o.u, q, __ldg(tw + 1));
     else gen_i8<LOGN, KM>(sm, t, S::T, o.u, q);
     auto st_u = [&](int idx, u64 uh) {
       c0[idx] = mul_shoup(uh, __ldg(k0 + idx), __ldg(k0s + idx), q);
@@ -120,8 +120,8 @@ __device__ __forceinline__ void fn_half_unit_q(const ulonglong2* tw, u64 q, int 
   if constexpr (!ZINC) {
     const u64* k0s = o.k0s;
     const u64* k1s = o.k1s;
-    if constexpr (TOP) gen_i8_half2<LOGH, KM, RELAX>(sm, t, S::T, h, o.u, q, w1p, __ldg(tw + tmul));
-    else gen_i8_half<LOGH, KM>(sm, t, S::T, h, o.u, q, w1p.x, w1p.y);
+    if constexpr (TOP) gen_i8_half2<LOGH, KM, RELAX, true>(sm, t, S::T, h, o.u, q, w1p, __ldg(tw + tmul), __ldg(tw + 5 - tmul));
+    else gen_i8_half<LOGH, KM, true>(sm, t, S::T, h, o.u, q, w1p.x, w1p.y);
     auto st_u = [&](int idx, u64 uh) {
       c0[idx] = mul_shoup(uh, __ldg(k0 + idx), __ldg(k0s + idx), q);
       c1[idx] = mul_shoup(uh, __ldg(k1 + idx), __ldg(k1s + idx), q);

@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(NttShape<LOGH, 5>::T) k_ms_special_half(DevPar
   const int8_t* sp = A.small + b * 3 * N;
   const u64* kn = A.keyn + (size_t)j * N + (size_t)h * HALF;
   const u64* kns = kn + 2 * (size_t)N;
-  gen_i8_half<LOGH>(sm, t, S::T, h, sp, p, w1.x, w1.y);
+  gen_i8_half<LOGH, 4, true>(sm, t, S::T, h, sp, p, w1.x, w1.y);
   auto st_u = [&](int idx, u64 uh) { sm[swz<LOGH>(idx)] = mul_shoup(uh, __ldg(kn + idx), __ldg(kns + idx), p); };
   ntt_chain<LOGH, 5, LOGH, false, decltype(st_u)>(sm, t, tw, 2 + h, p, st_u);
   u64* o = A.tmp + (b * 2 + j) * N + (size_t)h * HALF;

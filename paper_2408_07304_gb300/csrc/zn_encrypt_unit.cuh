@@ -41,9 +41,9 @@ __device__ __forceinline__ void encrypt_unit_q(const DevParams& P, const EncArgs
   const int8_t* sp = A.small + b * 2 * S::N;
   const u64* k0 = A.key + (size_t)i * S::N;
   const u64* k1 = k0 + (size_t)L * S::N;
-  auto load_small = [&](const int8_t* src) {
+  auto load_small = [&](const int8_t* src, auto tern) {
     if (!active) return;
-    if constexpr (TOP) gen_i8_top<LOGN, KM, RELAX>(sm, t, S::T, src, q, __ldg(tw + 1));
+    if constexpr (TOP) gen_i8_top<LOGN, KM, RELAX, decltype(tern)::value>(sm, t, S::T, src, q, __ldg(tw + 1));
     else gen_i8<LOGN, KM>(sm, t, S::T, src, q);
   };
   auto load_me = [&]() {
@@ -55,7 +55,7 @@ __device__ __forceinline__ void encrypt_unit_q(const DevParams& P, const EncArgs
     const u64* k0s = A.keys + (size_t)i * S::N;
     const u64* k1s = k0s + (size_t)L * S::N;
     // u-hat, then the two key products (kept lazily in [0, 2q) in the output)
-    load_small(sp);
+    load_small(sp, std::true_type{});
     auto st_u = [&](int idx, u64 uh) {
       if (!active) return;
       c0[idx] = mul_shoup(uh, __ldg(k0 + idx), __ldg(k0s + idx), q);
@@ -71,7 +71,7 @@ __device__ __forceinline__ void encrypt_unit_q(const DevParams& P, const EncArgs
     ntt_chain<LOGN, LOGPER, HI, RELAX, decltype(st_0), KM, true, KM == 3>(sm, t, tw, 1, q, st_0);
     // e1 -> c1
     __syncthreads();
-    load_small(sp + S::N);
+    load_small(sp + S::N, std::false_type{});
     auto st_1 = [&](int idx, u64 x) {
       if (active) c1[idx] = reduce_sum<RELAX>(c1[idx] + x, q);
     };
@@ -83,7 +83,7 @@ __device__ __forceinline__ void encrypt_unit_q(const DevParams& P, const EncArgs
     };
     ntt_chain<LOGN, LOGPER, HI, RELAX, decltype(st_0), KM, true, KM == 3>(sm, t, tw, 1, q, st_0);
     __syncthreads();
-    load_small(sp);
+    load_small(sp, std::false_type{});
     auto st_1 = [&](int idx, u64 x) {
       if (active) c1[idx] = reduce_sum<RELAX>(__ldg(k1 + idx) + x, q);
     };
@@ -117,9 +117,10 @@ __device__ __forceinline__ void encrypt_half_unit_q(const DevParams& P, const En
   const u64* k1 = k0 + (size_t)L * N;
   const int tmul = 2 + h;
   auto sum = [&](u64 a, u64 x) { return RAW ? reduce_sum<RELAX>(a + x, q) : reduce4(a + x, q); };
-  auto load_small = [&](const int8_t* src) {
-    if constexpr (TOP) gen_i8_half2<LOGH, KM, RELAX>(sm, t, S::T, h, src, q, w1p, __ldg(tw + tmul));
-    else gen_i8_half<LOGH, KM>(sm, t, S::T, h, src, q, w1, w1s);
+  auto load_small = [&](const int8_t* src, auto tern) {
+    constexpr bool TERN = decltype(tern)::value;
+    if constexpr (TOP) gen_i8_half2<LOGH, KM, RELAX, TERN>(sm, t, S::T, h, src, q, w1p, __ldg(tw + tmul), __ldg(tw + 5 - tmul));
+    else gen_i8_half<LOGH, KM, TERN>(sm, t, S::T, h, src, q, w1, w1s);
   };
   auto load_me = [&]() {
     if constexpr (TOP) gen_i64_half2<LOGH, KM, RELAX>(sm, t, S::T, h, me, q, mu, moff, w1p, __ldg(tw + tmul));
@@ -128,7 +129,7 @@ __device__ __forceinline__ void encrypt_half_unit_q(const DevParams& P, const En
   if constexpr (!ZINC) {
     const u64* k0s = A.keys + (size_t)i * N + off;
     const u64* k1s = k0s + (size_t)L * N;
-    load_small(sp);
+    load_small(sp, std::true_type{});
     auto st_u = [&](int idx, u64 uh) {
       c0[idx] = mul_shoup(uh, __ldg(k0 + idx), __ldg(k0s + idx), q);
       c1[idx] = mul_shoup(uh, __ldg(k1 + idx), __ldg(k1s + idx), q);
@@ -139,7 +140,7 @@ __device__ __forceinline__ void encrypt_half_unit_q(const DevParams& P, const En
     auto st_0 = [&](int idx, u64 x) { c0[idx] = sum(c0[idx], x); };
     ntt_chain<LOGH, LOGPER, HI, RELAX, decltype(st_0), KM, RAW, KM == 3>(sm, t, tw, tmul, q, st_0);
     __syncthreads();
-    load_small(sp + N);
+    load_small(sp + N, std::false_type{});
     auto st_1 = [&](int idx, u64 x) { c1[idx] = sum(c1[idx], x); };
     ntt_chain<LOGH, LOGPER, HI, RELAX, decltype(st_1), KM, RAW, KM == 3>(sm, t, tw, tmul, q, st_1);
   } else {
@@ -147,7 +148,7 @@ __device__ __forceinline__ void encrypt_half_unit_q(const DevParams& P, const En
     auto st_0 = [&](int idx, u64 x) { c0[idx] = sum(__ldg(k0 + idx), x); };
     ntt_chain<LOGH, LOGPER, HI, RELAX, decltype(st_0), KM, RAW, KM == 3>(sm, t, tw, tmul, q, st_0);
     __syncthreads();
-    load_small(sp);
+    load_small(sp, std::false_type{});
     auto st_1 = [&](int idx, u64 x) { c1[idx] = sum(__ldg(k1 + idx), x); };
     ntt_chain<LOGH, LOGPER, HI, RELAX, decltype(st_1), KM, RAW, KM == 3>(sm, t, tw, tmul, q, st_1);
   }
@@ -304,7 +305,7 @@ __device__ __forceinline__ void encrypt_mp_unit_q(const DevParams& P, const EncA
   } else {
     const ulonglong2 w1 = __ldg(tw + 1);
     if constexpr (!ZINC) {
-      gen_i8_half<LOGM>(sm, t, T, h, sp, q, w1.x, w1.y);
+      gen_i8_half<LOGM, 4, true>(sm, t, T, h, sp, q, w1.x, w1.y);
       gen_i64_half<LOGM>(sm + M, t, T, h, me, q, mu, moff, w1.x, w1.y);
       gen_i8_half<LOGM>(sm + 2 * M, t, T, h, sp + N, q, w1.x, w1.y);
     } else {
