@@ -449,6 +449,15 @@ int zn_probe_butterfly(int device, double* butterflies_per_s);
  * a transform's final reduction would do. */
 int zn_probe_butterfly_relaxed(int device, double* butterflies_per_s);
 
+/* Host-side fault injection for tests of the callers' error paths (no
+ * counterpart in the paper): the next `count` per-call scratch allocations,
+ * in any context and on any thread, fail as if the device memory pool were
+ * exhausted, so the calls that make them return ZN_ENOMEM before launching
+ * anything and leave their context usable.  Touches no device state and
+ * injects nothing on the GPU.  count = 0 clears a pending injection;
+ * count < 0 returns ZN_EINVAL. */
+int zn_inject_alloc_failures(int count);
+
 /* ------------------------------------------------ host-side tables (no GPU) */
 
 /* The host computations behind zn_ctx_create, exposed so that they can be

@@ -98,6 +98,7 @@ _SIGS = {
     "zn_autotune": (_i32, [_vp, _vp, _vp, _u32, _vp, _vp]),
     "zn_probe_butterfly": (_i32, [_i32, _vp]),
     "zn_probe_butterfly_relaxed": (_i32, [_i32, _vp]),
+    "zn_inject_alloc_failures": (_i32, [_i32]),
     "zn_timing_enable": (_i32, [_vp, _i32]),
     "zn_timing_read": (_i32, [_vp, _i32, _vp, _vp]),
     "zn_host_primes": (_i32, [_u32, _vp, _u32, _vp]),
@@ -737,6 +738,12 @@ def zn_probe_butterfly_relaxed(device=0):
     r = ctypes.c_double()
     _check(lib().zn_probe_butterfly_relaxed(device, ctypes.byref(r)), "zn_probe_butterfly_relaxed")
     return r.value
+
+
+def zn_inject_alloc_failures(count):
+    """Make the next `count` per-call scratch allocations fail with ZN_ENOMEM
+    (host-side fault injection for tests; 0 clears)."""
+    _check(lib().zn_inject_alloc_failures(int(count)), "zn_inject_alloc_failures")
 
 
 def zn_probe_butterfly(device=0):

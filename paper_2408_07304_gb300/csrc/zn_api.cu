@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <mutex>
 #include <cstdlib>
+#include <atomic>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -127,6 +128,17 @@ struct DeviceGuard {
     }                                      \
   } while (0)
 
+// Host-side fault injection (zn_inject_alloc_failures): the number of
+// scratch allocations still to fail.
+std::atomic<int> g_alloc_faults{0};
+
+bool take_alloc_fault() {
+  int n = g_alloc_faults.load(std::memory_order_relaxed);
+  while (n > 0)
+    if (g_alloc_faults.compare_exchange_weak(n, n - 1, std::memory_order_relaxed)) return true;
+  return false;
+}
+
 // Stream-ordered scratch from the context's memory pool: concurrent calls on
 // different streams never share scratch, and the allocations are legal
 // inside a CUDA-graph capture.
@@ -136,6 +148,10 @@ struct Scratch {
   void* p = nullptr;
   Scratch(zn_ctx* c_, cudaStream_t st_) : c(c_), st(st_) {}
   bool alloc(size_t bytes) {
+    if (take_alloc_fault()) {
+      p = nullptr;
+      return false;
+    }
     if (cudaMallocFromPoolAsync(&p, bytes, c->pool, st) != cudaSuccess) {
       cudaGetLastError();
       p = nullptr;
@@ -1722,6 +1738,12 @@ int zn_probe_butterfly_relaxed(int device, double* per_s) {
     return ZN_ECUDA;
   }
   return zn::probe_butterfly(sms, per_s, true) == cudaSuccess ? ZN_OK : ZN_ECUDA;
+}
+
+int zn_inject_alloc_failures(int count) {
+  if (count < 0) return ZN_EINVAL;
+  g_alloc_faults.store(count, std::memory_order_relaxed);
+  return ZN_OK;
 }
 
 // ------------------------------------------------------------ building blocks

@@ -12,7 +12,13 @@ and Zinc cache resident on the device and runs an event loop:
   copied on that stream, and the encryption launched on the same stream;
 * batches on different streams overlap on the device; a batch's HBM
   reservation (slots, ciphertexts, scratch) is released when its completion
-  event fires, which admits the next requests.
+  event fires, which admits the next requests;
+* a launch refused for lack of device memory (``ZN_ENOMEM``: the budget is
+  an estimate, the pool is shared) puts its batch back at the head of its
+  queue, in arrival order, to be retried after the next completion -- or,
+  with nothing in flight, after a short pause, at most ``max_alloc_retries``
+  times in a row; any other error, or running out of retries, fails only
+  that batch's requests, which are reported and not retried.
 
 Each request's ciphertext depends only on (key, seed, request id, slots):
 the request id is the Philox ct_index, so a result is bit-identical whether
@@ -72,9 +78,11 @@ def poisson_requests(n, rate, seed=5, weights=(0.5, 0.3, 0.2), zinc_frac=0.8):
 
 
 class Server:
-    def __init__(self, device=0, n_streams=4, max_batch=256, hbm_budget=16 << 30, seed=11, keep_results=False):
+    def __init__(self, device=0, n_streams=4, max_batch=256, hbm_budget=16 << 30, seed=11, keep_results=False,
+                 max_alloc_retries=100):
         import torch
         self.torch = torch
+        self.max_alloc_retries = max_alloc_retries
         self.dev = torch.device("cuda", device)
         torch.cuda.set_device(self.dev)
         self.max_batch = max_batch
@@ -117,6 +125,9 @@ class Server:
         inflight = []
         reserved = 0
         done = []
+        failed = []             # (rid, status) of requests whose batch failed
+        alloc_retries = 0
+        enomem_streak = 0       # consecutive refusals with nothing in flight
         peak_inflight = 0
         peak_reserved = 0
         t_ref = torch.cuda.Event(enable_timing=True)
@@ -144,7 +155,8 @@ class Server:
             inflight = still
             # launch while a stream and budget are available
             launched = False
-            while free:
+            refused = False
+            while free and not refused:
                 heads = [(q[0].arrival, key) for key, q in queues.items() if q]
                 if not heads:
                     break
@@ -164,22 +176,37 @@ class Server:
                     break           # over budget: wait for a completion
                 si = free.pop()
                 nbytes = self.batch_bytes(ring, len(batch), ns)
+                try:
+                    out = self._launch(self.streams[si], ring, zinc, batch, ns)
+                except api.ZincError as e:
+                    free.append(si)
+                    if e.status == api.ZN_ENOMEM and (inflight or enomem_streak < self.max_alloc_retries):
+                        q.extendleft(reversed(batch))       # retried first, arrival order kept
+                        alloc_retries += 1
+                        enomem_streak += 0 if inflight else 1
+                        refused = True                      # wait for a completion (or a pause)
+                    else:
+                        failed.extend((r.rid, e.status) for r in batch)
+                    continue
+                enomem_streak = 0
                 reserved += nbytes
                 peak_reserved = max(peak_reserved, reserved)
-                out = self._launch(self.streams[si], ring, zinc, batch, ns)
                 ev = torch.cuda.Event(enable_timing=True)
                 ev.record(self.streams[si])
                 inflight.append((ev, si, batch, nbytes, out))
                 peak_inflight = max(peak_inflight, len(inflight))
                 launched = True
-            if not launched:
+            if refused and not inflight:
+                time.sleep(1e-3)    # a pool short with nothing in flight: pause before the retry
+            elif not launched:
                 if pending and not inflight and not any(queues.values()):
                     time.sleep(max(0.0, min(pending[0].arrival - (time.perf_counter() - t0), 1e-3)))
                 else:
                     time.sleep(20e-6)
         torch.cuda.synchronize(self.dev)
         wall = time.perf_counter() - t0
-        return done, {"wall_s": wall, "peak_inflight_batches": peak_inflight, "peak_reserved_bytes": peak_reserved}
+        return done, {"wall_s": wall, "peak_inflight_batches": peak_inflight, "peak_reserved_bytes": peak_reserved,
+                      "failed": failed, "alloc_retries": alloc_retries}
 
     def _launch(self, stream, ring, zinc, batch, ns):
         torch = self.torch
@@ -211,7 +238,8 @@ def summarize(done, info, n_requests):
             "enc_per_s": len(done) / info["wall_s"], "wall_s": info["wall_s"],
             "zinc_fraction": float(np.mean([d.zinc for d in done])), "per_ring": dict(by_ring),
             "peak_inflight_batches": info["peak_inflight_batches"],
-            "peak_reserved_gib": info["peak_reserved_bytes"] / 2 ** 30}
+            "peak_reserved_gib": info["peak_reserved_bytes"] / 2 ** 30,
+            "failed": len(info.get("failed", ())), "alloc_retries": info.get("alloc_retries", 0)}
 
 
 def serve_benchmark(n_requests=20000, load=0.7, device=0, seed=5, **kw):

@@ -80,3 +80,12 @@ def test_invalid_params_rejected_without_gpu(built):
     with pytest.raises(api.ZincError) as e:
         api.zn_host_primes(12, (20,) * 40)        # runs out of 20-bit primes = 1 mod 8192
     assert e.value.status == api.ZN_ENOPRIME
+
+
+def test_alloc_fault_injector_arguments(built):
+    # host-side only: sets a counter, touches no device state
+    api.zn_inject_alloc_failures(3)
+    api.zn_inject_alloc_failures(0)
+    with pytest.raises(api.ZincError) as e:
+        api.zn_inject_alloc_failures(-1)
+    assert e.value.status == api.ZN_EINVAL

@@ -1,0 +1,91 @@
+"""Error paths under host-side fault injection (no GPU fault): per-call
+scratch allocations made to fail with zn_inject_alloc_failures.  A refused
+call returns ZN_ENOMEM before launching anything and leaves its context
+usable -- the next call gives the same ciphertexts as an undisturbed one --
+and the serving loop puts a refused batch back at the head of its queue,
+retries it, and completes every request bit-identically; when the retries
+run out with nothing in flight, only that batch's requests fail.
+"""
+import numpy as np
+import pytest
+
+from paper_2408_07304_gb300 import api, serve
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(autouse=True)
+def _clear():
+    yield
+    api.zn_inject_alloc_failures(0)
+
+
+def _ctx():
+    from paper_2408_07304_gb300 import build
+    build.build()
+    ctx = api.Context(12, (36, 36, 37), 30, device=0)
+    sk, pk = api.ckks_keygen(ctx, 1)
+    return ctx, sk, pk
+
+
+def test_refused_call_leaves_context_usable():
+    ctx, sk, pk = _ctx()
+    zc = api.zinc_precompute(ctx, pk, 2)
+    z = torch.tensor(np.random.default_rng(0).uniform(-1, 1, (3, 100)), device="cuda:0")
+    idx = torch.arange(3, dtype=torch.int64, device="cuda:0")
+    calls = [lambda: api.ckks_encrypt(ctx, pk, z, 5, idx), lambda: api.zinc_encrypt(ctx, zc, z, 5, idx),
+             lambda: api.ckks_encrypt_ms(ctx, pk, z, 5, idx)]
+    for call in calls:
+        ref = call()
+        torch.cuda.synchronize()
+        api.zn_inject_alloc_failures(1)
+        with pytest.raises(api.ZincError) as e:
+            call()
+        assert e.value.status == api.ZN_ENOMEM
+        assert torch.equal(call(), ref)
+    api.zn_sync_status(ctx)
+    # the host-buffer entry point refuses as a whole and then runs normally
+    hz, hidx = z.cpu().pin_memory(), idx.cpu().pin_memory()
+    out = torch.empty((3, 2, ctx.L, ctx.n), dtype=torch.int64, pin_memory=True)
+    api.zn_inject_alloc_failures(1)
+    with pytest.raises(api.ZincError) as e:
+        api.zn_encrypt_host(ctx, pk, hz, 5, hidx, out)
+    assert e.value.status == api.ZN_ENOMEM
+    api.zn_encrypt_host(ctx, pk, hz, 5, hidx, out)
+    assert torch.equal(out, calls[0]().cpu())
+
+
+@pytest.fixture(scope="module")
+def server():
+    from paper_2408_07304_gb300 import build
+    build.build()
+    return serve.Server(device=0, n_streams=3, max_batch=16, hbm_budget=4 << 30, keep_results=True)
+
+
+def test_server_retries_refused_batches(server):
+    reqs = serve.poisson_requests(96, rate=20000.0, seed=21)
+    api.zn_inject_alloc_failures(5)
+    done, info = server.run(reqs)
+    assert info["alloc_retries"] == 5 and not info["failed"]
+    assert sorted(d.rid for d in done) == list(range(len(reqs)))
+    by = {d.rid: d for d in done}
+    for rid in np.random.default_rng(1).choice(len(reqs), 12, replace=False):
+        assert torch.equal(by[rid].ct, server.encrypt_one(reqs[rid])), rid
+    s = serve.summarize(done, info, len(reqs))
+    assert s["alloc_retries"] == 5 and s["failed"] == 0
+
+
+def test_server_fails_batch_when_retries_run_out(server):
+    old = server.max_alloc_retries
+    server.max_alloc_retries = 2
+    try:
+        reqs = serve.poisson_requests(1, rate=None, seed=3)
+        api.zn_inject_alloc_failures(3)        # the first try and both retries
+        done, info = server.run(reqs)
+        assert not done and info["failed"] == [(0, api.ZN_ENOMEM)] and info["alloc_retries"] == 2
+        done, info = server.run(reqs)          # nothing left to inject: served normally
+        assert [d.rid for d in done] == [0] and not info["failed"]
+        assert torch.equal(done[0].ct, server.encrypt_one(reqs[0]))
+    finally:
+        server.max_alloc_retries = old
