@@ -9,7 +9,11 @@
  *  - Pointers marked "device" are CUDA device pointers owned by the caller
  *    (e.g. torch tensors' data_ptr()); "host" pointers are ordinary host memory.
  *    The library never frees caller memory.  Handles (zn_ctx, zn_sk, zn_pk,
- *    zn_zcache) are owned by the library and released by their destroy call.
+ *    zn_zcache, zn_nbasis, zn_slot_encoder, zn_batch) are owned by the
+ *    library and released by their destroy call; a handle made in a context
+ *    may be released before or after that context (it keeps its device).
+ *    Release calls consume any CUDA error of their own, so none surfaces at
+ *    the caller's next CUDA check.
  *  - Work is enqueued on the caller's cudaStream_t (passed as void*, 0 = the
  *    legacy default stream) and is asynchronous unless stated otherwise.
  *    Errors detected on the device (encode overflow) are latched in a status
@@ -83,7 +87,8 @@ void zn_ctx_destroy(zn_ctx* ctx);
 int zn_ctx_primes(const zn_ctx* ctx, uint64_t* primes, uint64_t* psis);
 
 /* Read and clear the device status word after synchronising `stream`;
- * returns ZN_OK, ZN_EOVERFLOW, ZN_ETIMEOUT or ZN_ECUDA. */
+ * returns ZN_OK, ZN_EOVERFLOW, ZN_ETIMEOUT, ZN_EINVAL (zn_ct_unpack met a
+ * residue not below its prime) or ZN_ECUDA. */
 int zn_sync_status(zn_ctx* ctx, void* stream);
 
 const char* zn_strerror(int status);
@@ -308,6 +313,30 @@ int zinc_encrypt_ntt(zn_ctx* ctx, const zn_zcache* zc, const zn_nbasis* nb, cons
 int zn_encrypt_host(zn_ctx* ctx, const zn_pk* pk, const zn_zcache* zc, const double* host_slots,
                     uint32_t n_slots, uint32_t batch, uint64_t seed, const uint64_t* host_ct_index,
                     uint64_t* host_ct, uint32_t chunk);
+
+/* ------------------------------------------- packed ciphertext serialization
+ * No counterpart in the paper (a wire format for the ciphertexts that
+ * Eq. 8 / Algorithm 1 produce).  Each residue mod q_i takes bits_i = bit
+ * length of q_i bits instead of a 64-bit word.  Per ciphertext: component 0,
+ * then 1; within a component prime 0..L-1; a limb is its N residues as one
+ * little-endian bit stream (residue j in bits [j bits_i, (j+1) bits_i),
+ * ceil(N bits_i / 64) uint64 words, unused high bits of the last word zero).
+ * The 60 + 6x50 + 60-bit chain packs to 420/512 of the plain size.
+ *
+ * zn_ct_packed_words: uint64 words of one packed ciphertext (0 for NULL).
+ * zn_ct_pack: device ct [batch][2][L][N] (residues below their primes) ->
+ *   device packed [batch][packed_words].  Stream-ordered.
+ * zn_ct_unpack: the inverse; a residue not below its prime is written as read
+ *   and latched (zn_sync_status then returns ZN_EINVAL).  Stream-ordered.
+ * zn_encrypt_host_packed: zn_encrypt_host with the output packed on the device
+ *   before the copy: host_packed [batch][packed_words]; equals zn_ct_pack of
+ *   zn_encrypt_host's ciphertexts.  Synchronous. */
+size_t zn_ct_packed_words(const zn_ctx* ctx);
+int zn_ct_pack(zn_ctx* ctx, const uint64_t* ct, size_t batch, uint64_t* packed, void* stream);
+int zn_ct_unpack(zn_ctx* ctx, const uint64_t* packed, size_t batch, uint64_t* ct, void* stream);
+int zn_encrypt_host_packed(zn_ctx* ctx, const zn_pk* pk, const zn_zcache* zc, const double* host_slots,
+                           uint32_t n_slots, uint32_t batch, uint64_t seed, const uint64_t* host_ct_index,
+                           uint64_t* host_packed, uint32_t chunk);
 
 /* -------------------------------------------------------------- decrypt */
 

@@ -89,6 +89,10 @@ _SIGS = {
     "zn_sample": (_i32, [_vp, _i32, _u64, _u32, _u32, _u32, _u64, _u32, _vp, _vp]),
     "zn_chi_eval": (_i32, [_vp, _vp, _u32, _vp, _vp]),
     "zn_encrypt_host": (_i32, [_vp, _vp, _vp, _vp, _u32, _u32, _u64, _vp, _vp, _u32]),
+    "zn_encrypt_host_packed": (_i32, [_vp, _vp, _vp, _vp, _u32, _u32, _u64, _vp, _vp, _u32]),
+    "zn_ct_packed_words": (ctypes.c_size_t, [_vp]),
+    "zn_ct_pack": (_i32, [_vp, _vp, ctypes.c_size_t, _vp, _vp]),
+    "zn_ct_unpack": (_i32, [_vp, _vp, ctypes.c_size_t, _vp, _vp]),
     "zn_batch_create": (_i32, [_vp, _u32, _i32, _pp]),
     "zn_batch_destroy": (None, [_vp]),
     "zn_batch_run": (_i32, [_vp, _vp, _i32]),
@@ -528,23 +532,61 @@ def bgv_decrypt(ctx, sk, t, ct, stream=None):
     return _int_dec(lib().bgv_decrypt, ctx, sk, t, ct, stream, "bgv_decrypt")
 
 
-def zn_encrypt_host(ctx, key, slots, seed, ct_index, out, chunk=0):
-    """Host-to-host encryption (pipelined copies + kernels).  key: PublicKey
-    (vanilla) or ZincCache (Zinc); slots: CPU float64 [B, n_slots]; ct_index:
-    CPU int64 [B]; out: CPU int64 [B, 2, L, N] (pinned tensors give
-    asynchronous copies).  Synchronous."""
+def _host_call(name, ctx, key, slots, seed, ct_index, out, out_shape, chunk):
     import torch
     B, ns = slots.shape
     for t, dt, shape, nm in ((slots, torch.float64, None, "slots"), (ct_index, torch.int64, (B,), "ct_index"),
-                             (out, torch.int64, (B, 2, ctx.L, ctx.n), "out")):
+                             (out, torch.int64, out_shape(B), "out")):
         if not isinstance(t, torch.Tensor) or t.is_cuda or t.dtype != dt or not t.is_contiguous():
             raise TypeError(f"{nm}: expected a contiguous CPU tensor of {dt}")
         if shape is not None and tuple(t.shape) != tuple(shape):
             raise ValueError(f"{nm}: expected shape {shape}")
     zinc = isinstance(key, ZincCache)
-    _check(lib().zn_encrypt_host(ctx.handle, None if zinc else key.handle, key.handle if zinc else None,
-                                 slots.data_ptr(), ns, B, seed, ct_index.data_ptr(), out.data_ptr(), chunk),
-           "zn_encrypt_host")
+    _check(getattr(lib(), name)(ctx.handle, None if zinc else key.handle, key.handle if zinc else None,
+                                slots.data_ptr(), ns, B, seed, ct_index.data_ptr(), out.data_ptr(), chunk), name)
+    return out
+
+
+def zn_encrypt_host(ctx, key, slots, seed, ct_index, out, chunk=0):
+    """Host-to-host encryption (pipelined copies + kernels).  key: PublicKey
+    (vanilla) or ZincCache (Zinc); slots: CPU float64 [B, n_slots]; ct_index:
+    CPU int64 [B]; out: CPU int64 [B, 2, L, N] (pinned tensors give
+    asynchronous copies).  Synchronous."""
+    return _host_call("zn_encrypt_host", ctx, key, slots, seed, ct_index, out,
+                      lambda B: (B, 2, ctx.L, ctx.n), chunk)
+
+
+def zn_ct_packed_words(ctx):
+    """uint64 words of one packed ciphertext of this context."""
+    return int(lib().zn_ct_packed_words(ctx.handle))
+
+
+def zn_encrypt_host_packed(ctx, key, slots, seed, ct_index, out, chunk=0):
+    """zn_encrypt_host with the ciphertexts packed (zn_ct_pack) on the device
+    before the copy: out CPU int64 [B, zn_ct_packed_words(ctx)]."""
+    return _host_call("zn_encrypt_host_packed", ctx, key, slots, seed, ct_index, out,
+                      lambda B: (B, zn_ct_packed_words(ctx)), chunk)
+
+
+def zn_ct_pack(ctx, ct, out=None, stream=None):
+    """Device int64 [B, 2, L, N] -> packed device int64 [B, zn_ct_packed_words(ctx)]."""
+    import torch
+    B, W = ct.shape[0], zn_ct_packed_words(ctx)
+    out = _out(out, (B, W), torch.int64, ct.device)
+    _dev(ct, torch.int64, (B, 2, ctx.L, ctx.n), "ct")
+    _dev(out, torch.int64, (B, W), "out")
+    _check(lib().zn_ct_pack(ctx.handle, ct.data_ptr(), B, out.data_ptr(), _stream(stream)), "zn_ct_pack")
+    return out
+
+
+def zn_ct_unpack(ctx, packed, out=None, stream=None):
+    """Packed device int64 [B, zn_ct_packed_words(ctx)] -> device int64 [B, 2, L, N]."""
+    import torch
+    B, W = packed.shape[0], zn_ct_packed_words(ctx)
+    out = _out(out, (B, 2, ctx.L, ctx.n), torch.int64, packed.device)
+    _dev(packed, torch.int64, (B, W), "packed")
+    _dev(out, torch.int64, (B, 2, ctx.L, ctx.n), "out")
+    _check(lib().zn_ct_unpack(ctx.handle, packed.data_ptr(), B, out.data_ptr(), _stream(stream)), "zn_ct_unpack")
     return out
 
 

@@ -49,6 +49,7 @@ enum : uint32_t {
 struct zn_slot_encoder {
   uint32_t tag = kTagSe;
   zn_ctx* ctx;
+  int device = 0;          // the context's device, kept for release after the context
   zn::BatchEnc E;
   void* d;                 // one allocation: twp [N], itw [N], itws [N], pos [N]
 };
@@ -57,6 +58,7 @@ struct zn_slot_encoder {
 struct zn_nbasis {
   uint32_t tag = kTagNb;
   zn_ctx* ctx;
+  int device = 0;          // the context's device, kept for release after the context
   uint32_t K;
   u64* E;                  // [2][K][L][N] NTT form
   u64* thi;                // [L][N/32] psi^(64 h) mod q
@@ -66,6 +68,7 @@ struct zn_nbasis {
 struct zn_pk {
   uint32_t tag = kTagPk;
   zn_ctx* ctx;
+  int device = 0;          // the context's device, kept for release after the context
   u64* d;    // [2][L][N] then Shoup companions [2][L][N]
   // L >= 2: the modulus-switched encryption's key forms -- pk_j p^-1 mod q_i
   // [2][L-1][N] + companions, then pk_{j,p} N^-1 mod p [2][N] + companions
@@ -75,12 +78,14 @@ struct zn_pk {
 struct zn_sk {
   uint32_t tag = kTagSk;
   zn_ctx* ctx;
+  int device = 0;          // the context's device, kept for release after the context
   u64* d;                    // [L][N] NTT form
   std::vector<int8_t> s;     // coefficients
 };
 struct zn_zcache {
   uint32_t tag = kTagZc;
   zn_ctx* ctx;
+  int device = 0;          // the context's device, kept for release after the context
   u64* d;    // [2][L][N]
   uint64_t t = 0;   // 0: a CKKS / BFV encryption of zero; t >= 2: a BGV one
 };
@@ -109,14 +114,23 @@ struct NvtxRange {
 inline size_t limb(const zn_ctx* c) { return (size_t)c->n; }
 inline size_t ring_words(const zn_ctx* c) { return (size_t)c->L * c->n; }
 
+// A release call's failure is not the caller's error: consume it, so that the
+// runtime's last-error state does not report it at the caller's next check.
+inline void released(cudaError_t e) {
+  if (e != cudaSuccess) cudaGetLastError();
+}
+
 struct DeviceGuard {
   int prev = -1;
   explicit DeviceGuard(int dev) {
-    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-    if (prev != dev) cudaSetDevice(dev);
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+      cudaGetLastError();
+      prev = -1;
+    }
+    if (prev != dev) released(cudaSetDevice(dev));
   }
   ~DeviceGuard() {
-    if (prev >= 0) cudaSetDevice(prev);
+    if (prev >= 0) released(cudaSetDevice(prev));
   }
 };
 
@@ -650,14 +664,14 @@ void zn_ctx_destroy(zn_ctx* c) {
   DeviceGuard g(c->device);
   zn_timing_enable(c, 0);
   for (cudaStream_t& h : c->hs)
-    if (h) cudaStreamDestroy(h);
-  cudaFree(c->d_tw);
-  cudaFree(c->d_etw);
-  cudaFree(c->d_slot);
-  cudaFree(c->d_status);
+    if (h) released(cudaStreamDestroy(h));
+  released(cudaFree(c->d_tw));
+  released(cudaFree(c->d_etw));
+  released(cudaFree(c->d_slot));
+  released(cudaFree(c->d_status));
   if (c->pool) {
-    cudaDeviceSynchronize();   // pending stream-ordered frees
-    cudaMemPoolDestroy(c->pool);
+    released(cudaDeviceSynchronize());   // pending stream-ordered frees
+    released(cudaMemPoolDestroy(c->pool));
   }
   delete c;
 }
@@ -680,6 +694,7 @@ int zn_sync_status(zn_ctx* c, void* stream) {
   ZN_CUDA(cudaMemset(c->d_status, 0, sizeof(unsigned)));
   if (st & zn::kStatusOverflow) return ZN_EOVERFLOW;
   if (st & zn::kStatusTimeout) return ZN_ETIMEOUT;
+  if (st & zn::kStatusRange) return ZN_EINVAL;
   return ZN_OK;
 }
 
@@ -688,7 +703,7 @@ int zn_timing_enable(zn_ctx* c, int on) {
   DeviceGuard g(c->device);
   if (!on) {
     for (auto& v : c->ev) {
-      for (cudaEvent_t e : v) cudaEventDestroy(e);
+      for (cudaEvent_t e : v) released(cudaEventDestroy(e));
       v.clear();
     }
   }
@@ -732,7 +747,9 @@ int ckks_keygen(zn_ctx* c, uint64_t seed, zn_sk** sk, zn_pk** pk) {
     return ZN_ENOMEM;
   }
   s->ctx = c;
+  s->device = c->device;
   k->ctx = c;
+  k->device = c->device;
   const size_t rw = ring_words(c);
   i64* d_s = nullptr;
   if (cudaMalloc(&s->d, sizeof(u64) * rw) != cudaSuccess || cudaMalloc(&k->d, sizeof(u64) * 4 * rw) != cudaSuccess ||
@@ -772,23 +789,23 @@ int ckks_keygen(zn_ctx* c, uint64_t seed, zn_sk** sk, zn_pk** pk) {
 void zn_sk_destroy(zn_sk* s) {
   if (!s || s->tag != kTagSk) return;
   s->tag = kTagDead;
-  DeviceGuard g(s->ctx->device);
-  cudaFree(s->d);
+  DeviceGuard g(s->device);
+  released(cudaFree(s->d));
   delete s;
 }
 
 void zn_pk_destroy(zn_pk* k) {
   if (!k || k->tag != kTagPk) return;
   k->tag = kTagDead;
-  DeviceGuard g(k->ctx->device);
-  cudaFree(k->d);
-  cudaFree(k->ms);
+  DeviceGuard g(k->device);
+  released(cudaFree(k->d));
+  released(cudaFree(k->ms));
   delete k;
 }
 
 int zn_pk_export(const zn_pk* k, uint64_t* host_out) {
   if (!k || k->tag != kTagPk || !host_out) return ZN_EINVAL;
-  DeviceGuard g(k->ctx->device);
+  DeviceGuard g(k->device);
   ZN_CUDA(cudaMemcpy(host_out, k->d, sizeof(u64) * 2 * ring_words(k->ctx), cudaMemcpyDeviceToHost));
   return ZN_OK;
 }
@@ -805,6 +822,7 @@ int zn_pk_import(zn_ctx* c, const uint64_t* host_in, zn_pk** out) {
   zn_pk* k = new (std::nothrow) zn_pk();
   if (!k) return ZN_ENOMEM;
   k->ctx = c;
+  k->device = c->device;
   if (cudaMalloc(&k->d, sizeof(u64) * 4 * rw) != cudaSuccess) {
     cudaGetLastError();
     delete k;
@@ -840,6 +858,7 @@ int zn_sk_import(zn_ctx* c, const int8_t* host_in, zn_sk** out) {
   zn_sk* s = new (std::nothrow) zn_sk();
   if (!s) return ZN_ENOMEM;
   s->ctx = c;
+  s->device = c->device;
   s->s.assign(host_in, host_in + c->n);
   const size_t rw = ring_words(c);
   int8_t* d_s = nullptr;
@@ -898,6 +917,7 @@ int zinc_precompute(zn_ctx* c, const zn_pk* pk, uint64_t seed, zn_zcache** out) 
   zn_zcache* z = new (std::nothrow) zn_zcache();
   if (!z) return ZN_ENOMEM;
   z->ctx = c;
+  z->device = c->device;
   if (cudaMalloc(&z->d, sizeof(u64) * 2 * ring_words(c)) != cudaSuccess) {
     cudaGetLastError();
     delete z;
@@ -945,14 +965,14 @@ int zinc_precompute(zn_ctx* c, const zn_pk* pk, uint64_t seed, zn_zcache** out) 
 void zn_zcache_destroy(zn_zcache* z) {
   if (!z || z->tag != kTagZc) return;
   z->tag = kTagDead;
-  DeviceGuard g(z->ctx->device);
-  cudaFree(z->d);
+  DeviceGuard g(z->device);
+  released(cudaFree(z->d));
   delete z;
 }
 
 int zn_zcache_export(const zn_zcache* z, uint64_t* host_out) {
   if (!z || z->tag != kTagZc || !host_out) return ZN_EINVAL;
-  DeviceGuard g(z->ctx->device);
+  DeviceGuard g(z->device);
   ZN_CUDA(cudaMemcpy(host_out, z->d, sizeof(u64) * 2 * ring_words(z->ctx), cudaMemcpyDeviceToHost));
   return ZN_OK;
 }
@@ -969,6 +989,7 @@ int zn_zcache_import(zn_ctx* c, const uint64_t* host_in, zn_zcache** out) {
   zn_zcache* z = new (std::nothrow) zn_zcache();
   if (!z) return ZN_ENOMEM;
   z->ctx = c;
+  z->device = c->device;
   if (cudaMalloc(&z->d, sizeof(u64) * 2 * rw) != cudaSuccess) {
     cudaGetLastError();
     delete z;
@@ -1015,6 +1036,7 @@ int zinc_precompute_ms(zn_ctx* c, const zn_pk* pk, uint64_t seed, zn_ctx* dc, zn
   zn_zcache* z = new (std::nothrow) zn_zcache();
   if (!z) return ZN_ENOMEM;
   z->ctx = dc;
+  z->device = dc->device;
   if (cudaMalloc(&z->d, sizeof(u64) * 2 * ring_words(dc)) != cudaSuccess) {
     cudaGetLastError();
     delete z;
@@ -1100,6 +1122,7 @@ int bgv_zinc_precompute(zn_ctx* c, const zn_pk* pk, uint64_t seed, zn_zcache** o
   zn_zcache* z = new (std::nothrow) zn_zcache();
   if (!z) return ZN_ENOMEM;
   z->ctx = c;
+  z->device = c->device;
   z->t = pk->t;
   if (cudaMalloc(&z->d, sizeof(u64) * 2 * ring_words(c)) != cudaSuccess) {
     cudaGetLastError();
@@ -1165,8 +1188,8 @@ int bgv_decrypt(zn_ctx* c, const zn_sk* sk, uint64_t t, const uint64_t* ct, uint
 void zn_slot_encoder_destroy(zn_slot_encoder* se) {
   if (!se || se->tag != kTagSe) return;
   se->tag = kTagDead;
-  DeviceGuard g(se->ctx->device);
-  cudaFree(se->d);
+  DeviceGuard g(se->device);
+  released(cudaFree(se->d));
   delete se;
 }
 
@@ -1178,6 +1201,7 @@ int zn_slot_encoder_create(zn_ctx* c, uint64_t t, zn_slot_encoder** out) {
   zn_slot_encoder* se = new (std::nothrow) zn_slot_encoder();
   if (!se) return ZN_ENOMEM;
   se->ctx = c;
+  se->device = c->device;
   const u64 psi = zn::find_psi(t, log_n);
   std::vector<u64> tw(n), tws(n), itw(n), itws(n);
   zn::ntt_tables(t, psi, log_n, tw.data(), tws.data(), itw.data(), itws.data());
@@ -1233,7 +1257,7 @@ int zn_slots_encode(zn_slot_encoder* se, const int64_t* slots, uint32_t batch, i
   if (!se || se->tag != kTagSe) return ZN_EINVAL;
   if (batch == 0) return ZN_OK;
   if (!slots || !m) return ZN_EINVAL;
-  DeviceGuard g(se->ctx->device);
+  DeviceGuard g(se->device);
   ZN_CUDA(zn::launch_batch_encode(se->E, slots, batch, m, S(stream)));
   return ZN_OK;
 }
@@ -1243,7 +1267,7 @@ int zn_slots_decode(zn_slot_encoder* se, const int64_t* m, uint32_t batch, int64
   if (!se || se->tag != kTagSe) return ZN_EINVAL;
   if (batch == 0) return ZN_OK;
   if (!slots || !m) return ZN_EINVAL;
-  DeviceGuard g(se->ctx->device);
+  DeviceGuard g(se->device);
   Scratch scratch(se->ctx, S(stream));
   if (!scratch.alloc(sizeof(u64) * batch * (size_t)se->ctx->n)) return ZN_ENOMEM;
   ZN_CUDA(zn::launch_batch_decode(se->E, m, batch, (u64*)scratch.p, slots, S(stream)));
@@ -1255,10 +1279,10 @@ int zn_slots_decode(zn_slot_encoder* se, const int64_t* m, uint32_t batch, int64
 void zn_nbasis_destroy(zn_nbasis* nb) {
   if (!nb || nb->tag != kTagNb) return;
   nb->tag = kTagDead;
-  DeviceGuard g(nb->ctx->device);
-  cudaFree(nb->E);
-  cudaFree(nb->thi);
-  cudaFree(nb->tlo);
+  DeviceGuard g(nb->device);
+  released(cudaFree(nb->E));
+  released(cudaFree(nb->thi));
+  released(cudaFree(nb->tlo));
   delete nb;
 }
 
@@ -1269,6 +1293,7 @@ int zinc_nbasis_create(zn_ctx* c, uint32_t K, uint64_t seed, zn_nbasis** out) {
   zn_nbasis* nb = new (std::nothrow) zn_nbasis();
   if (!nb) return ZN_ENOMEM;
   nb->ctx = c;
+  nb->device = c->device;
   nb->K = K;
   const size_t n = c->n, rw = ring_words(c), nhi = n / 32;
   // power tables on the host: psi^(64 h), h < 2N/64, and psi^l 2^64 (the
@@ -1438,13 +1463,13 @@ struct zn_batch {
 void zn_batch_destroy(zn_batch* b) {
   if (!b) return;
   DeviceGuard g(b->device);
-  if (b->exec) cudaGraphExecDestroy(b->exec);
-  cudaFree(b->d_jobs);
-  cudaFree(b->d_units);
-  cudaFree(b->d_packets);
-  cudaFree(b->d_counters);
-  cudaFree(b->d_me);
-  cudaFree(b->d_small);
+  if (b->exec) released(cudaGraphExecDestroy(b->exec));
+  released(cudaFree(b->d_jobs));
+  released(cudaFree(b->d_units));
+  released(cudaFree(b->d_packets));
+  released(cudaFree(b->d_counters));
+  released(cudaFree(b->d_me));
+  released(cudaFree(b->d_small));
   delete b;
 }
 
@@ -1598,14 +1623,31 @@ int zn_batch_info(const zn_batch* b, uint32_t* prep_units, uint32_t* packets) {
 
 // ------------------------------------------------------ host-buffer pipeline
 
-int zn_encrypt_host(zn_ctx* c, const zn_pk* pk, const zn_zcache* zc, const double* host_slots, uint32_t n_slots,
-                    uint32_t batch, uint64_t seed, const uint64_t* host_ct_index, uint64_t* host_ct,
-                    uint32_t chunk) {
-  NvtxRange nvtx("zn_encrypt_host");
+namespace {
+
+// Packing layout of a context's ciphertexts (see zn_pack.cu).
+zn::PackArgs pack_args(const zn_ctx* c) {
+  zn::PackArgs A;
+  std::memset(&A, 0, sizeof(A));
+  u64 off = 0;
+  for (uint32_t i = 0; i < c->L; ++i) {
+    A.bits[i] = 64u - (unsigned)__builtin_clzll(c->q[i]);
+    A.woff[i] = off;
+    off += ((u64)c->n * A.bits[i] + 63) / 64;
+  }
+  A.cwords = off;
+  return A;
+}
+
+// The host-buffer encryption; packed: each chunk is packed on the device and
+// only the packed words cross the host link.
+int encrypt_host_impl(zn_ctx* c, const zn_pk* pk, const zn_zcache* zc, const double* host_slots, uint32_t n_slots,
+                      uint32_t batch, uint64_t seed, const uint64_t* host_ct_index, uint64_t* host_out,
+                      uint32_t chunk, bool packed) {
   if (!c || (pk && zc) || (!pk && !zc) || (pk && !pk_of(pk, c)) || (zc && !zc_of(zc, c)) || n_slots > c->n / 2)
     return ZN_EINVAL;
   if (batch == 0) return ZN_OK;
-  if (!host_ct || !host_ct_index || (n_slots && !host_slots)) return ZN_EINVAL;
+  if (!host_out || !host_ct_index || (n_slots && !host_slots)) return ZN_EINVAL;
   if (chunk == 0) chunk = 256;
   if (chunk > batch) chunk = batch;
   DeviceGuard g(c->device);
@@ -1622,13 +1664,16 @@ int zn_encrypt_host(zn_ctx* c, const zn_pk* pk, const zn_zcache* zc, const doubl
   // no per-chunk pool allocation can make one stream wait for another's frees
   const uint32_t ech = chunk < encode_chunk(c) ? chunk : encode_chunk(c);
   const size_t en_b = (encrypt_scratch_bytes(c, ech) + 255) / 256 * 256;
+  zn::PackArgs pa = pack_args(c);
+  const size_t out_words = packed ? 2 * pa.cwords : 2 * ring_words(c);   // per ciphertext
+  const size_t pk_b = packed ? sizeof(u64) * out_words * chunk : 0;
   const bool zinc = zc != nullptr;
   int rc = ZN_OK;
   {
     Scratch st0(c, c->hs[0]), st1(c, c->hs[1]), st2(c, c->hs[2]);
     Scratch* stage[3] = {&st0, &st1, &st2};
     for (int k = 0; k < 3 && !rc; ++k)
-      if (!stage[k]->alloc(ct_b + sl_b + ix_b + en_b)) rc = ZN_ENOMEM;
+      if (!stage[k]->alloc(ct_b + sl_b + ix_b + en_b + pk_b)) rc = ZN_ENOMEM;
     for (uint32_t b0 = 0, k = 0; b0 < batch && !rc; b0 += chunk, k = (k + 1) % 3) {
       const uint32_t nb = (batch - b0) < chunk ? (batch - b0) : chunk;
       cudaStream_t st = c->hs[k];
@@ -1638,6 +1683,7 @@ int zn_encrypt_host(zn_ctx* c, const zn_pk* pk, const zn_zcache* zc, const doubl
       u64* d_ix = (u64*)(base + ct_b + sl_b);
       i64* d_me = (i64*)(base + ct_b + sl_b + ix_b);
       int8_t* d_small = (int8_t*)d_me + sizeof(i64) * ech * (size_t)c->n;
+      u64* d_out = packed ? (u64*)(base + ct_b + sl_b + ix_b + en_b) : d_ct;
       if ((n_slots && cudaMemcpyAsync(d_sl, host_slots + (size_t)b0 * n_slots, sizeof(double) * n_slots * nb,
                                       cudaMemcpyHostToDevice, st) != cudaSuccess) ||
           cudaMemcpyAsync(d_ix, host_ct_index + b0, sizeof(u64) * nb, cudaMemcpyHostToDevice, st) != cudaSuccess) {
@@ -1647,8 +1693,13 @@ int zn_encrypt_host(zn_ctx* c, const zn_pk* pk, const zn_zcache* zc, const doubl
       rc = zinc ? encrypt_with(c, true, zc->d, nullptr, d_sl, n_slots, nb, seed, d_ix, d_ct, d_me, d_small, ech, st)
                 : encrypt_with(c, false, pk->d, pk->d + 2 * ring_words(c), d_sl, n_slots, nb, seed, d_ix, d_ct, d_me,
                                d_small, ech, st);
-      if (!rc && cudaMemcpyAsync(host_ct + (size_t)b0 * 2 * ring_words(c), d_ct,
-                                 sizeof(u64) * 2 * ring_words(c) * nb, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+      if (!rc && packed) {
+        pa.ct = d_ct;
+        pa.packed = d_out;
+        if (zn::launch_ct_pack(c->dp, pa, nb, st) != cudaSuccess) rc = ZN_ECUDA;
+      }
+      if (!rc && cudaMemcpyAsync(host_out + (size_t)b0 * out_words, d_out, sizeof(u64) * out_words * nb,
+                                 cudaMemcpyDeviceToHost, st) != cudaSuccess)
         rc = ZN_ECUDA;
     }
     // staging is returned to the pool in stream order by the Scratch destructors
@@ -1657,6 +1708,50 @@ int zn_encrypt_host(zn_ctx* c, const zn_pk* pk, const zn_zcache* zc, const doubl
     if (cudaStreamSynchronize(h) != cudaSuccess) rc = rc ? rc : ZN_ECUDA;
   cudaGetLastError();
   return rc;
+}
+
+}  // namespace
+
+int zn_encrypt_host(zn_ctx* c, const zn_pk* pk, const zn_zcache* zc, const double* host_slots, uint32_t n_slots,
+                    uint32_t batch, uint64_t seed, const uint64_t* host_ct_index, uint64_t* host_ct,
+                    uint32_t chunk) {
+  NvtxRange nvtx("zn_encrypt_host");
+  return encrypt_host_impl(c, pk, zc, host_slots, n_slots, batch, seed, host_ct_index, host_ct, chunk, false);
+}
+
+int zn_encrypt_host_packed(zn_ctx* c, const zn_pk* pk, const zn_zcache* zc, const double* host_slots,
+                           uint32_t n_slots, uint32_t batch, uint64_t seed, const uint64_t* host_ct_index,
+                           uint64_t* host_packed, uint32_t chunk) {
+  NvtxRange nvtx("zn_encrypt_host_packed");
+  return encrypt_host_impl(c, pk, zc, host_slots, n_slots, batch, seed, host_ct_index, host_packed, chunk, true);
+}
+
+size_t zn_ct_packed_words(const zn_ctx* c) { return c ? 2 * pack_args(c).cwords : 0; }
+
+int zn_ct_pack(zn_ctx* c, const uint64_t* ct, size_t batch, uint64_t* packed, void* stream) {
+  NvtxRange nvtx("zn_ct_pack");
+  if (!c || batch > 0xffffffffu) return ZN_EINVAL;
+  if (batch == 0) return ZN_OK;
+  if (!ct || !packed) return ZN_EINVAL;
+  DeviceGuard g(c->device);
+  zn::PackArgs A = pack_args(c);
+  A.ct = const_cast<u64*>(ct);
+  A.packed = packed;
+  ZN_CUDA(zn::launch_ct_pack(c->dp, A, (uint32_t)batch, S(stream)));
+  return ZN_OK;
+}
+
+int zn_ct_unpack(zn_ctx* c, const uint64_t* packed, size_t batch, uint64_t* ct, void* stream) {
+  NvtxRange nvtx("zn_ct_unpack");
+  if (!c || batch > 0xffffffffu) return ZN_EINVAL;
+  if (batch == 0) return ZN_OK;
+  if (!ct || !packed) return ZN_EINVAL;
+  DeviceGuard g(c->device);
+  zn::PackArgs A = pack_args(c);
+  A.ct = ct;
+  A.packed = const_cast<u64*>(packed);
+  ZN_CUDA(zn::launch_ct_unpack(c->dp, A, (uint32_t)batch, S(stream)));
+  return ZN_OK;
 }
 
 // ------------------------------------------------------------- autotuning

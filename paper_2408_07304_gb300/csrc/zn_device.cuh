@@ -38,7 +38,7 @@ struct DevParams {
   unsigned* status;          // device status word (bit 0: encode overflow)
 };
 
-enum : unsigned { kStatusOverflow = 1u, kStatusTimeout = 2u };
+enum : unsigned { kStatusOverflow = 1u, kStatusTimeout = 2u, kStatusRange = 4u };
 
 // ------------------------------------------------------------ modular math
 

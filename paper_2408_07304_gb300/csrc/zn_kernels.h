@@ -200,6 +200,19 @@ cudaError_t launch_batch_encode(const BatchEnc& E, const i64* slots, uint32_t ba
 cudaError_t launch_batch_decode(const BatchEnc& E, const i64* m, uint32_t batch, u64* work, i64* slots,
                                 cudaStream_t st);
 
+// Packed ciphertext serialization (zn_pack.cu): bits[i] = bit length of q_i,
+// woff[i] = word offset of prime i's limb within a component, cwords = words
+// of one component.
+struct PackArgs {
+  u64* ct;                  // [B][2][L][N] plain residues
+  u64* packed;              // [B][2][cwords]
+  unsigned bits[kMaxL];
+  u64 woff[kMaxL];
+  u64 cwords;
+};
+cudaError_t launch_ct_pack(const DevParams& P, const PackArgs& A, uint32_t batch, cudaStream_t st);
+cudaError_t launch_ct_unpack(const DevParams& P, const PackArgs& A, uint32_t batch, cudaStream_t st);
+
 // pk0 += (t - 1) e-hat (per prime, NTT form) and its Shoup companions: Gen's key becomes BGV's.
 cudaError_t launch_bgv_key(const DevParams& P, u64 t, const u64* ehat, u64* pk, u64* pks, cudaStream_t st);
 // residues [L][N] of a signed int64 polynomial [N]

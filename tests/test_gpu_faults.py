@@ -89,3 +89,18 @@ def test_server_fails_batch_when_retries_run_out(server):
         assert torch.equal(done[0].ct, server.encrypt_one(reqs[0]))
     finally:
         server.max_alloc_retries = old
+
+
+def test_handles_released_after_their_context_leave_no_error():
+    # Python's cycle collector may release a context before its keys; each
+    # handle keeps its device, and no release leaves a CUDA error behind
+    ctx, sk, pk = _ctx()
+    zc = api.zinc_precompute(ctx, pk, 2)
+    nb = api.zinc_nbasis_create(ctx, 2, 3)
+    se = api.zn_slot_encoder_create(ctx, 65537)
+    ctx.close()
+    for h in (zc, nb, se, pk, sk):
+        h.close()
+    x = torch.arange(1 << 20, dtype=torch.float64, device="cuda:0")
+    assert float(x.sum()) == (1 << 20) * ((1 << 20) - 1) / 2
+    torch.cuda.synchronize()
