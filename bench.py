@@ -382,7 +382,7 @@ def run_ours(args, w):
                "d2h_gbs_fastest_step": 2 * host_v.numel() * 8 / min(step_s) / 1e9,
                "h2d_bytes_per_step": int(2 * (host_slots.numel() * 8 + host_idx.numel() * 8)),
                "d2h_bytes_per_step": int(2 * host_v.numel() * 8),
-               "steps": e2e_steps, "api": "zn_encrypt_host (pinned host buffers, chunks of 256 over 3 streams)"}
+               "steps": e2e_steps, "api": "zn_encrypt_host (pinned host buffers, automatic chunks (256 ciphertexts here) over 3 streams)"}
         del host_v, host_z
         # the same step with the ciphertexts packed on the device (residues at
         # their primes' bit lengths, zn_encrypt_host_packed): fewer bytes on

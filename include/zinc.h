@@ -303,9 +303,10 @@ int zinc_encrypt_ntt(zn_ctx* ctx, const zn_zcache* zc, const zn_nbasis* nb, cons
 /* Host memory in, host memory out: copies slot vectors and ct indices to the
  * device, encrypts -- vanilla (Eq. 8) under pk when zc is NULL, Zinc
  * (Algorithm 1) under zc otherwise (pass exactly one) -- and copies the
- * ciphertexts back, in chunks of `chunk` ciphertexts (0: 256) pipelined over
- * three internal streams so that the transfers of one chunk overlap the
- * kernels of the next.  host_slots [batch][n_slots] double, host_ct_index
+ * ciphertexts back, in chunks of `chunk` ciphertexts pipelined over three
+ * internal streams so that the transfers of one chunk overlap the kernels of
+ * the next (0: at most 256 ciphertexts and 512 MiB per chunk, and at most a
+ * quarter of the batch but not below 8).  host_slots [batch][n_slots] double, host_ct_index
  * [batch] uint64, host_ct [batch][2][L][N] uint64: page-locked host memory
  * gives asynchronous full-speed copies (pageable memory works, slower).
  * Results equal ckks_encrypt / zinc_encrypt.  Synchronous: returns when the

@@ -35,6 +35,8 @@ struct zn_ctx {
   cudaMemPool_t pool; // stream-ordered scratch (prep outputs)
   int variant;        // encryption launch shape (zn_autotune)
   cudaStream_t hs[3]; // internal streams of zn_encrypt_host (created on first use)
+  cudaStream_t hp;    // high-priority stream of its packing kernels, and their events
+  cudaEvent_t hev[6]; // [slot]: chunk encrypted; [3 + slot]: chunk packed
   // launch timing (benchmark instrumentation)
   bool timing;
   std::vector<cudaEvent_t> ev[ZN_TIME_KINDS];   // start/stop pairs
@@ -665,6 +667,9 @@ void zn_ctx_destroy(zn_ctx* c) {
   zn_timing_enable(c, 0);
   for (cudaStream_t& h : c->hs)
     if (h) released(cudaStreamDestroy(h));
+  if (c->hp) released(cudaStreamDestroy(c->hp));
+  for (cudaEvent_t& e : c->hev)
+    if (e) released(cudaEventDestroy(e));
   released(cudaFree(c->d_tw));
   released(cudaFree(c->d_etw));
   released(cudaFree(c->d_slot));
@@ -1639,6 +1644,26 @@ zn::PackArgs pack_args(const zn_ctx* c) {
   return A;
 }
 
+// The pack kernels assume 17 <= bits_i <= 62 (at most five residues per word).
+bool pack_ok(const zn_ctx* c) {
+  const zn::PackArgs A = pack_args(c);
+  for (uint32_t i = 0; i < c->L; ++i)
+    if (A.bits[i] < 17 || A.bits[i] > 62) return false;
+  return true;
+}
+
+// Default chunk of the host-buffer encryption: at most 256 ciphertexts and
+// 512 MiB of ciphertext, and at most a quarter of the batch (but not below
+// 8), so that the first chunk's encryption -- the one part of the call that
+// no copy overlaps -- stays short next to the link-bound copies.
+uint32_t host_chunk(const zn_ctx* c, uint32_t batch) {
+  size_t k = ((size_t)512 << 20) / (sizeof(u64) * 2 * ring_words(c));
+  if (k > 256) k = 256;
+  const size_t quarter = std::max<size_t>(8, ((size_t)batch + 3) / 4);
+  if (k > quarter) k = quarter;
+  return (uint32_t)std::max<size_t>(1, k);
+}
+
 // The host-buffer encryption; packed: each chunk is packed on the device and
 // only the packed words cross the host link.
 int encrypt_host_impl(zn_ctx* c, const zn_pk* pk, const zn_zcache* zc, const double* host_slots, uint32_t n_slots,
@@ -1647,8 +1672,8 @@ int encrypt_host_impl(zn_ctx* c, const zn_pk* pk, const zn_zcache* zc, const dou
   if (!c || (pk && zc) || (!pk && !zc) || (pk && !pk_of(pk, c)) || (zc && !zc_of(zc, c)) || n_slots > c->n / 2)
     return ZN_EINVAL;
   if (batch == 0) return ZN_OK;
-  if (!host_out || !host_ct_index || (n_slots && !host_slots)) return ZN_EINVAL;
-  if (chunk == 0) chunk = 256;
+  if (!host_out || !host_ct_index || (n_slots && !host_slots) || (packed && !pack_ok(c))) return ZN_EINVAL;
+  if (chunk == 0) chunk = host_chunk(c, batch);
   if (chunk > batch) chunk = batch;
   DeviceGuard g(c->device);
   for (cudaStream_t& h : c->hs)
@@ -1657,6 +1682,24 @@ int encrypt_host_impl(zn_ctx* c, const zn_pk* pk, const zn_zcache* zc, const dou
       h = nullptr;
       return ZN_ECUDA;
     }
+  if (packed && !c->hp) {
+    // the packing kernels run on a stream of the highest priority: a chunk's
+    // pack (and so its copy) must not wait behind the next chunk's encryption
+    // blocks, which would otherwise take every SM first
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&c->hp, cudaStreamNonBlocking, greatest) != cudaSuccess) {
+      cudaGetLastError();
+      c->hp = nullptr;
+      return ZN_ECUDA;
+    }
+    for (cudaEvent_t& e : c->hev)
+      if (!e && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        e = nullptr;
+        return ZN_ECUDA;
+      }
+  }
   const size_t ct_b = sizeof(u64) * 2 * ring_words(c) * chunk;
   const size_t sl_b = (sizeof(double) * n_slots * chunk + 255) / 256 * 256;
   const size_t ix_b = (sizeof(u64) * chunk + 255) / 256 * 256;
@@ -1696,7 +1739,12 @@ int encrypt_host_impl(zn_ctx* c, const zn_pk* pk, const zn_zcache* zc, const dou
       if (!rc && packed) {
         pa.ct = d_ct;
         pa.packed = d_out;
-        if (zn::launch_ct_pack(c->dp, pa, nb, st) != cudaSuccess) rc = ZN_ECUDA;
+        if (cudaEventRecord(c->hev[k], st) != cudaSuccess || cudaStreamWaitEvent(c->hp, c->hev[k], 0) != cudaSuccess ||
+            zn::launch_ct_pack(c->dp, pa, nb, c->hp) != cudaSuccess ||
+            cudaEventRecord(c->hev[3 + k], c->hp) != cudaSuccess || cudaStreamWaitEvent(st, c->hev[3 + k], 0) != cudaSuccess) {
+          cudaGetLastError();
+          rc = ZN_ECUDA;
+        }
       }
       if (!rc && cudaMemcpyAsync(host_out + (size_t)b0 * out_words, d_out, sizeof(u64) * out_words * nb,
                                  cudaMemcpyDeviceToHost, st) != cudaSuccess)
@@ -1706,6 +1754,7 @@ int encrypt_host_impl(zn_ctx* c, const zn_pk* pk, const zn_zcache* zc, const dou
   }
   for (cudaStream_t h : c->hs)
     if (cudaStreamSynchronize(h) != cudaSuccess) rc = rc ? rc : ZN_ECUDA;
+  if (c->hp && cudaStreamSynchronize(c->hp) != cudaSuccess) rc = rc ? rc : ZN_ECUDA;
   cudaGetLastError();
   return rc;
 }
@@ -1730,7 +1779,7 @@ size_t zn_ct_packed_words(const zn_ctx* c) { return c ? 2 * pack_args(c).cwords 
 
 int zn_ct_pack(zn_ctx* c, const uint64_t* ct, size_t batch, uint64_t* packed, void* stream) {
   NvtxRange nvtx("zn_ct_pack");
-  if (!c || batch > 0xffffffffu) return ZN_EINVAL;
+  if (!c || batch > 0xffffffffu || !pack_ok(c)) return ZN_EINVAL;
   if (batch == 0) return ZN_OK;
   if (!ct || !packed) return ZN_EINVAL;
   DeviceGuard g(c->device);
@@ -1743,7 +1792,7 @@ int zn_ct_pack(zn_ctx* c, const uint64_t* ct, size_t batch, uint64_t* packed, vo
 
 int zn_ct_unpack(zn_ctx* c, const uint64_t* packed, size_t batch, uint64_t* ct, void* stream) {
   NvtxRange nvtx("zn_ct_unpack");
-  if (!c || batch > 0xffffffffu) return ZN_EINVAL;
+  if (!c || batch > 0xffffffffu || !pack_ok(c)) return ZN_EINVAL;
   if (batch == 0) return ZN_OK;
   if (!ct || !packed) return ZN_EINVAL;
   DeviceGuard g(c->device);

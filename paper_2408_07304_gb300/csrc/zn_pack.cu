@@ -10,8 +10,10 @@
 
 namespace zn {
 
-// Output word w of limb y = (b, c, i): OR of the (at most ceil(64 / bits) + 1)
-// residues that overlap bits [64 w, 64 w + 64) of the limb's stream.
+// Output word w of limb y = (b, c, i): OR of the residues that overlap bits
+// [64 w, 64 w + 64) of the limb's stream -- at most ceil(64 / bits) + 1 <= 5
+// of them (the host admits 17 <= bits <= 62), loaded independently.  Bit
+// positions stay below N bits <= 2^15 * 62 < 2^32.
 __global__ void __launch_bounds__(256) k_ct_pack(DevParams P, PackArgs A, uint32_t b0) {
   const int L = P.L, N = 1 << P.log_n;
   const size_t y = blockIdx.y;
@@ -19,18 +21,18 @@ __global__ void __launch_bounds__(256) k_ct_pack(DevParams P, PackArgs A, uint32
   const int c = (int)(y / L) % 2, i = (int)(y % L);
   const unsigned bits = A.bits[i];
   const unsigned w = blockIdx.x * blockDim.x + threadIdx.x;
-  const unsigned words = (unsigned)(((u64)N * bits + 63) / 64);
+  const unsigned words = ((unsigned)N * bits + 63) / 64;
   if (w >= words) return;
   const u64* src = A.ct + ((b * 2 + c) * L + i) * (size_t)N;
   u64* dst = A.packed + b * 2 * A.cwords + c * A.cwords + A.woff[i];
-  const u64 bit0 = (u64)w * 64;
-  u64 out = 0;
-  for (unsigned j = (unsigned)(bit0 / bits); j < (unsigned)N; ++j) {
-    const long long s = (long long)j * bits - (long long)bit0;   // residue j's first bit, relative to the word
-    if (s >= 64) break;
-    const u64 r = __ldg(src + j);
-    out |= s >= 0 ? r << s : r >> -s;
-  }
+  const unsigned bit0 = w * 64u;
+  const unsigned j0 = bit0 / bits;
+  const unsigned sh = bit0 - j0 * bits;                 // residue j0 starts sh bits before the word
+  u64 out = __ldg(src + j0) >> sh;
+  unsigned s = j0 * bits + bits - bit0;                 // position of residue j0 + 1 in the word
+#pragma unroll
+  for (unsigned k = 1; k < 5; ++k, s += bits)
+    if (s < 64 && j0 + k < (unsigned)N) out |= __ldg(src + j0 + k) << s;
   dst[w] = out;
 }
 
@@ -45,11 +47,10 @@ __global__ void __launch_bounds__(256) k_ct_unpack(DevParams P, PackArgs A, uint
   if (j >= (unsigned)N) return;
   const unsigned bits = A.bits[i];
   const u64* src = A.packed + b * 2 * A.cwords + c * A.cwords + A.woff[i];
-  const u64 bit = (u64)j * bits;
-  const unsigned w = (unsigned)(bit >> 6), s = (unsigned)(bit & 63);
+  const unsigned bit = j * bits, w = bit >> 6, s = bit & 63;
   u64 v = __ldg(src + w) >> s;
   if (s + bits > 64) v |= __ldg(src + w + 1) << (64 - s);
-  if (bits < 64) v &= (1ull << bits) - 1;
+  v &= (1ull << bits) - 1;                              // bits <= 62
   if (v >= P.q[i]) atomicOr(P.status, kStatusRange);
   A.ct[((b * 2 + c) * L + i) * (size_t)N + j] = v;
 }
