@@ -82,17 +82,22 @@ def test_throughput_chain_packed_size_and_sampled_limbs():
 def test_encrypt_host_packed_equals_packed_device_ciphertexts():
     ctx, pk = _ctx(12, (36, 36, 37), 30)
     zc = api.zinc_precompute(ctx, pk, 2)
-    B = 600                                           # three chunks of 256, the last one ragged
+    B = 600
     rng = np.random.default_rng(7)
     hz = torch.tensor(rng.uniform(-1, 1, (B, 100))).pin_memory()
     hidx = torch.tensor(rng.integers(0, 2 ** 40, B), dtype=torch.int64).pin_memory()
-    for key in (pk, zc):
+    # chunk 256: 256 + 256 + 88 (a ragged last chunk); 0: the default, a
+    # quarter of the batch here (four chunks of 150); 7: many chunks, ragged
+    for key, chunk in ((pk, 256), (zc, 256), (pk, 0), (zc, 7)):
         out = torch.empty((B, api.zn_ct_packed_words(ctx)), dtype=torch.int64, pin_memory=True)
-        api.zn_encrypt_host_packed(ctx, key, hz, 9, hidx, out)
+        api.zn_encrypt_host_packed(ctx, key, hz, 9, hidx, out, chunk=chunk)
         fn = api.zinc_encrypt if key is zc else api.ckks_encrypt
         dev_ct = fn(ctx, key, hz.cuda(), 9, hidx.cuda())
-        assert torch.equal(out, api.zn_ct_pack(ctx, dev_ct).cpu())
+        assert torch.equal(out, api.zn_ct_pack(ctx, dev_ct).cpu()), chunk
         assert torch.equal(api.zn_ct_unpack(ctx, out.cuda()), dev_ct)
+        plain = torch.empty((B, 2, ctx.L, ctx.n), dtype=torch.int64, pin_memory=True)
+        api.zn_encrypt_host(ctx, key, hz, 9, hidx, plain, chunk=chunk)
+        assert torch.equal(plain, dev_ct.cpu()), chunk
 
 
 def test_unpack_latches_out_of_range_field():
