@@ -363,8 +363,10 @@ def run_ours(args, w):
         # their primes' bit lengths, zn_encrypt_host_packed): fewer bytes on
         # the link, every value kept
         pw = api.zn_ct_packed_words(ctx)
-        host_pv = torch.empty((B, pw), dtype=torch.int64, pin_memory=True)
-        host_pz = torch.empty((B, pw), dtype=torch.int64, pin_memory=True)
+        # the packed outputs reuse the front of the plain buffers (no second
+        # set of page-locked gigabytes)
+        host_pv = host_v.view(-1)[: B * pw].view(B, pw)
+        host_pz = host_z.view(-1)[: B * pw].view(B, pw)
         api.zn_encrypt_host_packed(ctx, pk, host_slots, w.seed, host_idx, host_pv)
         api.zn_encrypt_host_packed(ctx, zc, host_slots, w.seed, host_idx, host_pz)
         torch.cuda.synchronize(dev)
