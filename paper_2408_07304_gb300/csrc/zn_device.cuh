@@ -88,6 +88,20 @@ __device__ __forceinline__ u64 mul_tern(int v, u64 w, u64 q) {
   return v == 0 ? 0ull : v > 0 ? w : q - w;
 }
 
+// v w mod q in [0, 2q) for a small signed v (|v| < 2^31) and w with Shoup
+// companion ws: Shoup's quotient floor(|v| ws / 2^64) and the low word of
+// |v| w built from 32 x 64-bit products instead of 64 x 64-bit ones (the same
+// quotient as mul_shoup, so |v| w - quotient q lies in [0, 2q)); a negative v
+// takes 2q minus that (nonzero: the prime q divides neither |v| nor w).
+__device__ __forceinline__ u64 mul_small(int v, u64 w, u64 ws, u64 q) {
+  const unsigned a = (unsigned)(v < 0 ? -v : v);
+  const u64 lo = (u64)(unsigned)ws * a;
+  const unsigned qh = (unsigned)(((u64)(unsigned)(ws >> 32) * a + (lo >> 32)) >> 32);
+  const u64 aw = (u64)(unsigned)w * a + (((u64)(unsigned)(w >> 32) * a) << 32);
+  const u64 r = aw - ((u64)(unsigned)q * qh + (((u64)(unsigned)(q >> 32) * qh) << 32));
+  return v < 0 ? 2 * q - r : r;
+}
+
 // general a*b mod q (slow path: keygen and imports only)
 __device__ __forceinline__ u64 mulmod_slow(u64 a, u64 b, u64 q) {
   return (u64)(((u128)a * b) % q);
@@ -497,7 +511,8 @@ __device__ __forceinline__ void gen_i64_half(u64* sm, int t, int nt, int h, cons
                                        reduce_biased((u64)__ldg(a + k + HALF), q, mu, moff), h, w1, w1s, q);
 }
 
-// TERN: ternary polynomial, first-stage products by selection (below 2q).
+// Small inputs: the first stage's product is a small one (below 3q); TERN:
+// ternary polynomial, the product a selection (below 2q).
 template <int LOGH, int KM = 4, bool TERN = false>
 __device__ __forceinline__ void gen_i8_half(u64* sm, int t, int nt, int h, const int8_t* __restrict__ a, u64 q, u64 w1,
                                             u64 w1s) {
@@ -509,8 +524,10 @@ __device__ __forceinline__ void gen_i8_half(u64* sm, int t, int nt, int h, const
     }
     return;
   }
-  for (int k = t; k < HALF; k += nt)
-    sm[swz<LOGH, KM>(k)] = first_stage(small_res(__ldg(a + k), q), small_res(__ldg(a + k + HALF), q), h, w1, w1s, q);
+  for (int k = t; k < HALF; k += nt) {
+    const int b = __ldg(a + k + HALF);
+    sm[swz<LOGH, KM>(k)] = small_res(__ldg(a + k), q) + mul_small(h ? -b : b, w1, w1s, q);   // [0, 3q)
+  }
 }
 
 // Half generators that also run the half transform's top stage (slots k and
