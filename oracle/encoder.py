@@ -303,18 +303,60 @@ def encode(z, log_n: int, log2_delta: int):
     return np.array(m, dtype=np.int64)
 
 
-def encode_direct(z, log_n: int, log2_delta: int):
+def _cos_table(log_n: int):
+    """cos(pi x / N) for x < 2N, correctly rounded: the table ``twiddles`` gives
+    x < N, and cos(pi + t) = -cos(t) gives the rest exactly (a sign flip)."""
+    re, _ = twiddles(log_n)
+    return np.concatenate([re, -re])
+
+
+def encode_direct(z, log_n: int, log2_delta: int, chunk: int = 256):
     """The defining sum (2 Delta / N) Re sum_j z_j zeta^(-5^j k), k < N, in FP64
-    term by term with exactly reduced angles (pin only; O(N^2))."""
+    (pin only; O(N^2)).  Term j of output k is z_j cos(pi x / N) with the
+    exponent x = 5^j k mod 2N reduced exactly and the cosine taken from the
+    correctly rounded table (one rounding), the product rounded once; the terms
+    of each output are added pairwise (zero-padded to a power of two, halves
+    added level by level), so the result is within
+    ``encode_direct_error_bound`` of the exact sum."""
     n = 1 << log_n
     z = np.asarray(z, dtype=np.float64)
-    g = np.array([pow(5, j, 2 * n) for j in range(z.shape[0])], dtype=np.int64)
-    k = np.arange(n, dtype=np.int64)
-    out = np.zeros(n)
-    for j in range(z.shape[0]):
-        e = (g[j] * k) % (2 * n)                      # exponent of zeta^(+5^j k), exact
-        out += z[j] * np.cos(np.pi * e / n)           # Re zeta^(-x) = cos(pi x / N)
-    return out * (2.0 * 2.0 ** log2_delta / n)
+    ns = z.shape[0]
+    if ns == 0:
+        return np.zeros(n)
+    width = 1 << max(0, (ns - 1).bit_length())
+    zp = np.zeros(width)
+    zp[:ns] = z
+    g = np.zeros(width, dtype=np.int64)
+    g[:ns] = [pow(5, j, 2 * n) for j in range(ns)]
+    cos_t = _cos_table(log_n)
+    out = np.empty(n)
+    for k0 in range(0, n, chunk):
+        k = np.arange(k0, min(k0 + chunk, n), dtype=np.int64)
+        t = cos_t[(k[:, None] * g[None, :]) % (2 * n)] * zp[None, :]
+        while t.shape[1] > 1:                       # pairwise: one rounding per level
+            h = t.shape[1] // 2
+            t = t[:, :h] + t[:, h:]
+        out[k0:k0 + k.shape[0]] = t[:, 0]
+    return out * (2.0 * 2.0 ** log2_delta / n)       # a power of two: exact
+
+
+def encode_direct_error_bound(z, log_n: int, log2_delta: int):
+    """|encode_direct - exact| (coefficient units), by standard floating-point
+    error analysis with unit roundoff u = 2^-53 and gamma_k = k u / (1 - k u):
+    a term is z_j c (1 + d1)(1 + d2), |d1|, |d2| <= u (table entry, product),
+    so it is off by at most gamma_2 |z_j|; pairwise summation over 2^L terms
+    adds at most gamma_L times the sum of the terms' moduli; together
+    gamma_(L+2) sum_j |z_j|, plus half the smallest subnormal per product
+    (gradual underflow), times the exact scale 2 Delta / N."""
+    z = np.asarray(z, dtype=np.float64)
+    ns = z.shape[0]
+    if ns == 0:
+        return 0.0
+    L = max(0, (ns - 1).bit_length())
+    u = 2.0 ** -53
+    k = L + 2
+    gamma = k * u / (1.0 - k * u)
+    return (gamma * math.fsum(abs(float(v)) for v in z) + ns * 2.0 ** -1075) * 2.0 ** (log2_delta + 1 - log_n)
 
 
 def decode(m, log_n: int, log2_delta: int, n_slots: int):

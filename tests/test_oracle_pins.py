@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 
 from oracle import ckks, encoder, numtheory, philox, ring, sampler
+from paper_2408_07304_gb300 import workloads
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -407,13 +408,53 @@ def test_encode_single_slot_closed_form(j):
 
 @pytest.mark.parametrize("log_n,ld,n_slots", [(10, 30, 512), (12, 30, 2048), (12, 40, 700), (4, 20, 8)])
 def test_encode_fft_vs_definition(log_n, ld, n_slots):
-    # against the FP64 direct sum; its own error is at most (n_s + 2) ulp-sized
-    # terms of the sum of |z| times the scale
+    # against the FP64 direct sum, within both error bounds
     z = np.random.default_rng(log_n + n_slots).uniform(-1, 1, n_slots)
     real = encoder.encode_real(z, log_n, ld)
     direct = encoder.encode_direct(z, log_n, ld)
-    direct_err = (n_slots + 2) * 2.0 ** -52 * np.sum(np.abs(z)) * 2.0 ** (ld + 1 - log_n)
+    direct_err = encoder.encode_direct_error_bound(z, log_n, ld)
     assert np.max(np.abs(real - direct)) <= encoder.encode_error_bound(z, log_n, ld) + direct_err
+
+
+@pytest.mark.parametrize("name,rows", [("throughput", (0, 4095)), ("large", (0,)), ("batched", (1023,))])
+def test_encode_fixed_vs_definition_full_size(name, rows):
+    # The benchmarked rings: the fixed-point procedure's unrounded output and its
+    # integers m_k against the defining sum of the canonical embedding, on the
+    # workloads' own vectors (full slot count, their value ranges).
+    w = workloads.WORKLOADS[name]
+    for b in rows:
+        z = workloads.slots(w, batch=1, first=b)[0]
+        direct = encoder.encode_direct(z, w.log_n, w.log2_delta)
+        bound = (encoder.encode_error_bound(z, w.log_n, w.log2_delta)
+                 + encoder.encode_direct_error_bound(z, w.log_n, w.log2_delta))
+        real = encoder.encode_real(z, w.log_n, w.log2_delta)
+        assert np.max(np.abs(real - direct)) <= bound
+        m = encoder.encode(z, w.log_n, w.log2_delta)
+        assert np.max(np.abs(m - direct)) <= 0.5 + bound
+        # Parseval: m evaluated at the N odd 2N-th roots gives Delta z_j at each
+        # slot root and at its conjugate, so sum_k m_k^2 = 2 Delta^2 sum_j z_j^2 / N
+        # exactly for the defining sum (fixes its scale and that no slot is lost)
+        ratio = math.fsum(direct ** 2) / (2.0 ** (2 * w.log2_delta + 1) * math.fsum(z ** 2) / w.n)
+        assert abs(ratio - 1.0) < 1e-9
+
+
+def test_encode_direct_error_bound_holds():
+    # The direct sum's own bound against an exact evaluation with Python
+    # fractions of the same table cosines, so that the products and the
+    # pairwise additions are the roundings measured (the table's own rounding,
+    # also in the bound, is pinned against mpmath elsewhere).
+    from fractions import Fraction
+    log_n, ld = 7, 30
+    n = 1 << log_n
+    z = np.random.default_rng(77).uniform(-3, 3, n // 2)
+    direct = encoder.encode_direct(z, log_n, ld)
+    cos_t = encoder._cos_table(log_n)
+    g = [pow(5, j, 2 * n) for j in range(n // 2)]
+    bound = encoder.encode_direct_error_bound(z, log_n, ld)
+    scale = Fraction(2) ** (ld + 1 - log_n)
+    for k in range(0, n, 5):
+        exact = sum(Fraction(float(z[j])) * Fraction(float(cos_t[g[j] * k % (2 * n)])) for j in range(n // 2))
+        assert abs(Fraction(float(direct[k])) - exact * scale) <= Fraction(bound)
 
 
 def test_encode_linear_and_decode_roundtrip():
