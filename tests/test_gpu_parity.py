@@ -7,9 +7,11 @@ noise tolerance derived from the arithmetic:
     tol(N, Delta) = (10 * N * sigma + N) / Delta,
 ten standard deviations of the worst (Zinc) slot error N*sigma*sqrt(2/3*1.5)/Delta
 plus the deterministic rounding term N/2/Delta, twice over.
-Small rings are compared in full; the full-size workloads (in the launch
-configuration the benchmark times) on sampled outputs the oracle computes one
-by one.
+Small rings are compared in full.  The full-size workloads run in the launch
+configuration the benchmark times (the whole batch in one call); whole
+ciphertexts of them (the first and last of the call, both sides of a chunk
+boundary) are compared in full, others on sampled outputs the oracle computes
+one by one.
 """
 import functools
 
@@ -254,9 +256,30 @@ def _check_sampled(w, ct, zinc, z, idx, rows, seed):
         assert np.array_equal(np.array([got[b, p, i, k] for p, i, k in pos], dtype=np.uint64), ref), (b, zinc)
 
 
+def _check_whole(w, ct, zinc, z, idx, rows, seed):
+    """Every residue of the given rows (all 2 L N of them) against the oracle's
+    definitional transform of its coefficient-domain ciphertext."""
+    P, K, zero = oracle_model(w.log_n, w.bits, w.log2_delta, workloads.KEYGEN_SEED, workloads.CACHE_SEED)
+    got = api.as_u64(ct)
+    for b in rows:
+        if zinc:
+            ref = O.ct_ntt(P, O.zinc_encrypt_coeff(P, zero, z[b], seed, int(idx[b])))
+        else:
+            ref = O.ct_ntt(P, O.encrypt_coeff(P, K, z[b], seed, int(idx[b])))
+        assert np.array_equal(got[b], ref), (b, zinc)
+
+
+# rows compared in full: the first and last ciphertext of the call, and at
+# N = 2^13 and 2^14 both sides of the first 256-ciphertext chunk boundary
+WHOLE_ROWS = {"batched": {False: (0, 255, 256, 1023), True: (0, 255, 256, 1023)},
+              "throughput": {False: (0, 255, 256, 4095), True: (0, 255, 256, 4095)},
+              "large": {False: (511,), True: (0,)}}
+
+
 @pytest.mark.parametrize("name", ["batched", "throughput", "large"])
-def test_encrypt_full_size_sampled(name):
-    """The benchmark's launch configuration: the whole batch in one call."""
+def test_encrypt_full_size(name):
+    """The benchmark's launch configuration: the whole batch in one call; whole
+    ciphertexts and sampled residues of others against the oracle."""
     w = workloads.WORKLOADS[name]
     ctx = gpu_ctx(w.log_n, w.bits, w.log2_delta)
     sk, pk = gpu_keys(w.log_n, w.bits, w.log2_delta, workloads.KEYGEN_SEED)
@@ -267,7 +290,9 @@ def test_encrypt_full_size_sampled(name):
     ct_v = api.ckks_encrypt(ctx, pk, zd, w.seed, dev(idx, torch.int64))
     ct_z = api.zinc_encrypt(ctx, zc, zd, w.seed, dev(idx, torch.int64))
     api.zn_sync_status(ctx)
-    rows = [0, w.batch - 1, w.batch // 2 + 1]
+    _check_whole(w, ct_v, False, z, idx, WHOLE_ROWS[name][False], w.seed)
+    _check_whole(w, ct_z, True, z, idx, WHOLE_ROWS[name][True], w.seed)
+    rows = [w.batch // 2 + 1, w.batch // 3, w.batch - 2]
     _check_sampled(w, ct_v, False, z, idx, rows, w.seed)
     _check_sampled(w, ct_z, True, z, idx, rows, w.seed)
     # every ciphertext decrypts within tolerance (a property that holds at any size)
