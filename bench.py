@@ -35,8 +35,8 @@ UNIT = "encryptions/s"
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one encrypt
-# launch -- 256 ciphertexts of the throughput workload -- from the ncu capture
-# summarised in profiles/k_encrypt_half_n16384_l8.md, keyed by the kernel it
+# launch -- 256 ciphertexts of the throughput workload -- from a separate ncu
+# capture of that kernel (not measured by this run), keyed by the kernel it
 # was taken on.  Valid only while that kernel is unchanged and selected.
 NCU_TRAFFIC = {
     ("throughput", "k_encrypt_half<13,vanilla,radix-8,3 blocks/SM>", 256): 56.379648e6 + 531.450368e6,
@@ -179,11 +179,32 @@ def max_over_ranks(values, world, device, dist=None):
 
 
 # ------------------------------------------------------------------ GPU arm
-def modmuls_per_ct(w, zinc):
-    """Butterfly-equivalents (Shoup multiplications) per ciphertext: (N/2) log2 N
-    per NTT, 3 NTTs and 2 key products per prime (vanilla) or 2 NTTs (Zinc)."""
-    ntt = (w.n // 2) * w.log_n
-    return w.L * (2 * ntt if zinc else 3 * ntt + 2 * w.n)
+def butterflies_per_ct(w, zinc):
+    """Algorithmic butterflies per ciphertext: (N/2) log2 N per NTT, 3 NTTs per
+    prime (vanilla: m + e0, u, e1) or 2 (Zinc: m + e1', e2')."""
+    return w.L * (2 if zinc else 3) * (w.n // 2) * w.log_n
+
+
+def key_products_per_ct(w, zinc):
+    """Pointwise key products per ciphertext: pk0 u and pk1 u per prime (vanilla)."""
+    return 0 if zinc else 2 * w.L * w.n
+
+
+def decode_error(api, ctx, sk, ct, slots, chunk=256):
+    """Measured decrypt-decode error of a batch of ciphertexts against the
+    slot vectors they encrypt: max and RMS over every slot (absolute), and the
+    max relative to max |z|."""
+    import torch
+    B, ns = slots.shape
+    mx, ss = 0.0, 0.0
+    for b0 in range(0, B, chunk):
+        back = api.ckks_decrypt_decode(ctx, sk, ct[b0:b0 + chunk].contiguous(), ns)
+        d = (back - slots[b0:b0 + chunk]).abs()
+        mx = max(mx, float(d.max()))
+        ss += float((d * d).sum())
+    zmax = float(slots.abs().max())
+    return {"max": mx, "rms": (ss / (B * ns)) ** 0.5, "max_rel": mx / zmax if zmax else None,
+            "ciphertexts": B, "slots_per_ct": ns}
 
 
 def run_ours(args, w):
@@ -263,13 +284,24 @@ def run_ours(args, w):
     van_rate = B * world * args.steps / (van_ms / 1e3)
     zin_rate = B * world * args.steps / (zin_ms / 1e3)
 
-    # ---- roofline of the dominant kernel (the vanilla encrypt kernel)
-    # The path is bound by 64-bit modular arithmetic on the integer pipes, not
-    # by HBM: report the kernel against (a) a peak derived from unit counts
-    # and clocks -- 152 SMs x 64 32-bit IMAD/clk x 2.07 GHz, at 10 IMAD per
-    # Harvey/Shoup butterfly (a 64x64 high product = 4, two 64-bit low
-    # products = 3 each) -- and (b) the probe-measured ceiling of the same
-    # butterfly running from registers; the HBM fraction is reported beside.
+    # ---- measured decryption accuracy of every ciphertext of the last step,
+    # per mode (Theorem 1: Zinc adds e1' + e2' s to the cached zero's noise)
+    sig = 3.2
+    accuracy = {"vanilla": decode_error(api, ctx, sk, out_v, slots),
+                "zinc": decode_error(api, ctx, sk, out_z, slots),
+                "bound": (10 * w.n * sig + w.n) / 2.0 ** w.log2_delta * max(abs(w.lo), abs(w.hi)),
+                "bound_formula": "(10 N sigma + N) / Delta x max|z|"}
+    accuracy["zinc_over_vanilla_rms"] = accuracy["zinc"]["rms"] / accuracy["vanilla"]["rms"]
+
+    # ---- roofline of the dominant kernel (the vanilla encrypt kernel): its
+    # algorithmic HBM bytes (ciphertexts written + slots read, per ciphertext)
+    # over its event-timed launch duration against the measured copy peak.
+    # The kernel is bound by 64-bit modular arithmetic on the integer pipes,
+    # so it is also reported against (a) the probe-measured ceiling of the
+    # same butterfly running from registers and (b) a peak derived from unit
+    # counts and clocks -- SMs x 64 32-bit IMAD/clk x 2.07 GHz at 10 IMAD per
+    # Harvey/Shoup butterfly (an assumption: a 64 x 64 high product = 4, two
+    # 64-bit low products = 3 each).
     hbm_peak, peak_src = peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     derived_peak = sms * 64 * 2.07e9 / 10 / 1e9          # Gbutterfly/s
@@ -284,26 +316,43 @@ def run_ours(args, w):
     chunk_cts = B * args.steps / max(kv_n, 1)
     kv_avg = kv_ms / max(kv_n, 1)
     kz_avg = kz_ms / max(kz_n, 1)
-    bfly_v = chunk_cts * modmuls_per_ct(w, False)
-    bfly_z = chunk_cts * modmuls_per_ct(w, True)
+    bfly_v = chunk_cts * butterflies_per_ct(w, False)
+    bfly_z = chunk_cts * butterflies_per_ct(w, True)
+    kprod_v = chunk_cts * key_products_per_ct(w, False)
+    alg_bytes = chunk_cts * per_ct_bytes
+    hbm_achieved = alg_bytes / (kv_avg / 1e3) / 1e9
+    hbm_achieved_z = alg_bytes / (kz_avg / 1e3) / 1e9
     achieved = bfly_v / (kv_avg / 1e3) / 1e9
-    hbm_achieved = chunk_cts * ct_bytes / (kv_avg / 1e3) / 1e9
     kname = VARIANT_KERNEL.get(tune[0], "k_encrypt<{mode}> variant %d" % tune[0]) if w.log_n == 14 else \
         f"k_encrypt<{w.log_n},{{mode}}> variant {tune[0]}"
     traffic = NCU_TRAFFIC.get((w.name, kname.format(mode="vanilla"), int(round(chunk_cts))))
     int_pipe = NCU_INT_PIPE.get((w.name, kname.format(mode="vanilla"), int(round(chunk_cts))))
-    roofline = {"bound": "alu", "achieved": achieved, "peak": derived_peak, "unit": "Gbutterfly/s",
-                "frac": achieved / derived_peak, "traffic": traffic,
-                "traffic_unit": "DRAM bytes per launch (ncu)", "algorithmic_bytes": chunk_cts * ct_bytes,
+    roofline = {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": hbm_achieved / hbm_peak, "traffic": traffic,
+                "traffic_source": "ncu capture of this kernel at this launch size, taken separately "
+                                  "(not by this run); null when the selected kernel or size has none",
+                "algorithmic_bytes_per_launch": alg_bytes, "ciphertexts_per_launch": chunk_cts,
+                "algorithmic_bytes_per_ct": per_ct_bytes,
                 "kernel": kname.format(mode="vanilla") + f" (variant {tune[0]})",
-                "peak_source": "derived: SMs x 64 IMAD/clk x 2.07 GHz / 10 IMAD per butterfly",
-                "probe_peak": probe, "probe_frac": achieved / probe,
-                "probe_harvey": probe_h, "probe_relaxed": probe_r, "relaxed_prime_share": f_rel,
-                "zinc_kernel_achieved": bfly_z / (kz_avg / 1e3) / 1e9,
-                "int_pipe": {"pipe": "fmaheavy (32-bit integer multiply-add)", "busy_frac": int_pipe,
-                             "source": "ncu sm__pipe_fmaheavy_cycles_active, 256-ciphertext launch"},
-                "hbm": {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
-                        "frac": hbm_achieved / hbm_peak, "peak_source": peak_src}}
+                "peak_source": f"{peak_src} HBM copy rate (hbm_gbs)",
+                "zinc_kernel": {"achieved": hbm_achieved_z, "frac": hbm_achieved_z / hbm_peak,
+                                "ms_per_launch": kz_avg},
+                "alu": {"note": "the kernel's binding unit: 64-bit modular products on the integer pipes",
+                        "unit": "Gbutterfly/s", "butterflies_per_ct": butterflies_per_ct(w, False),
+                        "key_products_per_ct": key_products_per_ct(w, False),
+                        "achieved": achieved, "achieved_with_key_products": (bfly_v + kprod_v) / (kv_avg / 1e3) / 1e9,
+                        "probe_peak": probe, "probe_frac": achieved / probe,
+                        "probe_frac_with_key_products": (bfly_v + kprod_v) / (kv_avg / 1e3) / 1e9 / probe,
+                        "probe_source": "measured: the same butterfly from registers on every SM "
+                                        "(zn_probe_butterfly / _relaxed, weighted by the chain's prime mix)",
+                        "probe_harvey": probe_h, "probe_relaxed": probe_r, "relaxed_prime_share": f_rel,
+                        "derived_peak": derived_peak, "derived_frac": achieved / derived_peak,
+                        "derived_source": "assumption: SMs x 64 IMAD/clk x 2.07 GHz / 10 IMAD per butterfly",
+                        "zinc_kernel_achieved": bfly_z / (kz_avg / 1e3) / 1e9,
+                        "zinc_kernel_probe_frac": bfly_z / (kz_avg / 1e3) / 1e9 / probe,
+                        "int_pipe": {"pipe": "fmaheavy (32-bit integer multiply-add)", "busy_frac": int_pipe,
+                                     "source": "ncu sm__pipe_fmaheavy_cycles_active of the same capture as "
+                                               "traffic (not this run)"}}}
 
     # ---- the same step through the mixed-ring persistent path (one CUDA-graph
     # launch per step: a vanilla job and a Zinc job over the batch)
@@ -390,10 +439,11 @@ def run_ours(args, w):
         p_step_s = max_over_ranks(p_step_s, world, dev, dist)
         link_after = link_probe()
         link_gbs = max(link_before, link_after)
-        e2e_s = statistics.median(step_s)
+        e2e_s = sum(step_s) / len(step_s)
         link_bound = link_gbs * 1e9 / (2 * w.L * w.n * 8)
-        e2e = {"value": 2 * B * world / e2e_s, "unit": UNIT, "statistic": f"median of {e2e_steps} timed steps",
-               "step_s": step_s, "mean_enc_s": 2 * B * world * e2e_steps / sum(step_s),
+        e2e = {"value": 2 * B * world * e2e_steps / sum(step_s), "unit": UNIT,
+               "statistic": f"all ciphertexts of {e2e_steps} timed steps / their total time",
+               "step_s": step_s, "median_enc_s": 2 * B * world / statistics.median(step_s),
                "d2h_link_gbs": link_gbs, "d2h_link_gbs_before_after": [link_before, link_after],
                "link_bound_enc_s": link_bound * world,
                "of_link_bound": 2 * B / e2e_s / link_bound,
@@ -401,8 +451,10 @@ def run_ours(args, w):
                "h2d_bytes_per_step": int(2 * (host_slots.numel() * 8 + host_idx.numel() * 8)),
                "d2h_bytes_per_step": int(2 * host_v.numel() * 8),
                "steps": e2e_steps, "api": "zn_encrypt_host (pinned host buffers, automatic chunks (256 ciphertexts here) over 3 streams)",
-               "packed": {"value": 2 * B * world / statistics.median(p_step_s), "unit": UNIT,
-                          "statistic": f"median of {e2e_steps} timed steps, alternating with the plain ones",
+               "packed": {"value": 2 * B * world * e2e_steps / sum(p_step_s), "unit": UNIT,
+                          "statistic": f"all ciphertexts of {e2e_steps} timed steps / their total time, "
+                                       "alternating with the plain ones",
+                          "median_enc_s": 2 * B * world / statistics.median(p_step_s),
                           "step_s": p_step_s,
                           "d2h_bytes_per_step": int(2 * host_pv.numel() * 8),
                           "packed_over_plain_bytes": pw / (2 * w.L * w.n),
@@ -446,13 +498,18 @@ def run_ours(args, w):
         ms_ms, mz_ms = max_over_ranks([ms_ms, mz_ms], world, dev, dist)
         ms_rate = B * world * args.steps / (ms_ms / 1e3)
         mz_rate = B * world * args.steps / (mz_ms / 1e3)
+        sk_d = api.zn_sk_import(dctx, api.zn_sk_export(sk))
+        seal_acc = {"vanilla_ms": decode_error(api, dctx, sk_d, out_m, slots),
+                    "zinc_data_level": decode_error(api, dctx, sk_d, out_mz, slots)}
+        seal_acc["zinc_over_vanilla_rms"] = seal_acc["zinc_data_level"]["rms"] / seal_acc["vanilla_ms"]["rms"]
         seal = {"vanilla_ms_enc_s": ms_rate, "zinc_data_level_enc_s": mz_rate, "zinc_speedup": mz_rate / ms_rate,
+                "decode_err": seal_acc,
                 "data_primes": w.L - 1, "special_prime_bits": w.bits[-1],
                 "kernel_ms_per_launch": {"prep": kp_ms / max(kp_n, 1), "special": ks_ms / max(ks_n, 1),
                                          "data": kd_ms / max(kd_n, 1)},
                 "launches_per_step": (kp_n + ks_n + kd_n) / args.steps,
                 "paper_speedup_context": "Table 2 totals, CKKS over Zinc: 2.34x, 2.51x, 2.44x (SEAL, one EPYC 7302P thread, N=32768)"}
-        del out_m, out_mz, zc_d, dctx
+        del out_m, out_mz, zc_d, sk_d, dctx
 
     # ---- BFV (Eq. 12) and BGV (Eq. 13), vanilla and Zinc, on the same ring
     # and chain: coefficient plaintexts uniform in [0, t), t = 65537
@@ -549,7 +606,8 @@ def run_ours(args, w):
                        "l2": "working set above L2: slots 256 MiB read and 16 GiB of ciphertexts written per step"
                              if w.name == "throughput" else "see workload"},
             "vanilla_enc_s": van_rate, "zinc_enc_s": zin_rate, "zinc_speedup": zin_rate / van_rate,
-            "hbm_roofline_frac": value * per_ct_bytes / (hbm_peak * 1e9),
+            "decode_err": accuracy,
+            "hbm_frac_whole_step": value * per_ct_bytes / (hbm_peak * 1e9),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "serving": serving, "persistent_graph": persistent, "special_prime": seal, "bfv_bgv": intl,
             "zinc_ntt_domain": nttz,
