@@ -168,7 +168,9 @@ int zinc_encrypt(zn_ctx* ctx, const zn_zcache* zc, const double* slots, uint32_t
  *    must fit in ZN_NOALLOC_SCRATCH_BYTES; larger requests return ZN_ELIMIT
  *    without launching anything (split them into smaller calls).
  *  - The first call on a device looks up the array's device address (once
- *    per device); make that first call before any stream capture.
+ *    per device and process); make that first call before any stream
+ *    capture.  The address is kept for the life of the process, so calls
+ *    after a reset of the device (cudaDeviceReset) are not supported.
  *  - Every call on a device shares the one array: calls whose work overlaps
  *    on the GPU (different streams, or host threads) race and corrupt each
  *    other's results; serialise them.  The array keeps the last call's

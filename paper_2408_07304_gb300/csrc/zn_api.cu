@@ -1975,6 +1975,7 @@ int noalloc_scratch(int device, void** out) {
 extern "C" int zinc_encrypt_noalloc(zn_ctx* c, const zn_zcache* z, const double* slots, uint32_t n_slots,
                                     uint32_t batch, uint64_t seed, const uint64_t* ct_index, uint64_t* ct,
                                     void* stream) {
+  NvtxRange nvtx("zinc_encrypt_noalloc");
   if (!c || !zc_of(z, c) || n_slots > c->n / 2) return ZN_EINVAL;
   if (batch == 0) return ZN_OK;
   if (!ct || !ct_index || (n_slots && !slots)) return ZN_EINVAL;
@@ -2002,7 +2003,11 @@ extern "C" int zinc_encrypt_noalloc(zn_ctx* c, const zn_zcache* z, const double*
   A.me = pa.me;
   A.small = pa.small;
   A.out = ct;
-  ZN_CUDA(zn::launch_prep(c->dp, pa, true, batch, S(stream)));
+  {
+    TimedLaunch t(c, ZN_TIME_ENCODE, S(stream));
+    ZN_CUDA(zn::launch_prep(c->dp, pa, true, batch, S(stream)));
+  }
+  TimedLaunch t(c, ZN_TIME_ZINC, S(stream));
   ZN_CUDA(zn::launch_encrypt(c->dp, A, true, batch, c->variant, S(stream)));
   return ZN_OK;
 }

@@ -53,3 +53,24 @@ def test_noalloc_refuses_batches_beyond_its_array():
         api.zinc_encrypt_noalloc(ctx, zc, z, 9, idx, out)
     assert e.value.status == api.ZN_ELIMIT
     assert bool((out == 7).all())                 # nothing was launched
+
+
+def test_noalloc_takes_nothing_from_the_pool():
+    """The defining property: the call draws no scratch from the context's
+    memory pool.  With one pool allocation set to fail, the allocation-free
+    call still succeeds and the next pooled call is the one refused."""
+    ctx, zc = _setup(12, (36, 36, 36), 30)
+    batch = 4
+    w = workloads.small(12, (36, 36, 36), 30, batch, 100, seed=3)
+    z = torch.tensor(workloads.slots(w), dtype=torch.float64, device="cuda:0")
+    idx = torch.arange(batch, dtype=torch.int64, device="cuda:0")
+    out = torch.empty((batch, 2, ctx.L, ctx.n), dtype=torch.int64, device="cuda:0")
+    api.zn_inject_alloc_failures(1)
+    try:
+        api.zinc_encrypt_noalloc(ctx, zc, z, 9, idx, out)
+        with pytest.raises(api.ZincError) as e:
+            api.zinc_encrypt(ctx, zc, z, 9, idx)
+        assert e.value.status == api.ZN_ENOMEM
+    finally:
+        api.zn_inject_alloc_failures(0)
+    assert torch.equal(out, api.zinc_encrypt(ctx, zc, z, 9, idx))
