@@ -323,8 +323,12 @@ def run_ours(args, w):
     hbm_achieved = alg_bytes / (kv_avg / 1e3) / 1e9
     hbm_achieved_z = alg_bytes / (kz_avg / 1e3) / 1e9
     achieved = bfly_v / (kv_avg / 1e3) / 1e9
-    kname = VARIANT_KERNEL.get(tune[0], "k_encrypt<{mode}> variant %d" % tune[0]) if w.log_n == 14 else \
-        f"k_encrypt<{w.log_n},{{mode}}> variant {tune[0]}"
+    if w.log_n == 14:
+        kname = VARIANT_KERNEL.get(tune[0], "k_encrypt<{mode}> variant %d" % tune[0])
+    elif w.log_n == 15 and tune[0] in (6, 7):
+        kname = "k_encrypt_quarter<{mode},4-CTA cluster,radix-8,3 blocks/SM>"
+    else:
+        kname = f"k_encrypt<{w.log_n},{{mode}}> variant {tune[0]}"
     traffic = NCU_TRAFFIC.get((w.name, kname.format(mode="vanilla"), int(round(chunk_cts))))
     int_pipe = NCU_INT_PIPE.get((w.name, kname.format(mode="vanilla"), int(round(chunk_cts))))
     roofline = {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
@@ -396,17 +400,23 @@ def run_ours(args, w):
         # pinned buffer): the end-to-end rate cannot exceed it
         cstreams = [torch.cuda.Stream(dev) for _ in range(3)]
 
-        def link_probe(reps=3):
-            best = 0.0
-            for _ in range(reps):   # the best of a few: other tenants' traffic only slows a copy down
-                torch.cuda.synchronize(dev)
-                l0 = time.perf_counter()
-                for k, c0 in enumerate(range(0, B, 256)):
+        def copy_pass(dsts):
+            """Seconds to copy the device ciphertexts into `dsts` (one buffer
+            per mode) with the entry point's copy pattern, copies only."""
+            torch.cuda.synchronize(dev)
+            l0 = time.perf_counter()
+            k = 0
+            for src, dst in dsts:
+                for c0 in range(0, B, 256):
                     with torch.cuda.stream(cstreams[k % 3]):
-                        host_v[c0:c0 + 256].copy_(out_v[c0:c0 + 256], non_blocking=True)
-                torch.cuda.synchronize(dev)
-                best = max(best, host_v.numel() * 8 / (time.perf_counter() - l0) / 1e9)
-            return best
+                        dst[c0:c0 + 256].copy_(src[c0:c0 + 256], non_blocking=True)
+                    k += 1
+            torch.cuda.synchronize(dev)
+            return time.perf_counter() - l0
+
+        def link_probe(reps=3):
+            # the best of a few: other tenants' traffic only slows a copy down
+            return max(host_v.numel() * 8 / copy_pass([(out_v, host_v)]) / 1e9 for _ in range(reps))
 
         # the same step with the ciphertexts packed on the device (residues at
         # their primes' bit lengths, zn_encrypt_host_packed): fewer bytes on
@@ -425,7 +435,10 @@ def run_ours(args, w):
         # alternation: the host link of these boxes is shared with other
         # tenants and fluctuates, so each value is the median step of its
         # format over the same stretch of time
-        step_s, p_step_s = [], []
+        # a third, copy-only step moves the plain step's device-to-host bytes
+        # with the same copy pattern and no kernels: the link's own rate over
+        # the same stretch of time
+        step_s, p_step_s, c_step_s = [], [], []
         for _ in range(e2e_steps):
             t_start = time.perf_counter()
             api.zn_encrypt_host(ctx, pk, host_slots, w.seed, host_idx, host_v)
@@ -435,8 +448,11 @@ def run_ours(args, w):
             api.zn_encrypt_host_packed(ctx, pk, host_slots, w.seed, host_idx, host_pv)
             api.zn_encrypt_host_packed(ctx, zc, host_slots, w.seed, host_idx, host_pz)
             p_step_s.append(time.perf_counter() - t_start)
+            c_step_s.append(copy_pass([(out_v, host_v), (out_z, host_z)]))
         step_s = max_over_ranks(step_s, world, dev, dist)
         p_step_s = max_over_ranks(p_step_s, world, dev, dist)
+        c_step_s = max_over_ranks(c_step_s, world, dev, dist)
+        copy_gbs = 2 * host_v.numel() * 8 * e2e_steps / sum(c_step_s) / 1e9
         link_after = link_probe()
         link_gbs = max(link_before, link_after)
         e2e_s = sum(step_s) / len(step_s)
@@ -445,6 +461,11 @@ def run_ours(args, w):
                "statistic": f"all ciphertexts of {e2e_steps} timed steps / their total time",
                "step_s": step_s, "median_enc_s": 2 * B * world / statistics.median(step_s),
                "d2h_link_gbs": link_gbs, "d2h_link_gbs_before_after": [link_before, link_after],
+               "copy_only": {"step_s": c_step_s, "gbs": copy_gbs,
+                             "median_gbs": 2 * host_v.numel() * 8 / statistics.median(c_step_s) / 1e9,
+                             "what": "the plain step's device-to-host bytes, same copy pattern, no kernels, "
+                                     "interleaved with the timed steps"},
+               "of_copy_only_rate": (2 * B * e2e_steps / sum(step_s)) * (2 * w.L * w.n * 8) / (copy_gbs * 1e9),
                "link_bound_enc_s": link_bound * world,
                "of_link_bound": 2 * B / e2e_s / link_bound,
                "d2h_gbs_fastest_step": 2 * host_v.numel() * 8 / min(step_s) / 1e9,

@@ -552,7 +552,7 @@ int zn_ctx_create(const zn_params* p, int device, zn_ctx** out) {
   c->L = L;
   // default launch shape: the radix-8, three-blocks-per-SM kernels where they
   // apply (the fastest measured at 2^13 and 2^14), else kind 0
-  c->variant = (p->log_n >= 10 && p->log_n <= 14) ? 6 : 0;
+  c->variant = (p->log_n >= 10 && p->log_n <= 15) ? 6 : 0;
   if (zn::gen_primes(p->log_n, p->prime_bits, L, c->q)) {
     delete c;
     return ZN_ENOPRIME;

@@ -1,0 +1,75 @@
+// Hot path at N = 2^15 (the large ring and the paper's own parameters): one
+// limb of one ciphertext per four-CTA cluster, one output quarter per CTA
+// (zn_quarter.cuh), with the epilogue
+//   vanilla (Eq. 8):      c0 = pk0*u + NTT(m + e0),  c1 = pk1*u + NTT(e1)
+//   Zinc (Algorithm 1):   c0' = z0 + NTT(m + e1'),   c1' = z1 + NTT(e2')
+// on the integers the prep kernel prepared once per ciphertext.
+#include "zn_quarter.cuh"
+
+namespace zn {
+namespace {
+
+// Encoded message plus noise, stored with the offset 2^62: [0, 2q) after one
+// Barrett step.
+struct MeVal {
+  const i64* me;
+  u64 q, mu, moff;
+  __device__ __forceinline__ u64 operator()(int k) const { return reduce_biased((u64)__ldg(me + k), q, mu, moff); }
+};
+
+template <bool ZINC, bool RELAX>
+__device__ __forceinline__ void encrypt_quarter_unit_q(const DevParams& P, const EncArgs& A, int i, unsigned j,
+                                                       size_t b, u64* sm, int t) {
+  using namespace quarter;
+  const int L = P.L;
+  const u64 q = P.q[i];
+  const ulonglong2* tw = P.twp + (size_t)i * kN;
+  const size_t off = (size_t)j * kQ;
+  FnLimb o;
+  o.c0 = A.out + (b * 2 * L + i) * kN + off;
+  o.c1 = o.c0 + (size_t)L * kN;
+  o.k0 = A.key + (size_t)i * kN + off;
+  o.k1 = o.k0 + (size_t)L * kN;
+  o.k0s = ZINC ? nullptr : A.keys + (size_t)i * kN + off;
+  o.k1s = ZINC ? nullptr : o.k0s + (size_t)L * kN;
+  o.u = nullptr;
+  const int8_t* sp = A.small + b * 2 * kN;       // vanilla: u, e1; Zinc: e2'
+  const MeVal me{A.me + b * kN, q, P.mu[i], P.moff[i]};
+  auto g_me = [&] { gen_val<RELAX>(sm, t, j, me, tw, q); };
+  if constexpr (!ZINC) {
+    auto g_u = [&] { gen_i8<RELAX, true>(sm, t, j, sp, tw, q); };
+    auto g_e1 = [&] { gen_i8<RELAX, false>(sm, t, j, sp + kN, tw, q); };
+    unit<false, RELAX>(sm, t, j, tw, q, o, g_u, g_me, g_e1);
+  } else {
+    auto g_e2 = [&] { gen_i8<RELAX, false>(sm, t, j, sp, tw, q); };
+    unit<true, RELAX>(sm, t, j, tw, q, o, g_me, g_me, g_e2);
+  }
+}
+
+// grid (4L, B), or (4B, L) when A.swap; the CTA of cluster rank j owns
+// output quarter j
+template <bool ZINC>
+__global__ void __launch_bounds__(quarter::kT, 3) k_encrypt_quarter(DevParams P, EncArgs A) {
+  extern __shared__ u64 sm[];
+  const unsigned j = quarter::cluster_rank();
+  const int i = A.swap ? (int)blockIdx.y : (int)(blockIdx.x >> 2);
+  const size_t b = A.swap ? (size_t)(blockIdx.x >> 2) : blockIdx.y;
+  // the relaxed/Harvey choice is uniform per unit, so all four CTAs of a
+  // cluster take the same branch and meet at the same barriers
+  if (P.q[i] < kRelaxLimit) encrypt_quarter_unit_q<ZINC, true>(P, A, i, j, b, sm, threadIdx.x);
+  else encrypt_quarter_unit_q<ZINC, false>(P, A, i, j, b, sm, threadIdx.x);
+}
+
+}  // namespace
+
+cudaError_t launch_encrypt_quarter(const DevParams& P, const EncArgs& A, bool zinc, uint32_t batch,
+                                   cudaStream_t st) {
+  if (batch == 0) return cudaSuccess;
+  if (P.log_n != 15 || (!A.swap && batch > 65535u) || (A.swap && 4ull * batch > 0x7fffffffull))
+    return cudaErrorInvalidValue;
+  const dim3 grid = A.swap ? dim3(4 * batch, P.L) : dim3(4 * P.L, batch);
+  return zinc ? quarter::launch(k_encrypt_quarter<true>, grid, st, P, A)
+              : quarter::launch(k_encrypt_quarter<false>, grid, st, P, A);
+}
+
+}  // namespace zn

@@ -70,6 +70,10 @@ cudaError_t launch_encrypt_mp(const DevParams& P, const EncArgs& A, bool zinc, u
 // Register-capped per-polynomial kernels (2^10 <= N <= 2^14).
 cudaError_t launch_encrypt_occ(const DevParams& P, const EncArgs& A, bool zinc, uint32_t batch, cudaStream_t st);
 cudaError_t launch_encrypt_occ3(const DevParams& P, const EncArgs& A, bool zinc, uint32_t batch, cudaStream_t st);
+// N = 2^15: one four-CTA cluster per limb, one output quarter per CTA, the
+// first three stages exchanged through distributed shared memory.
+cudaError_t launch_encrypt_quarter(const DevParams& P, const EncArgs& A, bool zinc, uint32_t batch,
+                                   cudaStream_t st);
 cudaError_t launch_keygen(const DevParams& P, u64 seed, u64* sk_ntt, u64* pk, u64* pks, cudaStream_t st);
 cudaError_t launch_ntt_fwd(const DevParams& P, u64* data, uint32_t batch, u64* tmp, cudaStream_t st);
 cudaError_t launch_ntt_inv(const DevParams& P, u64* data, uint32_t batch, cudaStream_t st);

@@ -379,9 +379,10 @@ def test_invalid_arguments():
 def test_launch_variants_bit_identical(log_n, bits, ld):
     """Every launch shape the autotuner may choose gives the same ciphertexts."""
     ctx = gpu_ctx(log_n, bits, ld)
-    # a new context starts at the radix-8 kernels where they apply
+    # a new context starts at the radix-8 kernels where they apply (at 2^15
+    # the four-CTA cluster kernel)
     default = api.zn_get_variant(ctx)
-    assert default == (6 if 10 <= log_n <= 14 else 0)
+    assert default == (6 if 10 <= log_n <= 15 else 0)
     _, pk = gpu_keys(log_n, bits, ld, 1)
     zc = gpu_cache(log_n, bits, ld, 1, 2)
     w = workloads.small(log_n, bits, ld, 3, (1 << log_n) // 2 - 5, seed=8)
