@@ -29,7 +29,7 @@ struct zn_ctx {
   // device allocations owned by the context
   u64* d_tw;          // (tw, tws) pairs [L][N], itw [L][N], itws [L][N]: one allocation
   double* d_etw;      // [2][N] decoder twiddles, then [N] encoder Q62 pairs
-  int* d_slot;        // [N/2]
+  int* d_slot;        // [N]: slot_of_t, then pos_of_slot
   unsigned* d_status;
   u64 pinv[ZN_MAX_PRIMES], pinvs[ZN_MAX_PRIMES];   // p^-1 mod q_i (p the last prime), Shoup companions
   cudaMemPool_t pool; // stream-ordered scratch (prep outputs)
@@ -589,11 +589,22 @@ int zn_ctx_create(const zn_params* p, int device, zn_ctx** out) {
     }
     std::memcpy(etw.data() + 2 * (size_t)n, pairs.data(), sizeof(int64_t) * pairs.size());
   }
-  std::vector<int> slot(n / 2);
+  // [0, N/2): slot_of_t, the slot j with t_j = (5^j mod 2N - 1)/4 = t;
+  // [N/2, N): pos_of_slot, slot j's place in the encoder FFT's input (t_j even:
+  // re[brv(t_j / 2)], odd: im[brv(t_j / 2)], im following re at N/4)
+  std::vector<int> slot(n);
   {
+    const int lh = (int)p->log_n - 2;
+    auto brv = [&](uint32_t x) {
+      uint32_t r = 0;
+      for (int b = 0; b < lh; ++b) r |= ((x >> b) & 1u) << (lh - 1 - b);
+      return r;
+    };
     u64 g = 1;
     for (uint32_t j = 0; j < n / 2; ++j) {
-      slot[(g - 1) / 4] = (int)j;
+      const uint32_t t = (uint32_t)((g - 1) / 4);
+      slot[t] = (int)j;
+      slot[n / 2 + j] = (int)((t & 1u) * (n / 4) + brv(t >> 1));
       g = (g * 5) % (2ull * n);
     }
   }
@@ -656,6 +667,7 @@ int zn_ctx_create(const zn_params* p, int device, zn_ctx** out) {
   dp.etw = c->d_etw;
   dp.etq = reinterpret_cast<const longlong2*>(c->d_etw + 2 * (size_t)n);
   dp.slot_of_t = c->d_slot;
+  dp.pos_of_slot = c->d_slot + n / 2;
   dp.status = c->d_status;
   *out = c;
   return ZN_OK;

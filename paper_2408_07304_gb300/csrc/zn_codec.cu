@@ -23,16 +23,23 @@ __device__ __forceinline__ void encode_core(const DevParams& P, const double* __
   __shared__ u64 s_max[32];
   const int log_n = P.log_n, N = 1 << log_n, n = N >> 1, h = n >> 1, lh = log_n - 2;
   const u64 kAbs = ~(1ull << 63);
-  // raw bit patterns in bit-reversed order, and max |z| (as ordered bits)
+  // raw bit patterns in bit-reversed order (missing slots zero), and max |z|
+  // (as ordered bits): the slots are read in order (coalesced) and scattered
+  // to their FFT input places
+  if (n_slots < (uint32_t)n) {
+    for (int r = threadIdx.x; r < h; r += blockDim.x) {
+      re[r] = 0;
+      im[r] = 0;
+    }
+    __syncthreads();
+  }
   u64 mx = 0;
-  for (int r = threadIdx.x; r < h; r += blockDim.x) {
-    const int s2 = 2 * brv_bits(r, lh);
-    const int j0 = __ldg(P.slot_of_t + s2), j1 = __ldg(P.slot_of_t + s2 + 1);
-    const u64 b0 = (j0 < (int)n_slots) ? (u64)__double_as_longlong(__ldg(z + j0)) : 0ull;
-    const u64 b1 = (j1 < (int)n_slots) ? (u64)__double_as_longlong(__ldg(z + j1)) : 0ull;
-    re[r] = (i64)b0;
-    im[r] = (i64)b1;
-    mx = max(mx, max(b0 & kAbs, b1 & kAbs));
+  for (int j = threadIdx.x; j < (int)n_slots; j += blockDim.x) {
+    const u64 bits = (u64)__double_as_longlong(__ldg(z + j));
+    const int pos = __ldg(P.pos_of_slot + j);
+    if (pos < h) re[pos] = (i64)bits;
+    else im[pos - h] = (i64)bits;
+    mx = max(mx, bits & kAbs);
   }
 #pragma unroll
   for (int off = 16; off; off >>= 1) mx = max(mx, (u64)__shfl_xor_sync(0xffffffffu, (unsigned long long)mx, off));
@@ -137,7 +144,7 @@ __device__ __forceinline__ void prep_one(const DevParams& P, const PrepArgs& A, 
     encode_core(P, A.slots + b * A.n_slots, A.n_slots, re, im, st);
     __syncthreads();
   }
-#pragma unroll 1
+#pragma unroll 2
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
     const uint4 w = zn_rand(A.seed, (unsigned)k, tag_e, ct);
     if constexpr (MS) {
@@ -158,7 +165,7 @@ __device__ __forceinline__ void prep_one(const DevParams& P, const PrepArgs& A, 
   if constexpr (!ZINC) {
     int8_t* e1p = sp + (MS ? 2 : 1) * (size_t)N;
     const unsigned tag_u = rand_tag(A.domain, 0, 0), tag_1 = rand_tag(A.domain, 2, 0);
-#pragma unroll 1
+#pragma unroll 2
     for (int blk = threadIdx.x; blk < N / 4; blk += blockDim.x) {
       const uint4 w = zn_rand(A.seed, (unsigned)blk, tag_u, ct);
       sp[blk] = (int8_t)ternary_of(w.x);
@@ -166,7 +173,7 @@ __device__ __forceinline__ void prep_one(const DevParams& P, const PrepArgs& A, 
       sp[blk + N / 2] = (int8_t)ternary_of(w.z);
       sp[blk + 3 * N / 4] = (int8_t)ternary_of(w.w);
     }
-#pragma unroll 1
+#pragma unroll 2
     for (int blk = threadIdx.x; blk < n; blk += blockDim.x) {
       const uint4 w = zn_rand(A.seed, (unsigned)blk, tag_1, ct);
       e1p[blk] = (int8_t)cdt_search(w.x, w.y, cdt);
@@ -174,7 +181,7 @@ __device__ __forceinline__ void prep_one(const DevParams& P, const PrepArgs& A, 
     }
   } else {
     const unsigned tag_2 = rand_tag(A.domain, 1, 0);
-#pragma unroll 1
+#pragma unroll 2
     for (int blk = threadIdx.x; blk < n; blk += blockDim.x) {
       const uint4 w = zn_rand(A.seed, (unsigned)blk, tag_2, ct);
       sp[blk] = (int8_t)cdt_search(w.x, w.y, cdt);

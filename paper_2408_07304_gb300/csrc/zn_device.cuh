@@ -35,6 +35,7 @@ struct DevParams {
   const double* etw;         // [2][N] decoder twiddles (FP64): re, then im
   const longlong2* etq;      // [N] encoder twiddles (C[k], -S[k]), Q62
   const int* slot_of_t;      // [N/2] slot j with (5^j mod 2N - 1)/4 = t
+  const int* pos_of_slot;    // [N/2] slot j's place in the encoder FFT input (< N/4: re, else im)
   unsigned* status;          // device status word (bit 0: encode overflow)
 };
 
@@ -652,32 +653,72 @@ __device__ __forceinline__ void cmul_q62(i64 ar, i64 ai, longlong2 w, i64& re, i
   im = rnd62(add128(mul_wide(ar, w.y), mul_wide(ai, w.x)));
 }
 
+// One radix-2 DIT butterfly of the stage with half-size hh = 2^lh on the
+// pair (a, c), element k < hh of its block: t = cmul(c, W[k N / hh]),
+// (a + t, a - t).  W[0] = 1 and W[N/2] = -i make the product exact, so those
+// are taken directly.
+__device__ __forceinline__ void bfly_q62(i64& ar, i64& ai, i64& cr, i64& ci, int k, int lh, int N,
+                                         const longlong2* etq) {
+  const int hh = 1 << lh;
+  i64 tr, ti;
+  if (k == 0) {
+    tr = cr;
+    ti = ci;
+  } else if (2 * k == hh) {      // W = (0, -2^62)
+    tr = ci;
+    ti = -cr;
+  } else {
+    cmul_q62(cr, ci, __ldg(etq + k * (N >> lh)), tr, ti);
+  }
+  cr = ar - tr;
+  ci = ai - ti;
+  ar = ar + tr;
+  ai = ai + ti;
+}
+
 // Radix-2 decimation-in-time FFT of length 2^log_len on (re, im) int64 in
 // shared memory, input in bit-reversed order; the stage with half-size hh
-// uses W[k N / hh] (N = 2^log_n): t = cmul(c, W), (a + t, a - t).  W[0] = 1
-// and W[N/2] = -i make the product exact, so those are taken directly.
+// uses W[k N / hh] (N = 2^log_n).  Stages are taken two at a time (the four
+// elements p + {0, 1, 2, 3} hh of a block of 4 hh: stage lh on the pairs
+// (0, 1), (2, 3), then stage lh + 1 on (0, 2), (1, 3) with k and k + hh),
+// every radix-2 butterfly computed exactly as in the one-stage-per-pass
+// order, so the result is the same; an odd last stage runs alone.
 __device__ __forceinline__ void fft_dit_q62(i64* re, i64* im, int log_len, int log_n, const longlong2* etq) {
   const int len = 1 << log_len, N = 1 << log_n;
-  for (int lh = 0; lh < log_len; ++lh) {
+  int lh = 0;
+  for (; lh + 1 < log_len; lh += 2) {
+    const int hh = 1 << lh;
+    for (int idx = threadIdx.x; idx < len / 4; idx += blockDim.x) {
+      const int k = idx & (hh - 1);
+      const int p = ((idx >> lh) << (lh + 2)) + k;
+      i64 r0 = re[p], i0 = im[p], r1 = re[p + hh], i1 = im[p + hh];
+      i64 r2 = re[p + 2 * hh], i2 = im[p + 2 * hh], r3 = re[p + 3 * hh], i3 = im[p + 3 * hh];
+      bfly_q62(r0, i0, r1, i1, k, lh, N, etq);
+      bfly_q62(r2, i2, r3, i3, k, lh, N, etq);
+      bfly_q62(r0, i0, r2, i2, k, lh + 1, N, etq);
+      bfly_q62(r1, i1, r3, i3, k + hh, lh + 1, N, etq);
+      re[p] = r0;
+      im[p] = i0;
+      re[p + hh] = r1;
+      im[p + hh] = i1;
+      re[p + 2 * hh] = r2;
+      im[p + 2 * hh] = i2;
+      re[p + 3 * hh] = r3;
+      im[p + 3 * hh] = i3;
+    }
+    __syncthreads();
+  }
+  if (lh < log_len) {
     const int hh = 1 << lh;
     for (int idx = threadIdx.x; idx < len / 2; idx += blockDim.x) {
       const int k = idx & (hh - 1);
       const int p = ((idx >> lh) << (lh + 1)) + k;
-      const i64 ar = re[p], ai = im[p], cr = re[p + hh], ci = im[p + hh];
-      i64 tr, ti;
-      if (k == 0) {
-        tr = cr;
-        ti = ci;
-      } else if (2 * k == hh) {      // W = (0, -2^62)
-        tr = ci;
-        ti = -cr;
-      } else {
-        cmul_q62(cr, ci, __ldg(etq + k * (N >> lh)), tr, ti);
-      }
-      re[p] = ar + tr;
-      im[p] = ai + ti;
-      re[p + hh] = ar - tr;
-      im[p + hh] = ai - ti;
+      i64 ar = re[p], ai = im[p], cr = re[p + hh], ci = im[p + hh];
+      bfly_q62(ar, ai, cr, ci, k, lh, N, etq);
+      re[p] = ar;
+      im[p] = ai;
+      re[p + hh] = cr;
+      im[p + hh] = ci;
     }
     __syncthreads();
   }
