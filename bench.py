@@ -34,20 +34,23 @@ METRIC = "encryptions/s, vanilla CKKS vs Zinc, at N=2^14, 1 GB300; HBM roofline 
 UNIT = "encryptions/s"
 
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one encrypt
-# launch -- 256 ciphertexts of the throughput workload -- from a separate ncu
-# capture of that kernel (not measured by this run), keyed by the kernel it
-# was taken on.  Valid only while that kernel is unchanged and selected.
-NCU_TRAFFIC = {
-    ("throughput", "k_encrypt_half<13,vanilla,radix-8,3 blocks/SM>", 256): 56.379648e6 + 531.450368e6,
-    ("throughput", "k_encrypt_half<13,Zinc,radix-8,3 blocks/SM>", 256): 42.118912e6 + 495.075072e6,
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per ciphertext
+# of the N = 2^14 encrypt kernels, from a separate ncu capture of a
+# 512-ciphertext launch of the throughput workload (not measured by this run),
+# keyed by the kernel it was taken on and scaled to the launch size timed here
+# (a 256-ciphertext capture gave 2.7 % less per ciphertext: part of a smaller
+# launch's output is still in L2 when it ends).  Valid only while that kernel
+# is unchanged and selected.
+NCU_TRAFFIC_PER_CT = {
+    ("throughput", "k_encrypt_half<13,vanilla,radix-8,3 blocks/SM>"): (105.432832e6 + 1103.018e6) / 512,
+    ("throughput", "k_encrypt_half<13,Zinc,radix-8,3 blocks/SM>"): (79.886848e6 + 1047.185e6) / 512,
 }
 # Busy fraction of the SM's integer multiply-add pipe (ncu
 # sm__pipe_fmaheavy_cycles_active, which is also the kernel's
 # sm__throughput: the busiest unit of the SM) in the same capture.
 NCU_INT_PIPE = {
-    ("throughput", "k_encrypt_half<13,vanilla,radix-8,3 blocks/SM>", 256): 0.7371,
-    ("throughput", "k_encrypt_half<13,Zinc,radix-8,3 blocks/SM>", 256): 0.7184,
+    ("throughput", "k_encrypt_half<13,vanilla,radix-8,3 blocks/SM>"): 0.7478,
+    ("throughput", "k_encrypt_half<13,Zinc,radix-8,3 blocks/SM>"): 0.7264,
 }
 VARIANT_KERNEL = {6: "k_encrypt_half<13,{mode},radix-8,3 blocks/SM>",
                   7: "k_encrypt_half<13,{mode},radix-8,3 blocks/SM,ciphertext-major>"}
@@ -329,12 +332,15 @@ def run_ours(args, w):
         kname = "k_encrypt_quarter<{mode},4-CTA cluster,radix-8,3 blocks/SM>"
     else:
         kname = f"k_encrypt<{w.log_n},{{mode}}> variant {tune[0]}"
-    traffic = NCU_TRAFFIC.get((w.name, kname.format(mode="vanilla"), int(round(chunk_cts))))
-    int_pipe = NCU_INT_PIPE.get((w.name, kname.format(mode="vanilla"), int(round(chunk_cts))))
+    per_ct_traffic = NCU_TRAFFIC_PER_CT.get((w.name, kname.format(mode="vanilla")))
+    traffic = per_ct_traffic * chunk_cts if per_ct_traffic else None
+    int_pipe = NCU_INT_PIPE.get((w.name, kname.format(mode="vanilla")))
     roofline = {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": hbm_achieved / hbm_peak, "traffic": traffic,
-                "traffic_source": "ncu capture of this kernel at this launch size, taken separately "
-                                  "(not by this run); null when the selected kernel or size has none",
+                "traffic_source": "ncu capture of this kernel on a 512-ciphertext launch, taken separately "
+                                  "(not by this run), scaled per ciphertext to this launch size; null when the "
+                                  "selected kernel has none",
+                "traffic_over_algorithmic": (traffic / alg_bytes) if traffic else None,
                 "algorithmic_bytes_per_launch": alg_bytes, "ciphertexts_per_launch": chunk_cts,
                 "algorithmic_bytes_per_ct": per_ct_bytes,
                 "kernel": kname.format(mode="vanilla") + f" (variant {tune[0]})",
@@ -356,7 +362,7 @@ def run_ours(args, w):
                         "zinc_kernel_probe_frac": bfly_z / (kz_avg / 1e3) / 1e9 / probe,
                         "int_pipe": {"pipe": "fmaheavy (32-bit integer multiply-add)", "busy_frac": int_pipe,
                                      "source": "ncu sm__pipe_fmaheavy_cycles_active of the same capture as "
-                                               "traffic (not this run)"}}}
+                                               "traffic (512-ciphertext launch, not this run)"}}}
 
     # ---- the same step through the mixed-ring persistent path (one CUDA-graph
     # launch per step: a vanilla job and a Zinc job over the batch)
