@@ -127,6 +127,15 @@ int zn_sk_import(zn_ctx* ctx, const int8_t* host_in, zn_sk** out);
 int ckks_encode(zn_ctx* ctx, const double* slots, uint32_t n_slots, uint32_t batch,
                 int64_t* out, void* stream);
 
+/* The same encoding with a slot count per vector (the boundary's per-vector
+ * n_slots array): vector b has n_slots[b] slots (device uint32 [batch]), read
+ * from row b of `slots` (device double [batch][stride]; stride <= N/2, 0
+ * allowed when every count is 0); its missing slots are zero, so the result
+ * equals ckks_encode of that row zero-padded.  A count above stride latches
+ * ZN_EINVAL for zn_sync_status and encodes that vector as zero. */
+int ckks_encode_ragged(zn_ctx* ctx, const double* slots, const uint32_t* n_slots, uint32_t stride,
+                       uint32_t batch, int64_t* out, void* stream);
+
 /* -------------------------------------------------------------- encrypt */
 
 /* Vanilla public-key encryption, paper Eq. 8 (second component with pk1):
@@ -138,6 +147,15 @@ int ckks_encode(zn_ctx* ctx, const double* slots, uint32_t n_slots, uint32_t bat
 int ckks_encrypt(zn_ctx* ctx, const zn_pk* pk, const double* slots, uint32_t n_slots,
                  uint32_t batch, uint64_t seed, const uint64_t* ct_index, uint64_t* ct,
                  void* stream);
+
+/* ckks_encrypt with a slot count per vector, as ckks_encode_ragged: n_slots
+ * device uint32 [batch], slots device double [batch][stride].  Vector b's
+ * ciphertext equals ckks_encrypt's for its row zero-padded to any length
+ * (padding is exact); a count above stride latches ZN_EINVAL for
+ * zn_sync_status and encrypts the zero plaintext. */
+int ckks_encrypt_ragged(zn_ctx* ctx, const zn_pk* pk, const double* slots, const uint32_t* n_slots,
+                        uint32_t stride, uint32_t batch, uint64_t seed, const uint64_t* ct_index,
+                        uint64_t* ct, void* stream);
 
 /* Zinc precomputation (Section "Precomputation"): cache one Enc(0) — a vanilla
  * encryption of the zero plaintext under pk with sampling domain 3,
@@ -154,6 +172,12 @@ int zn_zcache_import(zn_ctx* ctx, const uint64_t* host_in, zn_zcache** out);
 int zinc_encrypt(zn_ctx* ctx, const zn_zcache* zc, const double* slots, uint32_t n_slots,
                  uint32_t batch, uint64_t seed, const uint64_t* ct_index, uint64_t* ct,
                  void* stream);
+
+/* zinc_encrypt with a slot count per vector (Algorithm 1; arguments as
+ * ckks_encrypt_ragged with the cache in place of the public key). */
+int zinc_encrypt_ragged(zn_ctx* ctx, const zn_zcache* zc, const double* slots, const uint32_t* n_slots,
+                        uint32_t stride, uint32_t batch, uint64_t seed, const uint64_t* ct_index,
+                        uint64_t* ct, void* stream);
 
 /* Allocation-free Zinc encryption (no counterpart in the paper).  For callers
  * that must not allocate device memory during a call: code running where

@@ -56,6 +56,9 @@ _SIGS = {
     "zn_sk_export": (_i32, [_vp, _vp]),
     "zn_sk_import": (_i32, [_vp, _vp, _pp]),
     "ckks_encode": (_i32, [_vp, _vp, _u32, _u32, _vp, _vp]),
+    "ckks_encode_ragged": (_i32, [_vp, _vp, _vp, _u32, _u32, _vp, _vp]),
+    "ckks_encrypt_ragged": (_i32, [_vp, _vp, _vp, _vp, _u32, _u32, _u64, _vp, _vp, _vp]),
+    "zinc_encrypt_ragged": (_i32, [_vp, _vp, _vp, _vp, _u32, _u32, _u64, _vp, _vp, _vp]),
     "ckks_encrypt": (_i32, [_vp, _vp, _vp, _u32, _u32, _u64, _vp, _vp, _vp]),
     "zinc_precompute": (_i32, [_vp, _vp, _u64, _pp]),
     "zn_zcache_destroy": (None, [_vp]),
@@ -307,6 +310,45 @@ def ckks_encode(ctx, slots, out=None, stream=None):
     _dev(out, torch.int64, (B, ctx.n), "out")
     _check(lib().ckks_encode(ctx.handle, slots.data_ptr(), ns, B, out.data_ptr(), _stream(stream)), "ckks_encode")
     return out
+
+
+def ckks_encode_ragged(ctx, slots, n_slots, out=None, stream=None):
+    """Per-vector slot counts: slots CUDA float64 [B, stride], n_slots CUDA
+    int32 [B] (vector b uses its first n_slots[b] entries) -> int64 [B, N]."""
+    import torch
+    B, stride = slots.shape
+    out = _out(out, (B, ctx.n), torch.int64, slots.device)
+    _dev(slots, torch.float64, None, "slots")
+    _dev(n_slots, torch.int32, (B,), "n_slots")
+    _dev(out, torch.int64, (B, ctx.n), "out")
+    _check(lib().ckks_encode_ragged(ctx.handle, slots.data_ptr(), n_slots.data_ptr(), stride, B, out.data_ptr(),
+                                    _stream(stream)), "ckks_encode_ragged")
+    return out
+
+
+def _enc_ragged(fn, ctx, key, slots, n_slots, seed, ct_index, out, stream, name):
+    import torch
+    B, stride = slots.shape
+    out = _out(out, (B, 2, ctx.L, ctx.n), torch.int64, slots.device)
+    _dev(slots, torch.float64, None, "slots")
+    _dev(n_slots, torch.int32, (B,), "n_slots")
+    _dev(ct_index, torch.int64, (B,), "ct_index")
+    _dev(out, torch.int64, (B, 2, ctx.L, ctx.n), "out")
+    _check(fn(ctx.handle, key.handle, slots.data_ptr(), n_slots.data_ptr(), stride, B, seed, ct_index.data_ptr(),
+              out.data_ptr(), _stream(stream)), name)
+    return out
+
+
+def ckks_encrypt_ragged(ctx, pk, slots, n_slots, seed, ct_index, out=None, stream=None):
+    """Vanilla encryption with a slot count per vector (n_slots CUDA int32 [B])."""
+    return _enc_ragged(lib().ckks_encrypt_ragged, ctx, pk, slots, n_slots, seed, ct_index, out, stream,
+                       "ckks_encrypt_ragged")
+
+
+def zinc_encrypt_ragged(ctx, zc, slots, n_slots, seed, ct_index, out=None, stream=None):
+    """Zinc encryption with a slot count per vector (n_slots CUDA int32 [B])."""
+    return _enc_ragged(lib().zinc_encrypt_ragged, ctx, zc, slots, n_slots, seed, ct_index, out, stream,
+                       "zinc_encrypt_ragged")
 
 
 def _enc(fn, ctx, key, slots, seed, ct_index, out, stream, name):

@@ -216,14 +216,19 @@ uint32_t encode_chunk(const zn_ctx* c) {
 // Prep + encrypt launch pairs over `batch` ciphertexts in chunks of `chunk`,
 // with caller-provided scratch for one chunk: me int64 [chunk][N], small
 // int8 [chunk][2][N].
+// nv != nullptr: per-vector slot counts (device [batch]) over rows of `stride`
+// doubles, in place of n_slots.
 int encrypt_with(zn_ctx* c, bool zinc, const u64* key, const u64* keys, const double* slots, uint32_t n_slots,
                  uint32_t batch, uint64_t seed, const uint64_t* ct_index, uint64_t* ct, i64* me, int8_t* small,
-                 uint32_t chunk, cudaStream_t st) {
+                 uint32_t chunk, cudaStream_t st, const uint32_t* nv = nullptr, uint32_t stride = 0) {
+  const size_t row = nv ? stride : n_slots;
   for (uint32_t b0 = 0; b0 < batch; b0 += chunk) {
     const uint32_t nb = (batch - b0) < chunk ? (batch - b0) : chunk;
     zn::PrepArgs pa;
-    pa.slots = slots + (size_t)b0 * n_slots;
+    pa.slots = slots ? slots + (size_t)b0 * row : nullptr;
     pa.n_slots = n_slots;
+    pa.n_slots_v = nv ? nv + b0 : nullptr;
+    pa.stride = stride;
     pa.ct_index = ct_index + b0;
     pa.ct_index0 = 0;
     pa.seed = seed;
@@ -254,10 +259,11 @@ size_t encrypt_scratch_bytes(const zn_ctx* c, uint32_t chunk) {
 }
 
 int encrypt_common(zn_ctx* c, bool zinc, const u64* key, const u64* keys, const double* slots, uint32_t n_slots,
-                   uint32_t batch, uint64_t seed, const uint64_t* ct_index, uint64_t* ct, void* stream) {
-  if (!c || !key || n_slots > c->n / 2) return ZN_EINVAL;
+                   uint32_t batch, uint64_t seed, const uint64_t* ct_index, uint64_t* ct, void* stream,
+                   const uint32_t* nv = nullptr, uint32_t stride = 0) {
+  if (!c || !key || n_slots > c->n / 2 || stride > c->n / 2) return ZN_EINVAL;
   if (batch == 0) return ZN_OK;
-  if (!ct || !ct_index || (n_slots && !slots)) return ZN_EINVAL;
+  if (!ct || !ct_index || (n_slots && !slots) || (nv && stride && !slots)) return ZN_EINVAL;
   DeviceGuard g(c->device);
   // equal chunks of at most encode_chunk(c), so that no launch is a small tail
   const uint32_t cap = encode_chunk(c);
@@ -267,7 +273,8 @@ int encrypt_common(zn_ctx* c, bool zinc, const u64* key, const u64* keys, const 
   if (!scratch.alloc(encrypt_scratch_bytes(c, first))) return ZN_ENOMEM;
   i64* me = (i64*)scratch.p;
   int8_t* small = (int8_t*)scratch.p + sizeof(i64) * first * (size_t)c->n;
-  return encrypt_with(c, zinc, key, keys, slots, n_slots, batch, seed, ct_index, ct, me, small, first, S(stream));
+  return encrypt_with(c, zinc, key, keys, slots, n_slots, batch, seed, ct_index, ct, me, small, first, S(stream), nv,
+                      stride);
 }
 
 // The modulus-switched encryption's arguments that depend only on the context.
@@ -922,6 +929,17 @@ int ckks_encode(zn_ctx* c, const double* slots, uint32_t n_slots, uint32_t batch
   return ZN_OK;
 }
 
+int ckks_encode_ragged(zn_ctx* c, const double* slots, const uint32_t* n_slots, uint32_t stride, uint32_t batch,
+                       int64_t* out, void* stream) {
+  NvtxRange nvtx("ckks_encode_ragged");
+  if (!c || stride > c->n / 2) return ZN_EINVAL;
+  if (batch == 0) return ZN_OK;
+  if (!out || !n_slots || (stride && !slots)) return ZN_EINVAL;
+  DeviceGuard g(c->device);
+  ZN_CUDA(zn::launch_encode_ragged(c->dp, slots, n_slots, stride, batch, (i64*)out, S(stream)));
+  return ZN_OK;
+}
+
 // -------------------------------------------------------------- encrypt
 
 int ckks_encrypt(zn_ctx* c, const zn_pk* pk, const double* slots, uint32_t n_slots, uint32_t batch, uint64_t seed,
@@ -930,6 +948,14 @@ int ckks_encrypt(zn_ctx* c, const zn_pk* pk, const double* slots, uint32_t n_slo
   if (!c || !pk_of(pk, c)) return ZN_EINVAL;
   return encrypt_common(c, false, pk->d, pk->d + 2 * ring_words(c), slots, n_slots, batch, seed, ct_index, ct,
                         stream);
+}
+
+int ckks_encrypt_ragged(zn_ctx* c, const zn_pk* pk, const double* slots, const uint32_t* n_slots, uint32_t stride,
+                        uint32_t batch, uint64_t seed, const uint64_t* ct_index, uint64_t* ct, void* stream) {
+  NvtxRange nvtx("ckks_encrypt_ragged");
+  if (!c || !pk_of(pk, c) || (batch && !n_slots)) return ZN_EINVAL;
+  return encrypt_common(c, false, pk->d, pk->d + 2 * ring_words(c), slots, 0, batch, seed, ct_index, ct, stream,
+                        n_slots, stride);
 }
 
 int zinc_precompute(zn_ctx* c, const zn_pk* pk, uint64_t seed, zn_zcache** out) {
@@ -1032,6 +1058,13 @@ int zinc_encrypt(zn_ctx* c, const zn_zcache* z, const double* slots, uint32_t n_
   NvtxRange nvtx("zinc_encrypt");
   if (!c || !zc_of(z, c)) return ZN_EINVAL;
   return encrypt_common(c, true, z->d, nullptr, slots, n_slots, batch, seed, ct_index, ct, stream);
+}
+
+int zinc_encrypt_ragged(zn_ctx* c, const zn_zcache* z, const double* slots, const uint32_t* n_slots, uint32_t stride,
+                        uint32_t batch, uint64_t seed, const uint64_t* ct_index, uint64_t* ct, void* stream) {
+  NvtxRange nvtx("zinc_encrypt_ragged");
+  if (!c || !zc_of(z, c) || (batch && !n_slots)) return ZN_EINVAL;
+  return encrypt_common(c, true, z->d, nullptr, slots, 0, batch, seed, ct_index, ct, stream, n_slots, stride);
 }
 
 // ------------------------------------- special prime and modulus switching

@@ -103,11 +103,26 @@ __device__ __forceinline__ void encode_one(const DevParams& P, const double* __r
   encode_core(P, z, n_slots, re, im, st);
 }
 
-__global__ void k_encode_smem(DevParams P, const double* __restrict__ slots, uint32_t n_slots, i64* __restrict__ out) {
+// The slot count of vector b: nv[b] (per-vector counts over rows of `stride`
+// doubles; a count above stride latches kStatusRange and encodes zero) or the
+// call's n_slots.
+__device__ __forceinline__ uint32_t slots_of(const DevParams& P, const uint32_t* nv, uint32_t stride,
+                                             uint32_t n_slots, size_t b) {
+  if (!nv) return n_slots;
+  const uint32_t k = __ldg(nv + b);
+  if (k <= stride) return k;
+  if (threadIdx.x == 0) atomicOr(P.status, kStatusRange);
+  return 0;
+}
+
+// nv == nullptr: n_slots per vector, rows of n_slots; else rows of `stride`.
+__global__ void k_encode_smem(DevParams P, const double* __restrict__ slots, uint32_t n_slots,
+                              const uint32_t* __restrict__ nv, uint32_t stride, i64* __restrict__ out) {
   extern __shared__ i64 smi[];
   const int N = 1 << P.log_n, h = N >> 2;
   const size_t b = blockIdx.x;
-  encode_one(P, slots + b * n_slots, n_slots, smi, smi + h, out + b * N);
+  const uint32_t ns = slots_of(P, nv, stride, n_slots, b);
+  encode_one(P, slots + b * (nv ? stride : n_slots), ns, smi, smi + h, out + b * N);
 }
 
 // -------------------------------------------------------------------- prep
@@ -132,23 +147,25 @@ __device__ __forceinline__ void prep_one(const DevParams& P, const PrepArgs& A, 
   i64* me = A.me + b * N;
   int8_t* sp = A.small + b * (MS ? 3 : 2) * (size_t)N;
   const unsigned tag_e = rand_tag(A.domain, ZINC ? 0 : 1, 0);
+  const uint32_t ns = slots_of(P, A.n_slots_v, A.stride, A.n_slots, b);
+  const double* z = A.slots + b * (A.n_slots_v ? A.stride : A.n_slots);
   // m first (kept apart from the sampler, which would otherwise share the
   // encoder's registers), then m + e once the block's stores are visible
-  if (A.n_slots) {
+  if (ns) {
     // MS: stored as m + 2^62 (non-negative), read back by the data primes as unsigned
     constexpr i64 off = MS ? (i64)kMsOffset : 0;
     auto st = [&](int k, i64 a, i64 c) {
       me[k] = a + off;
       me[k + n] = c + off;
     };
-    encode_core(P, A.slots + b * A.n_slots, A.n_slots, re, im, st);
+    encode_core(P, z, ns, re, im, st);
     __syncthreads();
   }
 #pragma unroll 2
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
     const uint4 w = zn_rand(A.seed, (unsigned)k, tag_e, ct);
     if constexpr (MS) {
-      if (!A.n_slots) {
+      if (!ns) {
         me[k] = (i64)kMsOffset;
         me[k + n] = (i64)kMsOffset;
       }
@@ -157,7 +174,7 @@ __device__ __forceinline__ void prep_one(const DevParams& P, const PrepArgs& A, 
     } else {
       // m + e with the offset 2^62 (non-negative as an unsigned word; the
       // encryption units remove it with reduce_biased)
-      const i64 a = A.n_slots ? me[k] : 0, c = A.n_slots ? me[k + n] : 0;
+      const i64 a = ns ? me[k] : 0, c = ns ? me[k + n] : 0;
       me[k] = (i64)((u64)(a + cdt_search(w.x, w.y, cdt)) + kMsOffset);
       me[k + n] = (i64)((u64)(c + cdt_search(w.z, w.w, cdt)) + kMsOffset);
     }
@@ -382,7 +399,19 @@ cudaError_t launch_encode(const DevParams& P, const double* slots, uint32_t n_sl
   const size_t smem = 2 * sizeof(i64) * (size_t)h;
   cudaError_t e = cudaFuncSetAttribute(k_encode_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_encode_smem<<<batch, block, smem, st>>>(P, slots, n_slots, out);
+  k_encode_smem<<<batch, block, smem, st>>>(P, slots, n_slots, nullptr, 0, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_encode_ragged(const DevParams& P, const double* slots, const uint32_t* nv, uint32_t stride,
+                                 uint32_t batch, i64* out, cudaStream_t st) {
+  if (batch == 0) return cudaSuccess;
+  const int h = 1 << (P.log_n - 2);
+  const int block = h / 2 < 512 ? (h / 2 < 32 ? 32 : h / 2) : 512;
+  const size_t smem = 2 * sizeof(i64) * (size_t)h;
+  cudaError_t e = cudaFuncSetAttribute(k_encode_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_encode_smem<<<batch, block, smem, st>>>(P, slots, 0, nv, stride, out);
   return cudaGetLastError();
 }
 
@@ -390,7 +419,7 @@ template <bool ZINC, bool MS = false>
 static cudaError_t prep_launch(const DevParams& P, const PrepArgs& A, uint32_t batch, cudaStream_t st) {
   const int h = 1 << (P.log_n - 2);
   const int block = h / 2 < 512 ? (h / 2 < 32 ? 32 : h / 2) : 512;
-  const size_t smem = A.n_slots ? 2 * sizeof(i64) * (size_t)h : 0;
+  const size_t smem = (A.n_slots || A.n_slots_v) ? 2 * sizeof(i64) * (size_t)h : 0;
   auto kern = k_prep_smem<ZINC, MS>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

@@ -6,7 +6,7 @@ namespace zn {
 
 // Per-ciphertext inputs prepared once for all primes by the prep kernel.
 struct PrepArgs {
-  const double* slots;  // [B][n_slots]
+  const double* slots;  // [B][n_slots], or [B][stride] with per-vector counts
   uint32_t n_slots;     // 0: zero plaintext
   const u64* ct_index;  // [B] or nullptr (then ct_index0 + b)
   u64 ct_index0;
@@ -14,6 +14,11 @@ struct PrepArgs {
   unsigned domain;      // sampling domain (0 vanilla, 1 Zinc, 3 Zinc cache)
   i64* me;              // [B][N] encoded message plus its noise polynomial
   int8_t* small;        // [B][2][N] small polynomials (vanilla: u, e1; Zinc: e2')
+  // Per-vector slot counts (device [B], each <= stride <= N/2; rows of
+  // `stride` doubles) in place of n_slots; nullptr: n_slots for every vector.
+  // A count above `stride` latches kStatusRange and encodes zero.
+  const uint32_t* n_slots_v = nullptr;
+  uint32_t stride = 0;
 };
 
 struct EncArgs {
@@ -27,6 +32,9 @@ struct EncArgs {
 
 cudaError_t launch_encode(const DevParams& P, const double* slots, uint32_t n_slots, uint32_t batch, i64* out,
                           cudaStream_t st);
+// Per-vector slot counts nv (device [batch]) over rows of `stride` doubles.
+cudaError_t launch_encode_ragged(const DevParams& P, const double* slots, const uint32_t* nv, uint32_t stride,
+                                 uint32_t batch, i64* out, cudaStream_t st);
 cudaError_t launch_prep(const DevParams& P, const PrepArgs& A, bool zinc, uint32_t batch, cudaStream_t st);
 // Mixed-ring batches (persistent kernels): one descriptor per job (a ring,
 // a mode, a key or cache, buffers), a work list of encrypt packets and one of

@@ -7,9 +7,10 @@ and Zinc cache resident on the device and runs an event loop:
 * arrived requests join a queue per (ring, mode);
 * whenever a CUDA stream is free and the HBM budget allows, the queue whose
   head has waited longest is cut into a batch (up to ``max_batch``
-  requests), its slots staged (zero-padded to the batch's longest vector --
-  missing slots are zero, so padding does not change any ciphertext) and
-  copied on that stream, and the encryption launched on the same stream;
+  requests), its slots staged in rows of the batch's longest vector with
+  each request's own slot count (the per-vector count entry points: a
+  request's missing slots are zero, so its ciphertext is the same as alone)
+  and copied on that stream, and the encryption launched on the same stream;
 * batches on different streams overlap on the device; a batch's HBM
   reservation (slots, ciphertexts, scratch) is released when its completion
   event fires, which admits the next requests;
@@ -212,21 +213,26 @@ class Server:
         torch = self.torch
         ctx, _, pk, zc = self.rings[ring]
         B = len(batch)
-        host = torch.zeros((B, ns), dtype=torch.float64, pin_memory=True)
+        # rows of the longest vector, entries past a request's count left as
+        # they are (never read)
+        host = torch.empty((B, ns), dtype=torch.float64, pin_memory=True)
         hv = host.numpy()
         for k, r in enumerate(batch):
             hv[k, : r.slots.shape[0]] = r.slots
         hidx = torch.tensor([r.rid for r in batch], dtype=torch.int64).pin_memory()
+        hcnt = torch.tensor([r.slots.shape[0] for r in batch], dtype=torch.int32).pin_memory()
         with torch.cuda.stream(stream):
             z = host.to(self.dev, non_blocking=True)
             idx = hidx.to(self.dev, non_blocking=True)
+            cnt = hcnt.to(self.dev, non_blocking=True)
             out = torch.empty((B, 2, ctx.L, ctx.n), dtype=torch.int64, device=self.dev)
-            fn = api.zinc_encrypt if zinc else api.ckks_encrypt
-            fn(ctx, zc if zinc else pk, z, self.seed, idx, out=out, stream=stream)
+            fn = api.zinc_encrypt_ragged if zinc else api.ckks_encrypt_ragged
+            fn(ctx, zc if zinc else pk, z, cnt, self.seed, idx, out=out, stream=stream)
             # keep the staging buffers alive until the stream has consumed them
             z.record_stream(stream)
             idx.record_stream(stream)
-        out._staging = (host, hidx)
+            cnt.record_stream(stream)
+        out._staging = (host, hidx, hcnt)
         return out
 
 
