@@ -400,8 +400,9 @@ int zn_sample(zn_ctx* ctx, int kind, uint64_t seed, uint32_t domain, uint32_t po
 
 /* chi's table step alone (no counterpart in the paper; a check of threshold
  * boundaries): out[i] = -19 + #{j : u[i] >= T_j} for device uint64 u[n],
- * device int32 out[n], computed by the binary search over the 38 thresholds
- * that the encryption path uses. */
+ * device int32 out[n], computed by the lookup the encryption path uses (a
+ * 256-bucket index over the top 8 bits of u, then a scan of the thresholds
+ * inside the bucket). */
 int zn_chi_eval(zn_ctx* ctx, const uint64_t* u, uint32_t n, int32_t* out, void* stream);
 
 /* ------------------------------------------------ mixed-ring batched launch */

@@ -137,10 +137,11 @@ __global__ void k_encode_smem(DevParams P, const double* __restrict__ slots, uin
 //     after it)
 // chi block k yields coefficients k and k + N/2 -- the pair that the
 // encoder's last loop produces at k.
-// cdt: the chi thresholds staged in shared memory by the calling kernel.
+// cdt: the chi thresholds and their bucket index, staged in shared memory by
+// the calling kernel.
 template <bool ZINC, bool MS = false>
 __device__ __forceinline__ void prep_one(const DevParams& P, const PrepArgs& A, size_t b, i64* re, i64* im,
-                                         const u64* cdt) {
+                                         const CdtTab* cdt) {
   static_assert(!(ZINC && MS), "the modulus-switched form is a vanilla encryption");
   const int N = 1 << P.log_n, n = N >> 1;
   const u64 ct = A.ct_index ? A.ct_index[b] : A.ct_index0 + b;
@@ -169,14 +170,14 @@ __device__ __forceinline__ void prep_one(const DevParams& P, const PrepArgs& A, 
         me[k] = (i64)kMsOffset;
         me[k + n] = (i64)kMsOffset;
       }
-      sp[N + k] = (int8_t)cdt_search(w.x, w.y, cdt);
-      sp[N + k + n] = (int8_t)cdt_search(w.z, w.w, cdt);
+      sp[N + k] = (int8_t)cdt_lookup(w.x, w.y, *cdt);
+      sp[N + k + n] = (int8_t)cdt_lookup(w.z, w.w, *cdt);
     } else {
       // m + e with the offset 2^62 (non-negative as an unsigned word; the
       // encryption units remove it with reduce_biased)
       const i64 a = ns ? me[k] : 0, c = ns ? me[k + n] : 0;
-      me[k] = (i64)((u64)(a + cdt_search(w.x, w.y, cdt)) + kMsOffset);
-      me[k + n] = (i64)((u64)(c + cdt_search(w.z, w.w, cdt)) + kMsOffset);
+      me[k] = (i64)((u64)(a + cdt_lookup(w.x, w.y, *cdt)) + kMsOffset);
+      me[k + n] = (i64)((u64)(c + cdt_lookup(w.z, w.w, *cdt)) + kMsOffset);
     }
   }
   if constexpr (!ZINC) {
@@ -193,32 +194,28 @@ __device__ __forceinline__ void prep_one(const DevParams& P, const PrepArgs& A, 
 #pragma unroll 2
     for (int blk = threadIdx.x; blk < n; blk += blockDim.x) {
       const uint4 w = zn_rand(A.seed, (unsigned)blk, tag_1, ct);
-      e1p[blk] = (int8_t)cdt_search(w.x, w.y, cdt);
-      e1p[blk + n] = (int8_t)cdt_search(w.z, w.w, cdt);
+      e1p[blk] = (int8_t)cdt_lookup(w.x, w.y, *cdt);
+      e1p[blk + n] = (int8_t)cdt_lookup(w.z, w.w, *cdt);
     }
   } else {
     const unsigned tag_2 = rand_tag(A.domain, 1, 0);
 #pragma unroll 2
     for (int blk = threadIdx.x; blk < n; blk += blockDim.x) {
       const uint4 w = zn_rand(A.seed, (unsigned)blk, tag_2, ct);
-      sp[blk] = (int8_t)cdt_search(w.x, w.y, cdt);
-      sp[blk + n] = (int8_t)cdt_search(w.z, w.w, cdt);
+      sp[blk] = (int8_t)cdt_lookup(w.x, w.y, *cdt);
+      sp[blk + n] = (int8_t)cdt_lookup(w.z, w.w, *cdt);
     }
   }
 }
 
-__device__ __forceinline__ void stage_cdt(const DevParams& P, u64* s_cdt) {
-  for (int j = threadIdx.x; j < kCdt; j += blockDim.x) s_cdt[j] = P.cdt[j];
-  __syncthreads();
-}
 
 template <bool ZINC, bool MS = false>
 __global__ void __launch_bounds__(512, 2) k_prep_smem(DevParams P, PrepArgs A) {
   extern __shared__ i64 smi[];
-  __shared__ u64 s_cdt[kCdt];
-  stage_cdt(P, s_cdt);
+  __shared__ CdtTab s_cdt;
+  stage_cdt_tab(P.cdt, s_cdt);
   const int h = 1 << (P.log_n - 2);
-  prep_one<ZINC, MS>(P, A, blockIdx.x, smi, smi + h, s_cdt);
+  prep_one<ZINC, MS>(P, A, blockIdx.x, smi, smi + h, &s_cdt);
 }
 
 // Persistent prep over a mixed work list: one 512-thread block per SM takes
@@ -228,7 +225,7 @@ __global__ void __launch_bounds__(512, 1) k_batch_prep(const JobDesc* __restrict
                                                        const PrepUnit* __restrict__ units, int n_units, int* counter) {
   extern __shared__ i64 smi[];
   __shared__ int s_next;
-  __shared__ u64 s_cdt[kCdt];
+  __shared__ CdtTab s_cdt;
   for (;;) {
     if (threadIdx.x == 0) s_next = atomicAdd(counter, 1);
     __syncthreads();
@@ -238,9 +235,9 @@ __global__ void __launch_bounds__(512, 1) k_batch_prep(const JobDesc* __restrict
     const PrepUnit u = units[p];
     const JobDesc& J = jobs[u.job];
     const int h = 1 << (J.P.log_n - 2);
-    stage_cdt(J.P, s_cdt);
-    if (J.zinc) prep_one<true>(J.P, J.Pr, u.b, smi, smi + h, s_cdt);
-    else prep_one<false>(J.P, J.Pr, u.b, smi, smi + h, s_cdt);
+    stage_cdt_tab(J.P.cdt, s_cdt);
+    if (J.zinc) prep_one<true>(J.P, J.Pr, u.b, smi, smi + h, &s_cdt);
+    else prep_one<false>(J.P, J.Pr, u.b, smi, smi + h, &s_cdt);
     __syncthreads();
   }
 }

@@ -191,15 +191,39 @@ __device__ __forceinline__ int cdt_of(unsigned lo, unsigned hi, const u64* cdt) 
   return c - kBound;
 }
 
-// The same count by a branchless binary search over the sorted thresholds
-// (pos ends at #{j : T_j <= U}), for a table in shared memory: six dependent
-// loads and compares instead of 38 compares against live constants.
-__device__ __forceinline__ int cdt_search(unsigned lo, unsigned hi, const u64* tab) {
+// The chi thresholds with a bucket index over the top 8 bits of U, staged in
+// shared memory: bucket x covers U in [x 2^56, (x + 1) 2^56); b[x] holds
+// lo = #{j : T_j <= x 2^56} and hi = #{j : T_j <= (x + 1) 2^56 - 1}.  The
+// thresholds are sorted, so for U in bucket x the count #{j : T_j <= U} is
+// lo plus the thresholds T_lo.. T_(hi-1) not above U: one shared-memory load
+// when lo = hi (most buckets hold no threshold), a short scan otherwise.
+struct CdtTab {
+  u64 t[kCdt];
+  uint16_t b[256];
+};
+
+// All threads of the block; ends with a barrier.
+__device__ __forceinline__ void stage_cdt_tab(const u64* cdt, CdtTab& T) {
+  for (int j = threadIdx.x; j < kCdt; j += blockDim.x) T.t[j] = cdt[j];
+  for (int x = threadIdx.x; x < 256; x += blockDim.x) {
+    const u64 a = (u64)x << 56, e = a + ((1ull << 56) - 1);
+    int lo = 0, hi = 0;
+    for (int j = 0; j < kCdt; ++j) {
+      lo += cdt[j] <= a ? 1 : 0;
+      hi += cdt[j] <= e ? 1 : 0;
+    }
+    T.b[x] = (uint16_t)(lo | (hi << 8));
+  }
+  __syncthreads();
+}
+
+// chi: -19 + #{j : U >= T_j} by the bucket index (the same count as cdt_of).
+__device__ __forceinline__ int cdt_lookup(unsigned lo, unsigned hi, const CdtTab& T) {
   const u64 u = ((u64)hi << 32) | lo;
-  int pos = 0;
-#pragma unroll
-  for (int step = 32; step; step >>= 1)
-    if (pos + step <= kCdt && u >= tab[pos + step - 1]) pos += step;
+  const unsigned e = T.b[hi >> 24];
+  int pos = (int)(e & 0xffu);
+  const int top = (int)(e >> 8);
+  while (pos < top && u >= T.t[pos]) ++pos;     // at most kCdt steps
   return pos - kBound;
 }
 
@@ -297,19 +321,21 @@ __device__ __forceinline__ void ntt_pass(u64* sm, int t, const ulonglong2* __res
 // STAGED: the last pass writes back to shared memory like the others and the
 // outputs are handed to store() in natural index order (consecutive lanes,
 // consecutive indices), which keeps the epilogue's global accesses coalesced
-// when the last pass owns several adjacent outputs per thread.
+// when the last pass owns several adjacent outputs per thread; EU is that
+// loop's unroll factor (a register-pressure knob: 4 keeps the vanilla units
+// spill-free at 80 registers, 2 the Zinc ones).
 template <int LOGN, int LOGPER, int HI, bool RELAX, class Store, int KM = NttShape<LOGN>::KMAX, bool RAW = false,
-          bool STAGED = false>
+          bool STAGED = false, int EU = 4>
 __device__ __forceinline__ void ntt_chain(u64* sm, int t, const ulonglong2* twp, int tmul, u64 q, Store& store) {
   constexpr int K = HI < KM ? HI : KM;
   constexpr int LO = HI - K;
   __syncthreads();
   ntt_pass<LOGN, LOGPER, LO, K, RELAX, Store, KM, RAW, STAGED>(sm, t, twp, tmul, q, store);
   if constexpr (LO > 0) {
-    ntt_chain<LOGN, LOGPER, LO, RELAX, Store, KM, RAW, STAGED>(sm, t, twp, tmul, q, store);
+    ntt_chain<LOGN, LOGPER, LO, RELAX, Store, KM, RAW, STAGED, EU>(sm, t, twp, tmul, q, store);
   } else if constexpr (STAGED) {
     __syncthreads();
-#pragma unroll 4
+#pragma unroll EU
     for (int idx = t; idx < (1 << LOGN); idx += NttShape<LOGN, LOGPER>::T) {
       const u64 x = sm[swz<LOGN, KM>(idx)];
       if constexpr (RAW) store(idx, x);
@@ -647,10 +673,20 @@ __device__ __forceinline__ i64 rnd62(i128 x) {
   const i64 hi = x.hi + (i64)(lo < x.lo);
   return (i64)(((u64)hi << 2) | (lo >> 62));
 }
-// (a_r + i a_i)(w_r + i w_i) with Q62 w: each part exact, rounded once
+// (a_r + i a_i)(w_r + i w_i) with Q62 w: each part exact, rounded once.
+// The exact numerators come from three products instead of four:
+//   a_r w_r - a_i w_i = w_r (a_r + a_i) - a_i (w_r + w_i)
+//   a_r w_i + a_i w_r = w_r (a_r + a_i) + a_r (w_i - w_r)
+// (integer identities, so the rounded parts are unchanged).  The encoder's
+// operands stay below 2^62 in magnitude and |w_r|, |w_i| <= 2^62 with
+// w_r^2 + w_i^2 ~ 2^124, so every 64-bit sum fits and every product is below
+// 2^125.
 __device__ __forceinline__ void cmul_q62(i64 ar, i64 ai, longlong2 w, i64& re, i64& im) {
-  re = rnd62(sub128(mul_wide(ar, w.x), mul_wide(ai, w.y)));
-  im = rnd62(add128(mul_wide(ar, w.y), mul_wide(ai, w.x)));
+  const i128 k1 = mul_wide(ar + ai, w.x);
+  const i128 k2 = mul_wide(ar, w.y - w.x);
+  const i128 k3 = mul_wide(ai, w.x + w.y);
+  re = rnd62(sub128(k1, k3));
+  im = rnd62(add128(k1, k2));
 }
 
 // One radix-2 DIT butterfly of the stage with half-size hh = 2^lh on the

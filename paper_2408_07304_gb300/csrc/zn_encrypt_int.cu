@@ -22,8 +22,8 @@ namespace zn {
 // (poly 0), e0 (poly 1), e1 (poly 2); Zinc e1' (poly 0), e2' (poly 1).
 template <bool BGV, bool ZINC>
 __global__ void __launch_bounds__(256) k_prep_int(DevParams P, IntPrepArgs A) {
-  __shared__ u64 s_cdt[kCdt];
-  for (int j = threadIdx.x; j < kCdt; j += blockDim.x) s_cdt[j] = P.cdt[j];
+  __shared__ CdtTab s_cdt;
+  stage_cdt_tab(P.cdt, s_cdt);
   __syncthreads();
   const int N = 1 << P.log_n, n = N >> 1;
   const size_t b = blockIdx.x;
@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(256) k_prep_int(DevParams P, IntPrepArgs A) {
 #pragma unroll 1
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
     const uint4 w = zn_rand(A.seed, (unsigned)k, tag_a, ct);
-    const int a0 = cdt_search(w.x, w.y, s_cdt), a1 = cdt_search(w.z, w.w, s_cdt);
+    const int a0 = cdt_lookup(w.x, w.y, s_cdt), a1 = cdt_lookup(w.z, w.w, s_cdt);
     ea[k] = (int8_t)a0;
     ea[k + n] = (int8_t)a1;
     const i64 m0 = m ? mod_t(__ldg(m + k)) : 0, m1 = m ? mod_t(__ldg(m + k + n)) : 0;
@@ -52,8 +52,8 @@ __global__ void __launch_bounds__(256) k_prep_int(DevParams P, IntPrepArgs A) {
 #pragma unroll 1
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
     const uint4 w = zn_rand(A.seed, (unsigned)k, tag_b, ct);
-    eb[k] = (int8_t)cdt_search(w.x, w.y, s_cdt);
-    eb[k + n] = (int8_t)cdt_search(w.z, w.w, s_cdt);
+    eb[k] = (int8_t)cdt_lookup(w.x, w.y, s_cdt);
+    eb[k + n] = (int8_t)cdt_lookup(w.z, w.w, s_cdt);
   }
   if constexpr (!ZINC) {
     const unsigned tag_u = rand_tag(A.domain, 0, 0);

@@ -146,11 +146,11 @@ __device__ __forceinline__ void encrypt_half_unit_q(const DevParams& P, const En
   } else {
     load_me();
     auto st_0 = [&](int idx, u64 x) { c0[idx] = sum(__ldg(k0 + idx), x); };
-    ntt_chain<LOGH, LOGPER, HI, RELAX, decltype(st_0), KM, RAW, KM == 3>(sm, t, tw, tmul, q, st_0);
+    ntt_chain<LOGH, LOGPER, HI, RELAX, decltype(st_0), KM, RAW, KM == 3, 2>(sm, t, tw, tmul, q, st_0);
     __syncthreads();
     load_small(sp, std::false_type{});
     auto st_1 = [&](int idx, u64 x) { c1[idx] = sum(__ldg(k1 + idx), x); };
-    ntt_chain<LOGH, LOGPER, HI, RELAX, decltype(st_1), KM, RAW, KM == 3>(sm, t, tw, tmul, q, st_1);
+    ntt_chain<LOGH, LOGPER, HI, RELAX, decltype(st_1), KM, RAW, KM == 3, 2>(sm, t, tw, tmul, q, st_1);
   }
 }
 

@@ -141,15 +141,15 @@ __global__ void k_sample(DevParams P, int kind, u64 seed, unsigned domain, unsig
   }
 }
 
-// chi's CDT step on given uniforms, by the shared-memory binary search of the
-// encryption path (a test hook for threshold boundaries).
+// chi's CDT step on given uniforms, by the bucket-indexed threshold lookup of
+// the encryption path (a test hook for threshold boundaries).
 __global__ void k_chi_eval(DevParams P, const u64* __restrict__ u, uint32_t n, int* __restrict__ out) {
-  __shared__ u64 s_cdt[kCdt];
-  for (int j = threadIdx.x; j < kCdt; j += blockDim.x) s_cdt[j] = P.cdt[j];
+  __shared__ CdtTab s_cdt;
+  stage_cdt_tab(P.cdt, s_cdt);
   __syncthreads();
   for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < n; x += (size_t)gridDim.x * blockDim.x) {
     const u64 v = u[x];
-    out[x] = cdt_search((unsigned)v, (unsigned)(v >> 32), s_cdt);
+    out[x] = cdt_lookup((unsigned)v, (unsigned)(v >> 32), s_cdt);
   }
 }
 

@@ -119,14 +119,18 @@ def test_ntt_large_sampled(log_n, bits):
 
 
 def test_chi_table_search_boundaries():
-    # the binary search of the encryption path equals -19 + #{j : U >= T_j} at
-    # every threshold, one below and one above it, the extremes and random U
+    # the lookup of the encryption path (a bucket index over the top 8 bits of
+    # U, then the thresholds inside the bucket) equals -19 + #{j : U >= T_j}
+    # at every threshold, one below and one above it, at every bucket edge,
+    # the extremes and random U
     from oracle import sampler as OS
     ctx = gpu_ctx(10, (50,), 30)
     T = [int(t) for t in OS.cdt_thresholds()]
     us = {0, 1, 2 ** 64 - 1, 2 ** 63}
     for t in T:
         us.update({t - 1, t, t + 1})
+    for x in range(1, 256):
+        us.update({(x << 56) - 1, x << 56, (x << 56) + 1})
     us = sorted(v for v in us if 0 <= v < 2 ** 64)
     rnd = np.random.default_rng(12).integers(0, 2 ** 63, 5000, dtype=np.uint64) * np.uint64(2) + np.uint64(1)
     u = np.concatenate([np.array(us, dtype=np.uint64), rnd])
