@@ -1506,6 +1506,7 @@ int ckks_add(zn_ctx* c, const uint64_t* a, const uint64_t* b, uint32_t batch, ui
 struct zn_batch {
   int device;
   int sms;
+  int clusters;           // resident four-CTA clusters of the 2^15 kernel
   uint32_t n_prep, n_packets, n_small;   // packets: [rings up to 2^14 | 2^15]
   zn::JobDesc* d_jobs;
   zn::PrepUnit* d_units;
@@ -1595,11 +1596,13 @@ int zn_batch_create(const zn_job* jobs, uint32_t n_jobs, int device, zn_batch** 
     const zn_job& J = jobs[j];
     const uint32_t log_n = J.ctx->prm.log_n, L = J.ctx->L;
     for (uint32_t k = 0; k < J.count; ++k) units.push_back({j, k});
-    if (log_n >= 14) {                 // output halves, one per block
-      std::vector<zn::EncPacket>& list = log_n == 15 ? big : packets;
+    if (log_n == 15) {                 // one limb per four-CTA cluster
+      for (uint32_t i = 0; i < L; ++i)
+        for (uint32_t k = 0; k < J.count; ++k) big.push_back({j, k, (uint16_t)i, 1, 0});
+    } else if (log_n == 14) {          // output halves, one per block
       for (uint32_t i = 0; i < L; ++i)
         for (uint32_t k = 0; k < J.count; ++k)
-          for (uint8_t h = 0; h < 2; ++h) list.push_back({j, k, (uint16_t)i, 1, h});
+          for (uint8_t h = 0; h < 2; ++h) packets.push_back({j, k, (uint16_t)i, 1, h});
     } else {                           // 2^(13 - log_n) limbs per 256-thread block
       const uint32_t per = 1u << (13 - log_n);
       for (uint32_t i = 0; i < L; ++i)
@@ -1620,7 +1623,7 @@ int zn_batch_create(const zn_job* jobs, uint32_t n_jobs, int device, zn_batch** 
                                        cudaMemcpyHostToDevice) != cudaSuccess) ||
               (b->n_packets && cudaMemcpy(b->d_packets, packets.data(), sizeof(zn::EncPacket) * b->n_packets,
                                           cudaMemcpyHostToDevice) != cudaSuccess) ||
-              zn::batch_set_attributes() != cudaSuccess))
+              zn::batch_set_attributes() != cudaSuccess || zn::batch_quarter_clusters(&b->clusters) != cudaSuccess))
     rc = ZN_ECUDA;
   if (rc) {
     cudaGetLastError();
@@ -1636,10 +1639,10 @@ static int batch_enqueue(zn_batch* b, cudaStream_t st) {
   if (b->n_prep)
     ZN_CUDA(zn::launch_batch_prep(b->d_jobs, b->d_units, (int)b->n_prep, b->d_counters, b->sms, st));
   if (b->n_small)
-    ZN_CUDA(zn::launch_batch_encrypt(b->d_jobs, b->d_packets, (int)b->n_small, b->d_counters + 1, b->sms, false, st));
+    ZN_CUDA(zn::launch_batch_encrypt(b->d_jobs, b->d_packets, (int)b->n_small, b->d_counters + 1, b->sms, st));
   if (b->n_packets > b->n_small)
-    ZN_CUDA(zn::launch_batch_encrypt(b->d_jobs, b->d_packets + b->n_small, (int)(b->n_packets - b->n_small),
-                                     b->d_counters + 2, b->sms, true, st));
+    ZN_CUDA(zn::launch_batch_encrypt_quarter(b->d_jobs, b->d_packets + b->n_small, (int)(b->n_packets - b->n_small),
+                                             b->d_counters + 2, b->clusters, st));
   return ZN_OK;
 }
 

@@ -1,49 +1,11 @@
 // Mixed rings in persistent launches: k_batch_encrypt3 walks the work list of
-// rings up to 2^14 (three 256-thread blocks per SM) and k_batch_encrypt the
-// list of 2^15 rings (one 512-thread block per SM), across rings of
-// different degree, chain and mode.  The unit code lives in
-// zn_encrypt_unit.cuh.
+// rings up to 2^14 (three 256-thread blocks per SM), across rings of
+// different degree, chain and mode; the list of 2^15 rings runs on
+// persistent four-CTA clusters (zn_encrypt_quarter.cu).  The unit code lives
+// in zn_encrypt_unit.cuh.
 #include "zn_encrypt_unit.cuh"
 
 namespace zn {
-
-// -------------------------------------------------- mixed rings, persistent
-
-// Packet: one unit of a 2^15 job -- ciphertext b0 at prime `prime`, output
-// half `half` -- processed by one 512-thread block with 2^14 shared words.
-// __noinline__: each path is register-allocated on its own instead of the
-// kernel carrying the union of every path's registers.
-template <bool ZINC>
-__device__ __noinline__ void batch_half(const JobDesc& J, const EncPacket& pk, u64* sm) {
-  encrypt_half_unit<14, ZINC, 5>(J.P, J.E, pk.prime, pk.half, pk.b0, sm, threadIdx.x);
-}
-
-template <bool ZINC>
-__device__ __forceinline__ void batch_packet(const JobDesc& J, const EncPacket& pk, u64* sm) {
-  if (J.P.log_n == 15) batch_half<ZINC>(J, pk, sm);
-}
-
-// Persistent: one 512-thread block per SM; each block takes the next packet
-// from a global counter until the list is exhausted (no block waits for any
-// other).  The counter must be zero at launch.
-__global__ void __launch_bounds__(512, 1) k_batch_encrypt(const JobDesc* __restrict__ jobs,
-                                                          const EncPacket* __restrict__ packets, int n_packets,
-                                                          int* counter) {
-  extern __shared__ u64 sm[];
-  __shared__ int s_next;
-  for (;;) {
-    if (threadIdx.x == 0) s_next = atomicAdd(counter, 1);
-    __syncthreads();
-    const int p = s_next;
-    __syncthreads();
-    if (p >= n_packets) break;
-    const EncPacket pk = packets[p];
-    const JobDesc& J = jobs[pk.job];
-    if (J.zinc) batch_packet<true>(J, pk, sm);
-    else batch_packet<false>(J, pk, sm);
-    __syncthreads();
-  }
-}
 
 // --------------------------------- rings up to 2^14, three blocks per SM
 // 256-thread blocks with 80 registers and 64 KiB of shared memory, so that
@@ -95,19 +57,16 @@ __global__ void __launch_bounds__(256, 3) k_batch_encrypt3(const JobDesc* __rest
 }
 
 cudaError_t batch_encrypt_attributes() {
-  cudaError_t e =
-      cudaFuncSetAttribute(k_batch_encrypt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(u64) << 14));
+  cudaError_t e = batch_quarter_attributes();
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_batch_encrypt3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(u64) << 13));
 }
 
 // Capturable: the attributes are set beforehand by batch_set_attributes().
-// big = true: the 2^15 work list on one 512-thread block per SM; else the
-// list of smaller rings on three 256-thread blocks per SM.
+// The list of rings up to 2^14 on three 256-thread blocks per SM.
 cudaError_t launch_batch_encrypt(const JobDesc* jobs, const EncPacket* packets, int n_packets, int* counter, int sms,
-                                 bool big, cudaStream_t st) {
-  if (big) k_batch_encrypt<<<sms, 512, sizeof(u64) << 14, st>>>(jobs, packets, n_packets, counter);
-  else k_batch_encrypt3<<<3 * sms, 256, sizeof(u64) << 13, st>>>(jobs, packets, n_packets, counter);
+                                 cudaStream_t st) {
+  k_batch_encrypt3<<<3 * sms, 256, sizeof(u64) << 13, st>>>(jobs, packets, n_packets, counter);
   return cudaGetLastError();
 }
 

@@ -51,7 +51,7 @@ struct EncPacket {
   uint32_t b0;      // first ciphertext of the packet (within the job)
   uint16_t prime;
   uint8_t count;    // ciphertexts in the packet (units sharing one block)
-  uint8_t half;     // N = 2^14 and 2^15: which output half
+  uint8_t half;     // N = 2^14: which output half
 };
 struct PrepUnit {
   uint32_t job;
@@ -61,8 +61,14 @@ cudaError_t batch_set_attributes();
 cudaError_t batch_encrypt_attributes();
 cudaError_t launch_batch_prep(const JobDesc* jobs, const PrepUnit* units, int n_units, int* counter, int grid,
                               cudaStream_t st);
+// Rings up to 2^14 (three 256-thread blocks per SM).
 cudaError_t launch_batch_encrypt(const JobDesc* jobs, const EncPacket* packets, int n_packets, int* counter, int sms,
-                                 bool big, cudaStream_t st);
+                                 cudaStream_t st);
+// 2^15 rings: persistent four-CTA clusters, one limb per packet.
+cudaError_t batch_quarter_attributes();
+cudaError_t batch_quarter_clusters(int* clusters);
+cudaError_t launch_batch_encrypt_quarter(const JobDesc* jobs, const EncPacket* packets, int n_packets, int* counter,
+                                         int clusters, cudaStream_t st);
 
 // variant = 2 * kind + order.  order 0 = prime-major grid, 1 =
 // ciphertext-major grid (all blocks of a wave share one prime's twiddles and
