@@ -47,7 +47,9 @@ def _encrypt(ctx, pk, B, seed=5):
     return api.ckks_encrypt(ctx, pk, z, seed, torch.arange(B, dtype=torch.int64, device="cuda:0")), z
 
 
-@pytest.mark.parametrize("log_n,bits,ld", [(4, (30, 40), 20), (6, (31, 45, 60), 25), (10, (40, 40, 41), 30)])
+# N >= 1024 with 16-byte aligned buffers runs the bulk-copy tile kernels, smaller rings the per-word ones
+@pytest.mark.parametrize("log_n,bits,ld", [(4, (30, 40), 20), (6, (31, 45, 60), 25), (10, (40, 40, 41), 30),
+                                           (12, (36, 59, 20, 61), 30)])
 def test_pack_matches_definition_and_round_trips(log_n, bits, ld):
     ctx, pk = _ctx(log_n, bits, ld)
     ct, _ = _encrypt(ctx, pk, 3)
@@ -115,3 +117,27 @@ def test_unpack_latches_out_of_range_field():
     assert e.value.status == api.ZN_EINVAL
     assert torch.equal(api.zn_ct_unpack(ctx, packed), ct)              # the context stays usable
     api.zn_sync_status(ctx)
+
+
+def test_tile_and_word_kernels_agree():
+    # 16-byte aligned buffers take the bulk-copy tile kernels, buffers 8 bytes
+    # off the per-word ones: the same words and residues either way, on the
+    # benchmark chain (50- and 60-bit fields, words spanning residues)
+    w = workloads.WORKLOADS["throughput"]
+    ctx, pk = _ctx(w.log_n, w.bits, w.log2_delta)
+    ct, _ = _encrypt(ctx, pk, 5)
+    W = api.zn_ct_packed_words(ctx)
+    flat_c = torch.empty(ct.numel() + 1, dtype=torch.int64, device="cuda:0")
+    flat_p = torch.empty(5 * W + 1, dtype=torch.int64, device="cuda:0")
+    off_c = flat_c[1:].view(tuple(ct.shape))
+    off_p = flat_p[1:].view(5, W)
+    assert off_c.data_ptr() % 16 == 8 and off_p.data_ptr() % 16 == 8
+    off_c.copy_(ct)
+    aligned = api.zn_ct_pack(ctx, ct)
+    api.zn_ct_pack(ctx, off_c, out=off_p)
+    assert torch.equal(aligned, off_p)
+    back = torch.empty_like(ct)
+    api.zn_ct_unpack(ctx, aligned, out=back)
+    api.zn_ct_unpack(ctx, off_p, out=off_c)
+    api.zn_sync_status(ctx)
+    assert torch.equal(back, ct) and torch.equal(off_c, ct)
