@@ -182,19 +182,25 @@ __device__ __forceinline__ void unit(u64* sm, int t, unsigned j, const ulonglong
     ntt_chain<kLog, 5, kLog - 1, RELAX, std::remove_reference_t<decltype(store)>, kKm, true, true>(sm, t, tw, tmul,
                                                                                                  q, store);
   };
+  // the finished ciphertext words are written once and not read again here:
+  // streaming stores (evict first) leave L2 to u-hat, the keys and the inputs
   if constexpr (!ZINC) {
     const u64* k0s = o.k0s;
     const u64* k1s = o.k1s;
     auto st_u = [&](int idx, u64 uh) { c1[idx] = uh; };
     transform(gu, st_u);
-    auto st_0 = [&](int idx, u64 x) { c0[idx] = sum(mul_shoup(c1[idx], __ldg(k0 + idx), __ldg(k0s + idx), q), x); };
+    auto st_0 = [&](int idx, u64 x) {
+      __stcs(c0 + idx, sum(mul_shoup(c1[idx], __ldg(k0 + idx), __ldg(k0s + idx), q), x));
+    };
     transform(g0, st_0);
-    auto st_1 = [&](int idx, u64 x) { c1[idx] = sum(mul_shoup(c1[idx], __ldg(k1 + idx), __ldg(k1s + idx), q), x); };
+    auto st_1 = [&](int idx, u64 x) {
+      __stcs(c1 + idx, sum(mul_shoup(c1[idx], __ldg(k1 + idx), __ldg(k1s + idx), q), x));
+    };
     transform(g1, st_1);
   } else {
-    auto st_0 = [&](int idx, u64 x) { c0[idx] = sum(__ldg(k0 + idx), x); };
+    auto st_0 = [&](int idx, u64 x) { __stcs(c0 + idx, sum(__ldg(k0 + idx), x)); };
     transform(g0, st_0);
-    auto st_1 = [&](int idx, u64 x) { c1[idx] = sum(__ldg(k1 + idx), x); };
+    auto st_1 = [&](int idx, u64 x) { __stcs(c1 + idx, sum(__ldg(k1 + idx), x)); };
     transform(g1, st_1);
   }
 }
