@@ -1507,6 +1507,8 @@ struct zn_batch {
   int device;
   int sms;
   int clusters;           // resident four-CTA clusters of the 2^15 kernel
+  size_t prep_smem;       // dynamic shared memory of the persistent prep: 4N of the largest ring
+  int prep_grid;          // its blocks: SMs x the blocks of that size that fit on an SM
   uint32_t n_prep, n_packets, n_small;   // packets: [rings up to 2^14 | 2^15]
   zn::JobDesc* d_jobs;
   zn::PrepUnit* d_units;
@@ -1625,6 +1627,14 @@ int zn_batch_create(const zn_job* jobs, uint32_t n_jobs, int device, zn_batch** 
                                           cudaMemcpyHostToDevice) != cudaSuccess) ||
               zn::batch_set_attributes() != cudaSuccess || zn::batch_quarter_clusters(&b->clusters) != cudaSuccess))
     rc = ZN_ECUDA;
+  if (!rc) {
+    uint32_t max_n = 0;
+    for (uint32_t j = 0; j < n_jobs; ++j) max_n = std::max(max_n, jobs[j].ctx->n);
+    b->prep_smem = 4 * (size_t)max_n;
+    int per_sm = 1;
+    if (zn::batch_prep_blocks_per_sm(b->prep_smem, &per_sm) != cudaSuccess) rc = ZN_ECUDA;
+    b->prep_grid = b->sms * per_sm;
+  }
   if (rc) {
     cudaGetLastError();
     zn_batch_destroy(b);
@@ -1637,7 +1647,8 @@ int zn_batch_create(const zn_job* jobs, uint32_t n_jobs, int device, zn_batch** 
 static int batch_enqueue(zn_batch* b, cudaStream_t st) {
   ZN_CUDA(cudaMemsetAsync(b->d_counters, 0, 3 * sizeof(int), st));
   if (b->n_prep)
-    ZN_CUDA(zn::launch_batch_prep(b->d_jobs, b->d_units, (int)b->n_prep, b->d_counters, b->sms, st));
+    ZN_CUDA(zn::launch_batch_prep(b->d_jobs, b->d_units, (int)b->n_prep, b->d_counters, b->prep_grid, b->prep_smem,
+                                  st));
   if (b->n_small)
     ZN_CUDA(zn::launch_batch_encrypt(b->d_jobs, b->d_packets, (int)b->n_small, b->d_counters + 1, b->sms, st));
   if (b->n_packets > b->n_small)

@@ -218,10 +218,11 @@ __global__ void __launch_bounds__(512, 2) k_prep_smem(DevParams P, PrepArgs A) {
   prep_one<ZINC, MS>(P, A, blockIdx.x, smi, smi + h, &s_cdt);
 }
 
-// Persistent prep over a mixed work list: one 512-thread block per SM takes
-// the next ciphertext from a global counter (zero at launch); the FFT of
-// rings up to 2^15 fits in the block's 128 KiB of shared memory.
-__global__ void __launch_bounds__(512, 1) k_batch_prep(const JobDesc* __restrict__ jobs,
+// Persistent prep over a mixed work list: 512-thread blocks take the next
+// ciphertext from a global counter (zero at launch); each holds the encoder
+// FFT of the batch's largest ring (4N bytes of shared memory: two blocks per
+// SM up to 2^14, one at 2^15).
+__global__ void __launch_bounds__(512, 2) k_batch_prep(const JobDesc* __restrict__ jobs,
                                                        const PrepUnit* __restrict__ units, int n_units, int* counter) {
   extern __shared__ i64 smi[];
   __shared__ int s_next;
@@ -435,9 +436,18 @@ cudaError_t launch_prep_ms(const DevParams& P, const PrepArgs& A, uint32_t batch
 }
 
 cudaError_t launch_batch_prep(const JobDesc* jobs, const PrepUnit* units, int n_units, int* counter, int grid,
-                              cudaStream_t st) {
-  k_batch_prep<<<grid, 512, sizeof(i64) << 14, st>>>(jobs, units, n_units, counter);
+                              size_t smem, cudaStream_t st) {
+  k_batch_prep<<<grid, 512, smem, st>>>(jobs, units, n_units, counter);
   return cudaGetLastError();
+}
+
+// Blocks of the persistent prep that fit on one SM with `smem` bytes of
+// dynamic shared memory (the attribute must be set first); at least 1.
+cudaError_t batch_prep_blocks_per_sm(size_t smem, int* blocks) {
+  int n = 0;
+  const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_prep, 512, smem);
+  *blocks = n > 0 ? n : 1;
+  return e;
 }
 
 cudaError_t batch_set_attributes() {

@@ -60,7 +60,8 @@ struct PrepUnit {
 cudaError_t batch_set_attributes();
 cudaError_t batch_encrypt_attributes();
 cudaError_t launch_batch_prep(const JobDesc* jobs, const PrepUnit* units, int n_units, int* counter, int grid,
-                              cudaStream_t st);
+                              size_t smem, cudaStream_t st);
+cudaError_t batch_prep_blocks_per_sm(size_t smem, int* blocks);
 // Rings up to 2^14 (three 256-thread blocks per SM).
 cudaError_t launch_batch_encrypt(const JobDesc* jobs, const EncPacket* packets, int n_packets, int* counter, int sms,
                                  cudaStream_t st);
