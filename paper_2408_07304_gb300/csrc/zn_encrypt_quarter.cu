@@ -17,9 +17,11 @@ struct MeVal {
   __device__ __forceinline__ u64 operator()(int k) const { return reduce_biased((u64)__ldg(me + k), q, mu, moff); }
 };
 
-template <bool ZINC, bool RELAX>
+// Park: quarter::ParkTmem, or quarter::ParkOut (its pointer unused: u-hat
+// goes to this unit's c1 words).
+template <bool ZINC, bool RELAX, class Park>
 __device__ __forceinline__ void encrypt_quarter_unit_q(const DevParams& P, const EncArgs& A, int i, unsigned j,
-                                                       size_t b, u64* sm, int t) {
+                                                       size_t b, u64* sm, int t, const Park& park) {
   using namespace quarter;
   const int L = P.L;
   const u64 q = P.q[i];
@@ -39,7 +41,8 @@ __device__ __forceinline__ void encrypt_quarter_unit_q(const DevParams& P, const
   if constexpr (!ZINC) {
     auto g_u = [&] { gen_i8<RELAX, true>(sm, t, j, sp, tw, q); };
     auto g_e1 = [&] { gen_i8<RELAX, false>(sm, t, j, sp + kN, tw, q); };
-    unit<false, RELAX>(sm, t, j, tw, q, o, g_u, g_me, g_e1);
+    if constexpr (std::is_same_v<Park, ParkOut>) unit<false, RELAX>(sm, t, j, tw, q, o, g_u, g_me, g_e1);
+    else unit<false, RELAX>(sm, t, j, tw, q, o, g_u, g_me, g_e1, park);
   } else {
     auto g_e2 = [&] { gen_i8<RELAX, false>(sm, t, j, sp, tw, q); };
     unit<true, RELAX>(sm, t, j, tw, q, o, g_me, g_me, g_e2);
@@ -47,7 +50,7 @@ __device__ __forceinline__ void encrypt_quarter_unit_q(const DevParams& P, const
 }
 
 // grid (4L, B), or (4B, L) when A.swap; the CTA of cluster rank j owns
-// output quarter j
+// output quarter j.  Vanilla parks u-hat in tensor memory.
 template <bool ZINC>
 __global__ void __launch_bounds__(quarter::kT, 3) k_encrypt_quarter(DevParams P, EncArgs A) {
   extern __shared__ u64 sm[];
@@ -56,17 +59,31 @@ __global__ void __launch_bounds__(quarter::kT, 3) k_encrypt_quarter(DevParams P,
   const size_t b = A.swap ? (size_t)(blockIdx.x >> 2) : blockIdx.y;
   // the relaxed/Harvey choice is uniform per unit, so all four CTAs of a
   // cluster take the same branch and meet at the same barriers
-  if (P.q[i] < kRelaxLimit) encrypt_quarter_unit_q<ZINC, true>(P, A, i, j, b, sm, threadIdx.x);
-  else encrypt_quarter_unit_q<ZINC, false>(P, A, i, j, b, sm, threadIdx.x);
+  const bool relax = P.q[i] < kRelaxLimit;
+  if constexpr (ZINC) {
+    const quarter::ParkOut park{nullptr};
+    if (relax) encrypt_quarter_unit_q<true, true>(P, A, i, j, b, sm, threadIdx.x, park);
+    else encrypt_quarter_unit_q<true, false>(P, A, i, j, b, sm, threadIdx.x, park);
+  } else {
+    __shared__ unsigned s_tmem;
+    const tmem::Scope tm(&s_tmem);
+    const quarter::ParkTmem park{tmem::thread_base(tm.base)};
+    if (relax) encrypt_quarter_unit_q<false, true>(P, A, i, j, b, sm, threadIdx.x, park);
+    else encrypt_quarter_unit_q<false, false>(P, A, i, j, b, sm, threadIdx.x, park);
+    tm.release();
+  }
 }
 
 // ---------------------------------------- persistent mixed-ring launch
 // Packet: one limb (ciphertext b0, prime `prime`) of a 2^15 job, run by one
 // four-CTA cluster.  Inlined: separate register allocation per path
 // (__noinline__) measured 3 % slower.
+// Vanilla parks u-hat in the c1 output words here: parking it in tensor
+// memory, as the single-ring kernel does, measured 38 % slower in this
+// kernel (more spills around the four inlined unit variants).
 template <bool ZINC, bool RELAX>
 __device__ __forceinline__ void batch_quarter(const JobDesc& J, const EncPacket& pk, unsigned j, u64* sm) {
-  encrypt_quarter_unit_q<ZINC, RELAX>(J.P, J.E, pk.prime, j, pk.b0, sm, threadIdx.x);
+  encrypt_quarter_unit_q<ZINC, RELAX>(J.P, J.E, pk.prime, j, pk.b0, sm, threadIdx.x, quarter::ParkOut{nullptr});
 }
 
 __device__ __forceinline__ int ld_cluster_s32(unsigned addr) {

@@ -15,6 +15,7 @@
 #include <type_traits>
 
 #include "zn_encrypt_fn.cuh"
+#include "zn_tmem.cuh"
 
 namespace zn {
 namespace quarter {
@@ -162,9 +163,23 @@ __device__ __forceinline__ void gen_i8(u64* sm, int t, unsigned j, const int8_t*
 // parks u-hat unreduced in c1 (one word per coefficient; Shoup's product
 // takes any 64-bit input) and each later epilogue forms its own key product;
 // the same thread reads and rewrites each index.
-template <bool ZINC, bool RELAX, class GU, class G0, class G1>
+//
+// Where vanilla parks u-hat between its transform and the two later
+// epilogues: in the c1 output words (ParkOut), or in tensor memory
+// (ParkTmem, zn_tmem.cuh: the staged epilogue hands thread t the indices
+// t + 256 i, i < 32, and i picks the columns).
+struct ParkOut {
+  u64* c1;
+  __device__ __forceinline__ void put(int idx, u64 v) const { c1[idx] = v; }
+  __device__ __forceinline__ u64 get(int idx) const { return c1[idx]; }
+  __device__ __forceinline__ void done() const {}
+};
+using ParkTmem = tmem::Park;
+static_assert(kT == 256 && kQ == 32 * kT, "ParkTmem: 32 outputs per thread, index t + 256 i");
+
+template <bool ZINC, bool RELAX, class GU, class G0, class G1, class Park>
 __device__ __forceinline__ void unit(u64* sm, int t, unsigned j, const ulonglong2* tw, u64 q, const FnLimb& o,
-                                     const GU& gu, const G0& g0, const G1& g1) {
+                                     const GU& gu, const G0& g0, const G1& g1, const Park& park) {
   static_assert(4 + 2 * 12 + 2 <= 32, "relaxed sums must stay below 32q");
   static_assert(NttShape<kLog, 5>::T == kT, "256 threads per quarter");
   const int tmul = 4 + (int)j;
@@ -187,14 +202,15 @@ __device__ __forceinline__ void unit(u64* sm, int t, unsigned j, const ulonglong
   if constexpr (!ZINC) {
     const u64* k0s = o.k0s;
     const u64* k1s = o.k1s;
-    auto st_u = [&](int idx, u64 uh) { c1[idx] = uh; };
+    auto st_u = [&](int idx, u64 uh) { park.put(idx, uh); };
     transform(gu, st_u);
+    park.done();
     auto st_0 = [&](int idx, u64 x) {
-      __stcs(c0 + idx, sum(mul_shoup(c1[idx], __ldg(k0 + idx), __ldg(k0s + idx), q), x));
+      __stcs(c0 + idx, sum(mul_shoup(park.get(idx), __ldg(k0 + idx), __ldg(k0s + idx), q), x));
     };
     transform(g0, st_0);
     auto st_1 = [&](int idx, u64 x) {
-      __stcs(c1 + idx, sum(mul_shoup(c1[idx], __ldg(k1 + idx), __ldg(k1s + idx), q), x));
+      __stcs(c1 + idx, sum(mul_shoup(park.get(idx), __ldg(k1 + idx), __ldg(k1s + idx), q), x));
     };
     transform(g1, st_1);
   } else {
@@ -203,6 +219,13 @@ __device__ __forceinline__ void unit(u64* sm, int t, unsigned j, const ulonglong
     auto st_1 = [&](int idx, u64 x) { __stcs(c1 + idx, sum(__ldg(k1 + idx), x)); };
     transform(g1, st_1);
   }
+}
+
+// u-hat parked in the c1 output words.
+template <bool ZINC, bool RELAX, class GU, class G0, class G1>
+__device__ __forceinline__ void unit(u64* sm, int t, unsigned j, const ulonglong2* tw, u64 q, const FnLimb& o,
+                                     const GU& gu, const G0& g0, const G1& g1) {
+  unit<ZINC, RELAX>(sm, t, j, tw, q, o, gu, g0, g1, ParkOut{o.c1});
 }
 
 // Launch a quarter kernel: clusters of four consecutive CTAs along x.
