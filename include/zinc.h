@@ -508,6 +508,16 @@ int zn_probe_butterfly(int device, double* butterflies_per_s);
  * a transform's final reduction would do. */
 int zn_probe_butterfly_relaxed(int device, double* butterflies_per_s);
 
+/* Diagnostic (no counterpart in the paper): the device-side timeout path of
+ * the bounded waits (the packed-serialization tiles wait on an mbarrier for
+ * their bulk copy).  One block waits, with the same code, on a barrier that
+ * nothing arrives on, polling at most `tries` times (1 <= tries <= 2^20; the
+ * tiles use 2^20), then latches the timeout bit of ctx's status word and
+ * returns: the next zn_sync_status(ctx, stream) reports ZN_ETIMEOUT and the
+ * context stays usable.  Asynchronous on `stream`; ZN_EINVAL for a null ctx
+ * or tries out of range. */
+int zn_probe_wait_timeout(zn_ctx* ctx, uint32_t tries, void* stream);
+
 /* Host-side fault injection for tests of the callers' error paths (no
  * counterpart in the paper): the next `count` per-call scratch allocations,
  * in any context and on any thread, fail as if the device memory pool were

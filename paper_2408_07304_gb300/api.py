@@ -106,6 +106,7 @@ _SIGS = {
     "zn_probe_butterfly": (_i32, [_i32, _vp]),
     "zn_probe_butterfly_relaxed": (_i32, [_i32, _vp]),
     "zn_inject_alloc_failures": (_i32, [_i32]),
+    "zn_probe_wait_timeout": (_i32, [_vp, _u32, _vp]),
     "zn_timing_enable": (_i32, [_vp, _i32]),
     "zn_timing_read": (_i32, [_vp, _i32, _vp, _vp]),
     "zn_host_primes": (_i32, [_u32, _vp, _u32, _vp]),
@@ -822,6 +823,12 @@ def zn_probe_butterfly_relaxed(device=0):
     r = ctypes.c_double()
     _check(lib().zn_probe_butterfly_relaxed(device, ctypes.byref(r)), "zn_probe_butterfly_relaxed")
     return r.value
+
+
+def zn_probe_wait_timeout(ctx, tries, stream=None):
+    """Run the bounded device wait on a barrier nothing arrives on (at most
+    `tries` polls): the next zn_sync_status reports ZN_ETIMEOUT."""
+    _check(lib().zn_probe_wait_timeout(ctx.handle, int(tries), _stream(stream)), "zn_probe_wait_timeout")
 
 
 def zn_inject_alloc_failures(count):

@@ -1949,6 +1949,13 @@ int zn_probe_butterfly_relaxed(int device, double* per_s) {
   return zn::probe_butterfly(sms, per_s, true) == cudaSuccess ? ZN_OK : ZN_ECUDA;
 }
 
+int zn_probe_wait_timeout(zn_ctx* c, uint32_t tries, void* stream) {
+  if (!c || tries == 0 || tries > (1u << 20)) return ZN_EINVAL;
+  DeviceGuard g(c->device);
+  ZN_CUDA(zn::launch_wait_probe(c->dp, tries, S(stream)));
+  return ZN_OK;
+}
+
 int zn_inject_alloc_failures(int count) {
   if (count < 0) return ZN_EINVAL;
   g_alloc_faults.store(count, std::memory_order_relaxed);

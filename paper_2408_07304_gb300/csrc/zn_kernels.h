@@ -231,6 +231,9 @@ struct PackArgs {
 };
 cudaError_t launch_ct_pack(const DevParams& P, const PackArgs& A, uint32_t batch, cudaStream_t st);
 cudaError_t launch_ct_unpack(const DevParams& P, const PackArgs& A, uint32_t batch, cudaStream_t st);
+// One block waits on a barrier nothing arrives on, with the tiles' bounded
+// wait limited to `tries` polls: latches kStatusTimeout.
+cudaError_t launch_wait_probe(const DevParams& P, unsigned tries, cudaStream_t st);
 
 // pk0 += (t - 1) e-hat (per prime, NTT form) and its Shoup companions: Gen's key becomes BGV's.
 cudaError_t launch_bgv_key(const DevParams& P, u64 t, const u64* ehat, u64* pk, u64* pks, cudaStream_t st);

@@ -78,10 +78,13 @@ __device__ __forceinline__ void tile_load(void* dst, const void* src, unsigned b
                ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
 }
 
-// Waits for phase 0 of the barrier, at most about a second (each try_wait
-// also suspends for a while); false if it gave up.
-__device__ __forceinline__ bool tile_wait(u64* bar) {
-  for (unsigned it = 0; it < (1u << 20); ++it) {
+// Waits for phase 0 of the barrier, at most `tries` polls (the default:
+// about a second, each try_wait also suspending for a while); false if it
+// gave up.
+constexpr unsigned kTileWaitTries = 1u << 20;
+
+__device__ __forceinline__ bool tile_wait(u64* bar, unsigned tries = kTileWaitTries) {
+  for (unsigned it = 0; it < tries; ++it) {
     unsigned ok;
     asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
                  "selp.u32 %0, 1, 0, p;\n\t}"
@@ -93,11 +96,22 @@ __device__ __forceinline__ bool tile_wait(u64* bar) {
 
 // A wait that gave up latches kStatusTimeout, waits once more (bounded) for
 // the copy still in flight, and the block returns without writing.
-__device__ __forceinline__ bool tile_arrived(const DevParams& P, u64* bar) {
-  if (tile_wait(bar)) return true;
+__device__ __forceinline__ bool tile_arrived(const DevParams& P, u64* bar, unsigned tries = kTileWaitTries) {
+  if (tile_wait(bar, tries)) return true;
   if (threadIdx.x == 0) atomicOr(P.status, kStatusTimeout);
-  tile_wait(bar);
+  tile_wait(bar, tries);
   return false;
+}
+
+// The timeout path on its own: a barrier that nothing arrives on (no copy
+// is issued), waited on by the same code as the tiles with a limit of
+// `tries` polls; the wait gives up, latches kStatusTimeout and the block
+// returns.
+__global__ void __launch_bounds__(32) k_wait_probe(DevParams P, unsigned tries) {
+  __shared__ __align__(8) u64 s_bar;
+  if (threadIdx.x == 0) mbar_init(&s_bar);
+  __syncthreads();
+  tile_arrived(P, &s_bar, tries);
 }
 
 // grid (N / 1024, limbs); tile x of limb y = (b, c, i)
@@ -185,6 +199,11 @@ cudaError_t launch_ct_pack(const DevParams& P, const PackArgs& A, uint32_t batch
 
 cudaError_t launch_ct_unpack(const DevParams& P, const PackArgs& A, uint32_t batch, cudaStream_t st) {
   return batch ? launch_pack_dir(P, A, batch, false, st) : cudaSuccess;
+}
+
+cudaError_t launch_wait_probe(const DevParams& P, unsigned tries, cudaStream_t st) {
+  k_wait_probe<<<1, 32, 0, st>>>(P, tries);
+  return cudaGetLastError();
 }
 
 }  // namespace zn

@@ -4,7 +4,10 @@ call returns ZN_ENOMEM before launching anything and leaves its context
 usable -- the next call gives the same ciphertexts as an undisturbed one --
 and the serving loop puts a refused batch back at the head of its queue,
 retries it, and completes every request bit-identically; when the retries
-run out with nothing in flight, only that batch's requests fail.
+run out with nothing in flight, only that batch's requests fail.  The
+device-side bounded wait (the packed-serialization tiles' mbarrier wait) is
+made to run out on a barrier that nothing arrives on: it latches
+ZN_ETIMEOUT in the context's status word and the context stays usable.
 """
 import numpy as np
 import pytest
@@ -104,3 +107,27 @@ def test_handles_released_after_their_context_leave_no_error():
     x = torch.arange(1 << 20, dtype=torch.float64, device="cuda:0")
     assert float(x.sum()) == (1 << 20) * ((1 << 20) - 1) / 2
     torch.cuda.synchronize()
+
+
+def test_bounded_wait_times_out_and_context_stays_usable():
+    ctx, sk, pk = _ctx()
+    z = torch.tensor(np.random.default_rng(1).uniform(-1, 1, (2, 64)), device="cuda:0")
+    idx = torch.arange(2, dtype=torch.int64, device="cuda:0")
+    ref = api.ckks_encrypt(ctx, pk, z, 7, idx)
+    packed = api.zn_ct_pack(ctx, ref)
+    api.zn_sync_status(ctx)
+    for tries in (1, 1024):
+        api.zn_probe_wait_timeout(ctx, tries)
+        with pytest.raises(api.ZincError) as e:
+            api.zn_sync_status(ctx)
+        assert e.value.status == api.ZN_ETIMEOUT
+        api.zn_sync_status(ctx)              # read and cleared
+    # the context, its stream and the tiles' own waits work as before
+    assert torch.equal(api.ckks_encrypt(ctx, pk, z, 7, idx), ref)
+    assert torch.equal(api.zn_ct_unpack(ctx, api.zn_ct_pack(ctx, ref)), ref)
+    assert torch.equal(api.zn_ct_pack(ctx, ref), packed)
+    api.zn_sync_status(ctx)
+    for bad in (0, (1 << 20) + 1):
+        with pytest.raises(api.ZincError) as e:
+            api.zn_probe_wait_timeout(ctx, bad)
+        assert e.value.status == api.ZN_EINVAL
