@@ -35,15 +35,18 @@ UNIT = "encryptions/s"
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per ciphertext
-# of the N = 2^14 encrypt kernels, from a separate ncu capture of a
-# 512-ciphertext launch of the throughput workload (not measured by this run),
-# keyed by the kernel it was taken on and scaled to the launch size timed here
-# (a 256-ciphertext capture gave 2.7 % less per ciphertext: part of a smaller
+# of the encrypt kernels, from separate ncu captures (not measured by this
+# run): a 512-ciphertext launch of the throughput workload (N = 2^14) and a
+# 64-ciphertext launch of the paper-shaped one (N = 2^15), keyed by the kernel
+# each was taken on and scaled to the launch size timed here (a 256-ciphertext
+# capture at N = 2^14 gave 2.7 % less per ciphertext: part of a smaller
 # launch's output is still in L2 when it ends).  Valid only while that kernel
 # is unchanged and selected.
 NCU_TRAFFIC_PER_CT = {
     ("throughput", "k_encrypt_half<13,vanilla,radix-8,3 blocks/SM>"): (105.432832e6 + 1103.018e6) / 512,
     ("throughput", "k_encrypt_half<13,Zinc,radix-8,3 blocks/SM>"): (79.886848e6 + 1047.185e6) / 512,
+    ("paper", "k_encrypt_quarter<vanilla,4-CTA cluster,radix-8,3 blocks/SM>"): (51.651072e6 + 482.746624e6) / 64,
+    ("paper", "k_encrypt_quarter<Zinc,4-CTA cluster,radix-8,3 blocks/SM>"): (37.274112e6 + 479.471616e6) / 64,
 }
 # Busy fraction of the SM's integer multiply-add pipe (ncu
 # sm__pipe_fmaheavy_cycles_active, which is also the kernel's
@@ -51,6 +54,8 @@ NCU_TRAFFIC_PER_CT = {
 NCU_INT_PIPE = {
     ("throughput", "k_encrypt_half<13,vanilla,radix-8,3 blocks/SM>"): 0.7478,
     ("throughput", "k_encrypt_half<13,Zinc,radix-8,3 blocks/SM>"): 0.7264,
+    ("paper", "k_encrypt_quarter<vanilla,4-CTA cluster,radix-8,3 blocks/SM>"): 0.7405,
+    ("paper", "k_encrypt_quarter<Zinc,4-CTA cluster,radix-8,3 blocks/SM>"): 0.7111,
 }
 VARIANT_KERNEL = {6: "k_encrypt_half<13,{mode},radix-8,3 blocks/SM>",
                   7: "k_encrypt_half<13,{mode},radix-8,3 blocks/SM,ciphertext-major>"}
@@ -337,9 +342,9 @@ def run_ours(args, w):
     int_pipe = NCU_INT_PIPE.get((w.name, kname.format(mode="vanilla")))
     roofline = {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": hbm_achieved / hbm_peak, "traffic": traffic,
-                "traffic_source": "ncu capture of this kernel on a 512-ciphertext launch, taken separately "
-                                  "(not by this run), scaled per ciphertext to this launch size; null when the "
-                                  "selected kernel has none",
+                "traffic_source": "ncu capture of this kernel (512 ciphertexts at N=2^14, 64 at the paper's "
+                                  "parameters), taken separately (not by this run), scaled per ciphertext to this "
+                                  "launch size; null when the selected kernel has none",
                 "traffic_over_algorithmic": (traffic / alg_bytes) if traffic else None,
                 "algorithmic_bytes_per_launch": alg_bytes, "ciphertexts_per_launch": chunk_cts,
                 "algorithmic_bytes_per_ct": per_ct_bytes,
@@ -362,7 +367,7 @@ def run_ours(args, w):
                         "zinc_kernel_probe_frac": bfly_z / (kz_avg / 1e3) / 1e9 / probe,
                         "int_pipe": {"pipe": "fmaheavy (32-bit integer multiply-add)", "busy_frac": int_pipe,
                                      "source": "ncu sm__pipe_fmaheavy_cycles_active of the same capture as "
-                                               "traffic (512-ciphertext launch, not this run)"}}}
+                                               "traffic (not this run)"}}}
 
     # ---- the same step through the mixed-ring persistent path (one CUDA-graph
     # launch per step: a vanilla job and a Zinc job over the batch)
