@@ -64,8 +64,17 @@ struct FnLimb {
   const int8_t* u;  // vanilla: u, int8 [N]
 };
 
+// Write a finished ciphertext word: plain, or (STREAM) with a streaming
+// (evict-first) store, which leaves L2 to the words the epilogues still
+// read back.
+template <bool STREAM>
+__device__ __forceinline__ void put_ct(u64* p, u64 v) {
+  if constexpr (STREAM) __stcs(p, v);
+  else *p = v;
+}
+
 // Full transform (N = 2^LOGN <= 2^14).
-template <int LOGN, int LOGPER, bool RELAX, int KM, bool ZINC, class V0, class V1>
+template <int LOGN, int LOGPER, bool RELAX, int KM, bool ZINC, bool STREAM, class V0, class V1>
 __device__ __forceinline__ void fn_unit_q(const ulonglong2* tw, u64 q, const FnLimb& o, const V0& v0, const V1& v1,
                                           u64* sm, int t) {
   using S = NttShape<LOGN, LOGPER>;
@@ -91,19 +100,19 @@ __device__ __forceinline__ void fn_unit_q(const ulonglong2* tw, u64 q, const FnL
   }
   if constexpr (TOP) gen_val_top<LOGN, KM, RELAX>(sm, t, S::T, v0, q, __ldg(tw + 1));
   else gen_val<LOGN, KM>(sm, t, S::T, v0);
-  auto st_0 = [&](int idx, u64 x) { c0[idx] = reduce_sum<RELAX>((ZINC ? __ldg(k0 + idx) : c0[idx]) + x, q); };
+  auto st_0 = [&](int idx, u64 x) { put_ct<STREAM>(c0 + idx, reduce_sum<RELAX>((ZINC ? __ldg(k0 + idx) : c0[idx]) + x, q)); };
   ntt_chain<LOGN, LOGPER, HI, RELAX, decltype(st_0), KM, true, KM == 3>(sm, t, tw, 1, q, st_0);
   __syncthreads();
   if constexpr (TOP) gen_val_top<LOGN, KM, RELAX>(sm, t, S::T, v1, q, __ldg(tw + 1));
   else gen_val<LOGN, KM>(sm, t, S::T, v1);
-  auto st_1 = [&](int idx, u64 x) { c1[idx] = reduce_sum<RELAX>((ZINC ? __ldg(k1 + idx) : c1[idx]) + x, q); };
+  auto st_1 = [&](int idx, u64 x) { put_ct<STREAM>(c1 + idx, reduce_sum<RELAX>((ZINC ? __ldg(k1 + idx) : c1[idx]) + x, q)); };
   ntt_chain<LOGN, LOGPER, HI, RELAX, decltype(st_1), KM, true, KM == 3>(sm, t, tw, 1, q, st_1);
 }
 
 // Output half h, N = 2^(LOGH+1): the generators run the first stage
 // (distance N/2) for the half; o's outputs and keys point at the half, o.u
 // and the functors index the whole ring.
-template <int LOGH, int LOGPER, bool RELAX, int KM, bool ZINC, class V0, class V1>
+template <int LOGH, int LOGPER, bool RELAX, int KM, bool ZINC, bool STREAM, class V0, class V1>
 __device__ __forceinline__ void fn_half_unit_q(const ulonglong2* tw, u64 q, int h, const FnLimb& o, const V0& v0,
                                                const V1& v1, u64* sm, int t) {
   using S = NttShape<LOGH, LOGPER>;
@@ -131,12 +140,12 @@ __device__ __forceinline__ void fn_half_unit_q(const ulonglong2* tw, u64 q, int 
   }
   if constexpr (TOP) gen_val_half2<LOGH, KM, RELAX>(sm, t, S::T, h, v0, q, w1p, __ldg(tw + tmul));
   else gen_val_half<LOGH, KM>(sm, t, S::T, h, v0, q, w1p.x, w1p.y);
-  auto st_0 = [&](int idx, u64 x) { c0[idx] = sum(ZINC ? __ldg(k0 + idx) : c0[idx], x); };
+  auto st_0 = [&](int idx, u64 x) { put_ct<STREAM>(c0 + idx, sum(ZINC ? __ldg(k0 + idx) : c0[idx], x)); };
   ntt_chain<LOGH, LOGPER, HI, RELAX, decltype(st_0), KM, RAW, KM == 3>(sm, t, tw, tmul, q, st_0);
   __syncthreads();
   if constexpr (TOP) gen_val_half2<LOGH, KM, RELAX>(sm, t, S::T, h, v1, q, w1p, __ldg(tw + tmul));
   else gen_val_half<LOGH, KM>(sm, t, S::T, h, v1, q, w1p.x, w1p.y);
-  auto st_1 = [&](int idx, u64 x) { c1[idx] = sum(ZINC ? __ldg(k1 + idx) : c1[idx], x); };
+  auto st_1 = [&](int idx, u64 x) { put_ct<STREAM>(c1 + idx, sum(ZINC ? __ldg(k1 + idx) : c1[idx], x)); };
   ntt_chain<LOGH, LOGPER, HI, RELAX, decltype(st_1), KM, RAW, KM == 3>(sm, t, tw, tmul, q, st_1);
 }
 

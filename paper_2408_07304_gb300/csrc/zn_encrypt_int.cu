@@ -123,7 +123,7 @@ __device__ __forceinline__ void int_unit_q(const DevParams& P, const IntArgs& A,
   IntV0<BGV> v0;
   IntV1<BGV> v1;
   int_inputs<BGV, ZINC>(P, A, i, b, N, v0, v1);
-  fn_unit_q<LOGN, LOGPER, RELAX, KM, ZINC>(P.twp + (size_t)i * N, P.q[i], o, v0, v1, sm, t);
+  fn_unit_q<LOGN, LOGPER, RELAX, KM, ZINC, false>(P.twp + (size_t)i * N, P.q[i], o, v0, v1, sm, t);
 }
 
 template <int LOGH, int LOGPER, bool RELAX, int KM, bool BGV, bool ZINC>
@@ -143,7 +143,7 @@ __device__ __forceinline__ void int_half_unit_q(const DevParams& P, const IntArg
   IntV0<BGV> v0;
   IntV1<BGV> v1;
   int_inputs<BGV, ZINC>(P, A, i, b, N, v0, v1);
-  fn_half_unit_q<LOGH, LOGPER, RELAX, KM, ZINC>(P.twp + (size_t)i * N, P.q[i], h, o, v0, v1, sm, t);
+  fn_half_unit_q<LOGH, LOGPER, RELAX, KM, ZINC, false>(P.twp + (size_t)i * N, P.q[i], h, o, v0, v1, sm, t);
 }
 
 // N = 2^15: output quarter j of prime i on a four-CTA cluster (zn_quarter.cuh).

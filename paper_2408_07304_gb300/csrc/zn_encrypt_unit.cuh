@@ -66,26 +66,26 @@ __device__ __forceinline__ void encrypt_unit_q(const DevParams& P, const EncArgs
     __syncthreads();
     load_me();
     auto st_0 = [&](int idx, u64 x) {
-      if (active) c0[idx] = reduce_sum<RELAX>(c0[idx] + x, q);
+      if (active) __stcs(c0 + idx, reduce_sum<RELAX>(c0[idx] + x, q));
     };
     ntt_chain<LOGN, LOGPER, HI, RELAX, decltype(st_0), KM, true, KM == 3>(sm, t, tw, 1, q, st_0);
     // e1 -> c1
     __syncthreads();
     load_small(sp + S::N, std::false_type{});
     auto st_1 = [&](int idx, u64 x) {
-      if (active) c1[idx] = reduce_sum<RELAX>(c1[idx] + x, q);
+      if (active) __stcs(c1 + idx, reduce_sum<RELAX>(c1[idx] + x, q));
     };
     ntt_chain<LOGN, LOGPER, HI, RELAX, decltype(st_1), KM, true, KM == 3>(sm, t, tw, 1, q, st_1);
   } else {
     load_me();
     auto st_0 = [&](int idx, u64 x) {
-      if (active) c0[idx] = reduce_sum<RELAX>(__ldg(k0 + idx) + x, q);
+      if (active) __stcs(c0 + idx, reduce_sum<RELAX>(__ldg(k0 + idx) + x, q));
     };
     ntt_chain<LOGN, LOGPER, HI, RELAX, decltype(st_0), KM, true, KM == 3>(sm, t, tw, 1, q, st_0);
     __syncthreads();
     load_small(sp, std::false_type{});
     auto st_1 = [&](int idx, u64 x) {
-      if (active) c1[idx] = reduce_sum<RELAX>(__ldg(k1 + idx) + x, q);
+      if (active) __stcs(c1 + idx, reduce_sum<RELAX>(__ldg(k1 + idx) + x, q));
     };
     ntt_chain<LOGN, LOGPER, HI, RELAX, decltype(st_1), KM, true, KM == 3>(sm, t, tw, 1, q, st_1);
   }
