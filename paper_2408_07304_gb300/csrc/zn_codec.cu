@@ -209,8 +209,12 @@ __device__ __forceinline__ void prep_one(const DevParams& P, const PrepArgs& A, 
 }
 
 
-template <bool ZINC, bool MS = false>
-__global__ void __launch_bounds__(512, 2) k_prep_smem(DevParams P, PrepArgs A) {
+// TB threads per block: 512 (two blocks per SM up to 2^14), or 1024 at
+// 2^15, where the encoder's 128 KiB of shared memory allows one block per
+// SM and the wider block doubles the warps that hide its latency (64
+// registers either way).
+template <bool ZINC, bool MS = false, int TB = 512>
+__global__ void __launch_bounds__(TB, 1024 / TB) k_prep_smem(DevParams P, PrepArgs A) {
   extern __shared__ i64 smi[];
   __shared__ CdtTab s_cdt;
   stage_cdt_tab(P.cdt, s_cdt);
@@ -218,11 +222,12 @@ __global__ void __launch_bounds__(512, 2) k_prep_smem(DevParams P, PrepArgs A) {
   prep_one<ZINC, MS>(P, A, blockIdx.x, smi, smi + h, &s_cdt);
 }
 
-// Persistent prep over a mixed work list: 512-thread blocks take the next
-// ciphertext from a global counter (zero at launch); each holds the encoder
-// FFT of the batch's largest ring (4N bytes of shared memory: two blocks per
-// SM up to 2^14, one at 2^15).
-__global__ void __launch_bounds__(512, 2) k_batch_prep(const JobDesc* __restrict__ jobs,
+// Persistent prep over a mixed work list: blocks take the next ciphertext
+// from a global counter (zero at launch); each holds the encoder FFT of the
+// batch's largest ring (4N bytes of shared memory: two 512-thread blocks per
+// SM up to 2^14, one 1024-thread block at 2^15).
+template <int TB>
+__global__ void __launch_bounds__(TB, 1024 / TB) k_batch_prep(const JobDesc* __restrict__ jobs,
                                                        const PrepUnit* __restrict__ units, int n_units, int* counter) {
   extern __shared__ i64 smi[];
   __shared__ int s_next;
@@ -416,9 +421,10 @@ cudaError_t launch_encode_ragged(const DevParams& P, const double* slots, const 
 template <bool ZINC, bool MS = false>
 static cudaError_t prep_launch(const DevParams& P, const PrepArgs& A, uint32_t batch, cudaStream_t st) {
   const int h = 1 << (P.log_n - 2);
-  const int block = h / 2 < 512 ? (h / 2 < 32 ? 32 : h / 2) : 512;
+  const bool wide = P.log_n >= 15;
+  const int block = wide ? 1024 : h / 2 < 512 ? (h / 2 < 32 ? 32 : h / 2) : 512;
   const size_t smem = (A.n_slots || A.n_slots_v) ? 2 * sizeof(i64) * (size_t)h : 0;
-  auto kern = k_prep_smem<ZINC, MS>;
+  auto kern = wide ? k_prep_smem<ZINC, MS, 1024> : k_prep_smem<ZINC, MS>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<batch, block, smem, st>>>(P, A);
@@ -435,9 +441,13 @@ cudaError_t launch_prep_ms(const DevParams& P, const PrepArgs& A, uint32_t batch
   return prep_launch<false, true>(P, A, batch, st);
 }
 
+// 1024-thread blocks when the largest ring is 2^15 (more than 64 KiB each).
+static bool batch_prep_wide(size_t smem) { return smem > (size_t)(64 << 10); }
+
 cudaError_t launch_batch_prep(const JobDesc* jobs, const PrepUnit* units, int n_units, int* counter, int grid,
                               size_t smem, cudaStream_t st) {
-  k_batch_prep<<<grid, 512, smem, st>>>(jobs, units, n_units, counter);
+  if (batch_prep_wide(smem)) k_batch_prep<1024><<<grid, 1024, smem, st>>>(jobs, units, n_units, counter);
+  else k_batch_prep<512><<<grid, 512, smem, st>>>(jobs, units, n_units, counter);
   return cudaGetLastError();
 }
 
@@ -445,14 +455,19 @@ cudaError_t launch_batch_prep(const JobDesc* jobs, const PrepUnit* units, int n_
 // dynamic shared memory (the attribute must be set first); at least 1.
 cudaError_t batch_prep_blocks_per_sm(size_t smem, int* blocks) {
   int n = 0;
-  const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_prep, 512, smem);
+  const cudaError_t e = batch_prep_wide(smem)
+                            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_prep<1024>, 1024, smem)
+                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_prep<512>, 512, smem);
   *blocks = n > 0 ? n : 1;
   return e;
 }
 
 cudaError_t batch_set_attributes() {
-  cudaError_t e = cudaFuncSetAttribute(k_batch_prep, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_batch_prep<512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)(sizeof(i64) << 14));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_batch_prep<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(sizeof(i64) << 14));
   if (e != cudaSuccess) return e;
   return batch_encrypt_attributes();
 }
