@@ -91,10 +91,15 @@ struct Scope {
     fence_after_sync();
     base = *slot;
   }
+  // every thread's loads have completed (ld_u64 waits); the fence pair
+  // around the barrier orders them before the free
   __device__ __forceinline__ void release() const {
     fence_before_sync();
     __syncthreads();
-    if (__shfl_sync(0xffffffffu, threadIdx.x >> 5, 0) == 0) dealloc(base);
+    if (__shfl_sync(0xffffffffu, threadIdx.x >> 5, 0) == 0) {
+      fence_after_sync();
+      dealloc(base);
+    }
   }
 };
 
