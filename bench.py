@@ -57,8 +57,8 @@ NCU_INT_PIPE = {
     ("paper", "k_encrypt_quarter<vanilla,4-CTA cluster,radix-8,3 blocks/SM>"): 0.7405,
     ("paper", "k_encrypt_quarter<Zinc,4-CTA cluster,radix-8,3 blocks/SM>"): 0.7111,
 }
-VARIANT_KERNEL = {6: "k_encrypt_half<13,{mode},radix-8,3 blocks/SM>",
-                  7: "k_encrypt_half<13,{mode},radix-8,3 blocks/SM,ciphertext-major>"}
+VARIANT_KERNEL = {6: "k_encrypt_pair<{mode},2-CTA cluster,radix-8,3 blocks/SM>",
+                  7: "k_encrypt_pair<{mode},2-CTA cluster,radix-8,3 blocks/SM,ciphertext-major>"}
 
 
 def peaks():

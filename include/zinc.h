@@ -459,10 +459,11 @@ int zn_batch_info(const zn_batch* b, uint32_t* prep_units, uint32_t* packets);
  * output pointers); kind 2 = kind 0 capped at 128 registers per thread so
  * that several blocks share an SM, N = 2^14 split into output halves
  * (2^10 <= N <= 2^14); kind 3 = kind 2 with radix-8 passes capped at 80
- * registers (three blocks of 256 threads per SM), and at N = 2^15 one
- * cluster of four such blocks per limb, each owning an output quarter and
- * the first three butterfly stages exchanged through distributed shared
- * memory.  Where a kind does not apply, kind 0 runs.  A new context starts
+ * registers (three blocks of 256 threads per SM); at N = 2^14 one cluster
+ * of two such blocks per limb, each owning an output half, the first two
+ * butterfly stages split between them and exchanged through distributed
+ * shared memory, and at N = 2^15 one cluster of four, each owning an output
+ * quarter, the first three stages exchanged.  Where a kind does not apply, kind 0 runs.  A new context starts
  * at variant 6 for 2^10 <= N <= 2^15 and at variant 0 otherwise. */
 #define ZN_VARIANTS 8
 int zn_set_variant(zn_ctx* ctx, int variant);

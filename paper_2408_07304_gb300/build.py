@@ -16,7 +16,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libzinc.so")
 
-CU_SOURCES = ["zn_encrypt.cu", "zn_encrypt_mp.cu", "zn_encrypt_occ.cu", "zn_encrypt_occ3.cu", "zn_encrypt_quarter.cu", "zn_encrypt_ms.cu", "zn_encrypt_int.cu", "zn_zinc_ntt.cu", "zn_bencode.cu", "zn_pack.cu", "zn_batch.cu", "zn_keys.cu", "zn_codec.cu", "zn_probe.cu", "zn_api.cu"]
+CU_SOURCES = ["zn_encrypt.cu", "zn_encrypt_mp.cu", "zn_encrypt_occ.cu", "zn_encrypt_occ3.cu", "zn_encrypt_quarter.cu", "zn_encrypt_pair.cu", "zn_encrypt_ms.cu", "zn_encrypt_int.cu", "zn_zinc_ntt.cu", "zn_bencode.cu", "zn_pack.cu", "zn_batch.cu", "zn_keys.cu", "zn_codec.cu", "zn_probe.cu", "zn_api.cu"]
 CPP_SOURCES = ["zn_host.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

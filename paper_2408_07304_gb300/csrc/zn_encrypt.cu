@@ -13,8 +13,8 @@ namespace zn {
 // variant = 2 * kind + order; order 0 prime-major, 1 ciphertext-major.  Kind
 // 1 applies for 2^10 <= N <= 2^14 with 16-byte aligned key, companion and
 // output pointers, kind 2 for 2^10 <= N <= 2^14, kind 3 for 2^10 <= N <= 2^15
-// (at 2^15 the four-CTA cluster kernel, zn_encrypt_quarter.cu); otherwise
-// kind 0 runs.
+// (at 2^14 the two-CTA cluster kernel, zn_encrypt_pair.cu, at 2^15 the
+// four-CTA one, zn_encrypt_quarter.cu); otherwise kind 0 runs.
 template <bool ZINC>
 static cudaError_t enc_dispatch(const DevParams& P, const EncArgs& A_in, uint32_t batch, int variant,
                                 cudaStream_t st) {
@@ -25,7 +25,8 @@ static cudaError_t enc_dispatch(const DevParams& P, const EncArgs& A_in, uint32_
       (ZINC || aligned16(A.keys)))
     return launch_encrypt_mp(P, A, ZINC, batch, st);
   if (kind == 2 && P.log_n >= 10 && P.log_n <= 14) return launch_encrypt_occ(P, A, ZINC, batch, st);
-  if (kind == 3 && P.log_n >= 10 && P.log_n <= 14) return launch_encrypt_occ3(P, A, ZINC, batch, st);
+  if (kind == 3 && P.log_n == 14) return launch_encrypt_pair(P, A, ZINC, batch, st);
+  if (kind == 3 && P.log_n >= 10 && P.log_n <= 13) return launch_encrypt_occ3(P, A, ZINC, batch, st);
   if (kind == 3 && P.log_n == 15) return launch_encrypt_quarter(P, A, ZINC, batch, st);
   switch (P.log_n) {
     case 4: return enc_full<4, ZINC, 5>(P, A, batch, st);

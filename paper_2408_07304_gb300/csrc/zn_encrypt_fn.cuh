@@ -53,6 +53,14 @@ __device__ __forceinline__ void gen_val_half2(u64* sm, int t, int nt, int h, V& 
   }
 }
 
+// The CKKS transform input m + e, stored by the prep kernel with the offset
+// 2^62: [0, 2q) after one Barrett step.
+struct MeVal {
+  const i64* me;
+  u64 q, mu, moff;
+  __device__ __forceinline__ u64 operator()(int k) const { return reduce_biased((u64)__ldg(me + k), q, mu, moff); }
+};
+
 // Output limb (or half) of a unit and its key operands.
 struct FnLimb {
   u64* c0;

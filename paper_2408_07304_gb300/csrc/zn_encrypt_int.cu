@@ -13,6 +13,7 @@
 // Rings 2^10..2^15, in the launch shapes of the plain encryption's default
 // kernels.
 #include "zn_encrypt_fn.cuh"
+#include "zn_pair.cuh"
 #include "zn_quarter.cuh"
 
 namespace zn {
@@ -172,6 +173,43 @@ __device__ __forceinline__ void int_quarter_unit_q(const DevParams& P, const Int
   unit<ZINC, RELAX>(sm, t, j, tw, q, o, gu, g0, g1);
 }
 
+// N = 2^14: output half h of prime i on a two-CTA cluster (zn_pair.cuh).
+template <bool RELAX, bool BGV, bool ZINC>
+__device__ __forceinline__ void int_pair_unit_q(const DevParams& P, const IntArgs& A, int i, unsigned h, size_t b,
+                                                u64* sm, int t) {
+  using namespace pair;
+  const int L = P.L;
+  const u64 q = P.q[i];
+  const size_t off = (size_t)h * kH;
+  FnLimb o;
+  o.c0 = A.out + (b * 2 * L + i) * kN + off;
+  o.c1 = o.c0 + (size_t)L * kN;
+  o.k0 = A.key + (size_t)i * kN + off;
+  o.k1 = o.k0 + (size_t)L * kN;
+  o.k0s = ZINC ? nullptr : A.keys + (size_t)i * kN + off;
+  o.k1s = ZINC ? nullptr : o.k0s + (size_t)L * kN;
+  o.u = A.small + b * 3 * kN;
+  IntV0<BGV> v0;
+  IntV1<BGV> v1;
+  int_inputs<BGV, ZINC>(P, A, i, b, kN, v0, v1);
+  const ulonglong2* tw = P.twp + (size_t)i * kN;
+  auto gu = [&] { gen_i8<RELAX, true>(sm, t, h, o.u, tw, q); };
+  auto g0 = [&] { gen_val<RELAX>(sm, t, h, v0, tw, q); };
+  auto g1 = [&] { gen_val<RELAX>(sm, t, h, v1, tw, q); };
+  unit<ZINC, RELAX>(sm, t, h, tw, q, o, gu, g0, g1);
+}
+
+// grid (2L, B), or (2B, L) when A.swap; cluster rank h owns half h
+template <bool BGV, bool ZINC>
+__global__ void __launch_bounds__(pair::kT, 3) k_encrypt_int_pair(DevParams P, IntArgs A) {
+  extern __shared__ u64 sm[];
+  const unsigned h = cluster::cluster_rank();
+  const int i = A.swap ? (int)blockIdx.y : (int)(blockIdx.x >> 1);
+  const size_t b = A.swap ? (size_t)(blockIdx.x >> 1) : blockIdx.y;
+  if (P.q[i] < kRelaxLimit) int_pair_unit_q<true, BGV, ZINC>(P, A, i, h, b, sm, threadIdx.x);
+  else int_pair_unit_q<false, BGV, ZINC>(P, A, i, h, b, sm, threadIdx.x);
+}
+
 // grid (4L, B), or (4B, L) when A.swap; cluster rank j owns quarter j
 template <bool BGV, bool ZINC>
 __global__ void __launch_bounds__(quarter::kT, 3) k_encrypt_int_quarter(DevParams P, IntArgs A) {
@@ -310,6 +348,13 @@ static cudaError_t int_half(const DevParams& P, const IntArgs& A, uint32_t batch
 }
 
 template <bool BGV, bool ZINC>
+static cudaError_t int_pair(const DevParams& P, const IntArgs& A, uint32_t batch, cudaStream_t st) {
+  if ((!A.swap && batch > 65535u) || (A.swap && 2ull * batch > 0x7fffffffull)) return cudaErrorInvalidValue;
+  const dim3 grid = A.swap ? dim3(2 * batch, P.L) : dim3(2 * P.L, batch);
+  return pair::launch(k_encrypt_int_pair<BGV, ZINC>, grid, st, P, A);
+}
+
+template <bool BGV, bool ZINC>
 static cudaError_t int_quarter(const DevParams& P, const IntArgs& A, uint32_t batch, cudaStream_t st) {
   if ((!A.swap && batch > 65535u) || (A.swap && 4ull * batch > 0x7fffffffull)) return cudaErrorInvalidValue;
   const dim3 grid = A.swap ? dim3(4 * batch, P.L) : dim3(4 * P.L, batch);
@@ -323,7 +368,7 @@ static cudaError_t int_dispatch(const DevParams& P, const IntArgs& A, uint32_t b
     case 11: return int_full<11, 5, 12, 3, BGV, ZINC>(P, A, batch, st);
     case 12: return int_full<12, 5, 6, 3, BGV, ZINC>(P, A, batch, st);
     case 13: return int_full<13, 5, 3, 3, BGV, ZINC>(P, A, batch, st);
-    case 14: return int_half<13, 5, 3, 3, BGV, ZINC>(P, A, batch, st);
+    case 14: return int_pair<BGV, ZINC>(P, A, batch, st);
     case 15: return int_quarter<BGV, ZINC>(P, A, batch, st);
     default: return cudaErrorInvalidValue;
   }

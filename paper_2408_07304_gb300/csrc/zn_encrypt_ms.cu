@@ -17,6 +17,7 @@
 // two half blocks plus k_ms_special_top), then k_encrypt_ms (the data primes,
 // in the launch shapes of the plain encryption's radix-8 kernels).
 #include "zn_encrypt_fn.cuh"
+#include "zn_pair.cuh"
 #include "zn_quarter.cuh"
 
 namespace zn {
@@ -301,6 +302,43 @@ __global__ void __launch_bounds__(quarter::kT, 3) k_encrypt_ms_quarter(DevParams
   else ms_quarter_unit_q<false>(P, A, i, j, b, sm, threadIdx.x);
 }
 
+// N = 2^14: output half h of data prime i on a two-CTA cluster
+// (zn_pair.cuh), the vanilla-shaped unit with the MsVal inputs and streaming
+// stores for the finished words.
+template <bool RELAX>
+__device__ __forceinline__ void ms_pair_unit_q(const DevParams& P, const MsArgs& A, int i, unsigned h, size_t b,
+                                               u64* sm, int t) {
+  using namespace pair;
+  const int Ld = P.L - 1;
+  const u64 q = P.q[i];
+  const size_t off = (size_t)h * kH;
+  FnLimb o;
+  o.c0 = A.out + (b * 2 * Ld + i) * kN + off;
+  o.c1 = o.c0 + (size_t)Ld * kN;
+  o.k0 = A.keyms + (size_t)i * kN + off;
+  o.k1 = o.k0 + (size_t)Ld * kN;
+  o.k0s = o.k0 + 2 * (size_t)Ld * kN;
+  o.k1s = o.k1 + 2 * (size_t)Ld * kN;
+  o.u = A.small + b * 3 * kN;
+  const MsVal v0{A.d + b * 2 * kN, A.m + b * kN, q, P.mu[i], A.pinv[i], A.pinvs[i], A.kc0[i]};
+  const MsVal v1{A.d + b * 2 * kN + kN, nullptr, q, P.mu[i], A.pinv[i], A.pinvs[i], A.kc1[i]};
+  const ulonglong2* tw = P.twp + (size_t)i * kN;
+  auto gu = [&] { gen_i8<RELAX, true>(sm, t, h, o.u, tw, q); };
+  auto g0 = [&] { gen_val<RELAX>(sm, t, h, v0, tw, q); };
+  auto g1 = [&] { gen_val<RELAX>(sm, t, h, v1, tw, q); };
+  unit<false, RELAX, true>(sm, t, h, tw, q, o, gu, g0, g1);
+}
+
+// grid (2(L-1), B), or (2B, L-1) when A.swap; cluster rank h owns half h
+__global__ void __launch_bounds__(pair::kT, 3) k_encrypt_ms_pair(DevParams P, MsArgs A) {
+  extern __shared__ u64 sm[];
+  const unsigned h = cluster::cluster_rank();
+  const int i = A.swap ? (int)blockIdx.y : (int)(blockIdx.x >> 1);
+  const size_t b = A.swap ? (size_t)(blockIdx.x >> 1) : blockIdx.y;
+  if (P.q[i] < kRelaxLimit) ms_pair_unit_q<true>(P, A, i, h, b, sm, threadIdx.x);
+  else ms_pair_unit_q<false>(P, A, i, h, b, sm, threadIdx.x);
+}
+
 // ---------------------------------------------------------------- keys
 // keyms[j][i][k] = pk_j[i][k] p^-1 mod q_i (i < L-1), keyn[j][k] = pk_j[L-1][k] N^-1 mod p,
 // each followed by its Shoup companions.
@@ -411,6 +449,12 @@ static cudaError_t data_half(const DevParams& P, const MsArgs& A, uint32_t batch
   return cudaGetLastError();
 }
 
+static cudaError_t data_pair(const DevParams& P, const MsArgs& A, uint32_t batch, cudaStream_t st) {
+  if ((!A.swap && batch > 65535u) || (A.swap && 2ull * batch > 0x7fffffffull)) return cudaErrorInvalidValue;
+  const dim3 grid = A.swap ? dim3(2 * batch, P.L - 1) : dim3(2 * (P.L - 1), batch);
+  return pair::launch(k_encrypt_ms_pair, grid, st, P, A);
+}
+
 static cudaError_t data_quarter(const DevParams& P, const MsArgs& A, uint32_t batch, cudaStream_t st) {
   if ((!A.swap && batch > 65535u) || (A.swap && 4ull * batch > 0x7fffffffull)) return cudaErrorInvalidValue;
   const dim3 grid = A.swap ? dim3(4 * batch, P.L - 1) : dim3(4 * (P.L - 1), batch);
@@ -418,8 +462,8 @@ static cudaError_t data_quarter(const DevParams& P, const MsArgs& A, uint32_t ba
 }
 
 // The plain encryption's default shapes: radix-8, three 256-thread blocks
-// per SM for 2^10..2^14 (2^14 as output halves), one block per limb below,
-// four-CTA clusters (one output quarter each) at 2^15.
+// per SM for 2^10..2^13, one block per limb below, two-CTA clusters (one
+// output half each) at 2^14, four-CTA clusters (one quarter each) at 2^15.
 cudaError_t launch_ms_data(const DevParams& P, const MsArgs& A, uint32_t batch, cudaStream_t st) {
   if (batch == 0) return cudaSuccess;
   if (P.L < 2) return cudaErrorInvalidValue;
@@ -434,7 +478,7 @@ cudaError_t launch_ms_data(const DevParams& P, const MsArgs& A, uint32_t batch, 
     case 11: return data_full<11, 5, 12, 3>(P, A, batch, st);
     case 12: return data_full<12, 5, 6, 3>(P, A, batch, st);
     case 13: return data_full<13, 5, 3, 3>(P, A, batch, st);
-    case 14: return data_half<13, 5, 3, 3>(P, A, batch, st);
+    case 14: return data_pair(P, A, batch, st);
     case 15: return data_quarter(P, A, batch, st);
     default: return cudaErrorInvalidValue;
   }

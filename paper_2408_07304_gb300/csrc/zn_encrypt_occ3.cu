@@ -1,8 +1,9 @@
-// Hot path, register-capped launch shapes (kind 3): at most 80 registers per
-// thread (768 threads' worth per SM, three blocks of 256 threads) with
-// radix-8 passes, which need fewer live registers than radix-16 ones.  2^10 <= N <= 2^13: one block per prime and
-// ciphertext, 2^(LOGN-5) threads; N = 2^14: one block per output half of
-// each limb (64 KiB of shared memory, 256 threads).
+// Register-capped launch shapes (kind 3): at most 80 registers per thread
+// (768 threads' worth per SM, three blocks of 256 threads) with radix-8
+// passes, which need fewer live registers than radix-16 ones.  2^10 <= N <=
+// 2^13: one block per prime and ciphertext, 2^(LOGN-5) threads.  (Kind 3 at
+// N = 2^14 and 2^15 runs the cluster kernels, zn_encrypt_pair.cu and
+// zn_encrypt_quarter.cu.)
 #include "zn_encrypt_kern.cuh"
 
 namespace zn {
@@ -14,7 +15,6 @@ static cudaError_t enc_occ3_dispatch(const DevParams& P, const EncArgs& A, uint3
     case 11: return enc_full<11, ZINC, 5, 12, 3>(P, A, batch, st);
     case 12: return enc_full<12, ZINC, 5, 6, 3>(P, A, batch, st);
     case 13: return enc_full<13, ZINC, 5, 3, 3>(P, A, batch, st);
-    case 14: return enc_half<13, ZINC, 5, 3, 3>(P, A, batch, st);
     default: return cudaErrorInvalidValue;
   }
 }

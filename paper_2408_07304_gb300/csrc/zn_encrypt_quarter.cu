@@ -9,14 +9,6 @@
 namespace zn {
 namespace {
 
-// Encoded message plus noise, stored with the offset 2^62: [0, 2q) after one
-// Barrett step.
-struct MeVal {
-  const i64* me;
-  u64 q, mu, moff;
-  __device__ __forceinline__ u64 operator()(int k) const { return reduce_biased((u64)__ldg(me + k), q, mu, moff); }
-};
-
 // Park: quarter::ParkTmem, or quarter::ParkOut (its pointer unused: u-hat
 // goes to this unit's c1 words).
 template <bool ZINC, bool RELAX, class Park>

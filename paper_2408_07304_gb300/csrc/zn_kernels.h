@@ -71,6 +71,8 @@ cudaError_t batch_quarter_clusters(int* clusters);
 cudaError_t launch_batch_encrypt_quarter(const JobDesc* jobs, const EncPacket* packets, int n_packets, int* counter,
                                          int clusters, cudaStream_t st);
 
+// N = 2^14 on two-CTA clusters, one output half per CTA (kind 3 at 2^14).
+cudaError_t launch_encrypt_pair(const DevParams& P, const EncArgs& A, bool zinc, uint32_t batch, cudaStream_t st);
 // variant = 2 * kind + order.  order 0 = prime-major grid, 1 =
 // ciphertext-major grid (all blocks of a wave share one prime's twiddles and
 // keys); kind 0 = per-polynomial kernel, 1 = multi-polynomial kernel, 2 and
@@ -82,7 +84,8 @@ cudaError_t launch_encrypt(const DevParams& P, const EncArgs& A, bool zinc, uint
 // Multi-polynomial kernel (2^10 <= N <= 2^14; key, companion and output
 // pointers 16-byte aligned; grid order from A.swap).
 cudaError_t launch_encrypt_mp(const DevParams& P, const EncArgs& A, bool zinc, uint32_t batch, cudaStream_t st);
-// Register-capped per-polynomial kernels (2^10 <= N <= 2^14).
+// Register-capped per-polynomial kernels (kind 2: 2^10 <= N <= 2^14; kind 3:
+// 2^10 <= N <= 2^13).
 cudaError_t launch_encrypt_occ(const DevParams& P, const EncArgs& A, bool zinc, uint32_t batch, cudaStream_t st);
 cudaError_t launch_encrypt_occ3(const DevParams& P, const EncArgs& A, bool zinc, uint32_t batch, cudaStream_t st);
 // N = 2^15: one four-CTA cluster per limb, one output quarter per CTA, the

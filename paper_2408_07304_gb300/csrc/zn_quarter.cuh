@@ -14,6 +14,7 @@
 #pragma once
 #include <type_traits>
 
+#include "zn_cluster.cuh"
 #include "zn_encrypt_fn.cuh"
 #include "zn_tmem.cuh"
 
@@ -26,37 +27,12 @@ constexpr int kN = 4 * kQ;            // N = 2^15
 constexpr int kT = 256;               // threads per CTA
 constexpr int kKm = 3;                // radix-8 passes (shared-memory layout swz<13, 3>)
 
-__device__ __forceinline__ unsigned cluster_rank() {
-  unsigned r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
+using cluster::cluster_rank;
+using cluster::cluster_sync;
+using cluster::map_rank;
+using cluster::st_cluster;
 
-// Every thread of every CTA of the cluster; release / acquire order the
-// shared-memory accesses before the barrier against those after it.
-__device__ __forceinline__ void cluster_sync() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
-// Shared-memory address of `p` in the CTA of cluster rank `rank`.
-__device__ __forceinline__ unsigned map_rank(const void* p, unsigned rank) {
-  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
-  unsigned r;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
-  return r;
-}
-
-__device__ __forceinline__ void st_cluster(unsigned addr, u64 v) {
-  asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(addr), "l"(v) : "memory");
-}
-
-// Harvey keeps [0, 4q); a relaxed stage adds 2q: the generators bring their
-// outputs back below 4q so that the 12 local stages end below 28q.
-template <bool RELAX>
-__device__ __forceinline__ u64 below4q(u64 x, u64 q) {
-  if constexpr (RELAX) return x >= 4 * q ? x - 4 * q : x;
-  return x;
-}
+using cluster::below4q;
 
 // Work items of CTA j: index k < N/8, k in [j N/32, (j+1) N/32), with eight
 // inputs at k + m N/4 and k + N/8 + m N/4 (m < 4).  x[m] and x[4 + m] hold
@@ -231,22 +207,7 @@ __device__ __forceinline__ void unit(u64* sm, int t, unsigned j, const ulonglong
 // Launch a quarter kernel: clusters of four consecutive CTAs along x.
 template <class... Args>
 cudaError_t launch(void (*kern)(Args...), dim3 grid, cudaStream_t st, Args... args) {
-  const size_t smem = sizeof(u64) * kQ;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = dim3(kT);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = 4;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kern, args...);
+  return cluster::launch(4, sizeof(u64) * kQ, kern, grid, kT, st, args...);
 }
 
 }  // namespace quarter

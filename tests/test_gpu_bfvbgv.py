@@ -71,7 +71,7 @@ def plaintexts(n, t, batch, seed):
 
 # N = 2^15 runs the four-CTA cluster kernels (a relaxed and a Harvey prime)
 SMALL = [(10, (40, 40, 41), 65537), (10, (50, 60), 2), (12, (36, 36, 36), 257), (13, (60, 40, 60), (1 << 20) + 7),
-         (15, (55, 60), 65537)]
+         (14, (50, 60), 65537), (15, (55, 60), 65537)]
 
 
 @pytest.mark.parametrize("log_n,bits,t", SMALL)

@@ -62,7 +62,8 @@ def dev(a, dtype):
 
 # N = 2^15 runs the four-CTA cluster kernels (a relaxed and a Harvey data prime)
 SMALL = [(4, (30, 40), 20, 8), (6, (40, 41, 50), 25, 20), (10, (40, 40, 41), 30, 500),
-         (12, (36, 36, 36), 30, 2048), (13, (60, 40, 60), 40, 100), (15, (55, 60, 60), 55, 16384)]
+         (12, (36, 36, 36), 30, 2048), (13, (60, 40, 60), 40, 100), (14, (50, 60, 60), 50, 8192),
+         (15, (55, 60, 60), 55, 16384)]
 
 
 @pytest.mark.parametrize("log_n,bits,ld,n_slots", SMALL)

@@ -212,7 +212,8 @@ def test_keygen_sampled_full_size(name):
 
 
 # ---------------------------------------------------------------- encryption
-SMALL = [(4, (30,), 20, 8), (6, (40, 41), 25, 20), (10, (40, 40, 41), 30, 500), (12, (36, 36, 36), 30, 2048)]
+SMALL = [(4, (30,), 20, 8), (6, (40, 41), 25, 20), (10, (40, 40, 41), 30, 500), (12, (36, 36, 36), 30, 2048),
+         (14, (50, 60), 40, 8192)]
 
 
 @pytest.mark.parametrize("log_n,bits,ld,n_slots", SMALL)
@@ -273,10 +274,11 @@ def _check_whole(w, ct, zinc, z, idx, rows, seed):
         assert np.array_equal(got[b], ref), (b, zinc)
 
 
-# rows compared in full: the first and last ciphertext of the call, and at
-# N = 2^13 and 2^14 both sides of the first 256-ciphertext chunk boundary
+# rows compared in full: the first and last ciphertext of the call, two in
+# between, and at N = 2^14 both sides of the boundary between the call's two
+# launches (prep scratch of 256 MiB: 2048 ciphertexts per launch)
 WHOLE_ROWS = {"batched": {False: (0, 255, 256, 1023), True: (0, 255, 256, 1023)},
-              "throughput": {False: (0, 255, 256, 4095), True: (0, 255, 256, 4095)},
+              "throughput": {False: (0, 2047, 2048, 4095), True: (0, 2047, 2048, 4095)},
               "large": {False: (511,), True: (0,)}}
 
 
