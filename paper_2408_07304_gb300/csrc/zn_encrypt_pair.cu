@@ -29,9 +29,12 @@ __device__ __forceinline__ void encrypt_pair_unit_q(const DevParams& P, const En
   const MeVal me{A.me + b * kN, q, P.mu[i], P.moff[i]};
   auto g_me = [&] { gen_val<RELAX>(sm, t, h, me, tw, q); };
   if constexpr (!ZINC) {
+    // streaming stores for the finished words: the parked key products stay
+    // in L2 (DRAM traffic 1.42x -> 1.08x of the algorithmic bytes, the
+    // launch 0.3 % slower)
     auto g_u = [&] { gen_i8<RELAX, true>(sm, t, h, sp, tw, q); };
     auto g_e1 = [&] { gen_i8<RELAX, false>(sm, t, h, sp + kN, tw, q); };
-    unit<false, RELAX>(sm, t, h, tw, q, o, g_u, g_me, g_e1);
+    unit<false, RELAX, true>(sm, t, h, tw, q, o, g_u, g_me, g_e1);
   } else {
     auto g_e2 = [&] { gen_i8<RELAX, false>(sm, t, h, sp, tw, q); };
     unit<true, RELAX>(sm, t, h, tw, q, o, g_me, g_me, g_e2);
