@@ -429,14 +429,16 @@ typedef struct zn_batch zn_batch;
 /* Plan a batch over jobs of mixed ring degree, chain and mode (all contexts
  * on `device`): builds the work lists (one prep unit per ciphertext; encrypt
  * packets, largest rings first: for N <= 2^13 the 2^(13 - log_n) limbs that
- * fill a 256-thread block, for N = 2^14 and 2^15 one output half of a limb)
- * and allocates the scratch for every ciphertext.  Synchronous. */
+ * fill a 256-thread block, for N = 2^14 and 2^15 one limb, run by a cluster
+ * of two or four 256-thread blocks) and allocates the scratch for every
+ * ciphertext.  Synchronous. */
 int zn_batch_create(const zn_job* jobs, uint32_t n_jobs, int device, zn_batch** out);
 void zn_batch_destroy(zn_batch* b);
 
-/* Enqueue the batch on `stream`: persistent launches -- prep (one 512-thread
- * block per SM), encryption of the rings up to 2^14 (three 256-thread blocks
- * per SM), encryption of the 2^15 rings (one 512-thread block per SM) -- whose
+/* Enqueue the batch on `stream`: persistent launches -- prep (512-thread
+ * blocks, 1024-thread ones when the largest ring is 2^15), encryption of the
+ * rings up to 2^13 (three 256-thread blocks per SM), of the 2^14 rings
+ * (two-CTA clusters) and of the 2^15 rings (four-CTA clusters) -- whose
  * blocks take work from device counters.  graph != 0:
  * the first call captures the launches into a CUDA graph on `stream` and
  * every call replays it (one graph launch per run).  Results are identical to

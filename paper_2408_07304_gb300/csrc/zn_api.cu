@@ -1507,13 +1507,14 @@ struct zn_batch {
   int device;
   int sms;
   int clusters;           // resident four-CTA clusters of the 2^15 kernel
+  int pair_clusters;      // resident two-CTA clusters of the 2^14 kernel
   size_t prep_smem;       // dynamic shared memory of the persistent prep: 4N of the largest ring
   int prep_grid;          // its blocks: SMs x the blocks of that size that fit on an SM
-  uint32_t n_prep, n_packets, n_small;   // packets: [rings up to 2^14 | 2^15]
+  uint32_t n_prep, n_packets, n_small, n_mid;   // packets: [rings up to 2^13 | 2^14 | 2^15]
   zn::JobDesc* d_jobs;
   zn::PrepUnit* d_units;
   zn::EncPacket* d_packets;
-  int* d_counters;        // [3]: prep, encrypt (up to 2^14), encrypt (2^15)
+  int* d_counters;        // [4]: prep, encrypt (up to 2^13), encrypt (2^14), encrypt (2^15)
   i64* d_me;
   int8_t* d_small;
   cudaGraphExec_t exec;
@@ -1565,10 +1566,10 @@ int zn_batch_create(const zn_job* jobs, uint32_t n_jobs, int device, zn_batch** 
   int rc = ZN_OK;
   if ((me_words && cudaMalloc(&b->d_me, sizeof(i64) * me_words) != cudaSuccess) ||
       (small_bytes && cudaMalloc(&b->d_small, small_bytes) != cudaSuccess) ||
-      cudaMalloc(&b->d_counters, 3 * sizeof(int)) != cudaSuccess)
+      cudaMalloc(&b->d_counters, 4 * sizeof(int)) != cudaSuccess)
     rc = ZN_ENOMEM;
   std::vector<zn::PrepUnit> units;
-  std::vector<zn::EncPacket> packets, big;
+  std::vector<zn::EncPacket> packets, mid, big;
   size_t me_off = 0, sm_off = 0;
   for (uint32_t j = 0; j < n_jobs && !rc; ++j) {
     const zn_job& J = jobs[j];
@@ -1601,10 +1602,9 @@ int zn_batch_create(const zn_job* jobs, uint32_t n_jobs, int device, zn_batch** 
     if (log_n == 15) {                 // one limb per four-CTA cluster
       for (uint32_t i = 0; i < L; ++i)
         for (uint32_t k = 0; k < J.count; ++k) big.push_back({j, k, (uint16_t)i, 1, 0});
-    } else if (log_n == 14) {          // output halves, one per block
+    } else if (log_n == 14) {          // one limb per two-CTA cluster
       for (uint32_t i = 0; i < L; ++i)
-        for (uint32_t k = 0; k < J.count; ++k)
-          for (uint8_t h = 0; h < 2; ++h) packets.push_back({j, k, (uint16_t)i, 1, h});
+        for (uint32_t k = 0; k < J.count; ++k) mid.push_back({j, k, (uint16_t)i, 1, 0});
     } else {                           // 2^(13 - log_n) limbs per 256-thread block
       const uint32_t per = 1u << (13 - log_n);
       for (uint32_t i = 0; i < L; ++i)
@@ -1614,7 +1614,9 @@ int zn_batch_create(const zn_job* jobs, uint32_t n_jobs, int device, zn_batch** 
   }
   b->n_prep = (uint32_t)units.size();
   b->n_small = (uint32_t)packets.size();
-  packets.insert(packets.end(), big.begin(), big.end());     // [small list | 2^15 list]
+  b->n_mid = (uint32_t)mid.size();
+  packets.insert(packets.end(), mid.begin(), mid.end());     // [small list | 2^14 list | 2^15 list]
+  packets.insert(packets.end(), big.begin(), big.end());
   b->n_packets = (uint32_t)packets.size();
   if (!rc && (cudaMalloc(&b->d_jobs, sizeof(zn::JobDesc) * n_jobs) != cudaSuccess ||
               (b->n_prep && cudaMalloc(&b->d_units, sizeof(zn::PrepUnit) * b->n_prep) != cudaSuccess) ||
@@ -1625,7 +1627,8 @@ int zn_batch_create(const zn_job* jobs, uint32_t n_jobs, int device, zn_batch** 
                                        cudaMemcpyHostToDevice) != cudaSuccess) ||
               (b->n_packets && cudaMemcpy(b->d_packets, packets.data(), sizeof(zn::EncPacket) * b->n_packets,
                                           cudaMemcpyHostToDevice) != cudaSuccess) ||
-              zn::batch_set_attributes() != cudaSuccess || zn::batch_quarter_clusters(&b->clusters) != cudaSuccess))
+              zn::batch_set_attributes() != cudaSuccess || zn::batch_quarter_clusters(&b->clusters) != cudaSuccess ||
+              zn::batch_pair_clusters(&b->pair_clusters) != cudaSuccess))
     rc = ZN_ECUDA;
   if (!rc) {
     uint32_t max_n = 0;
@@ -1645,15 +1648,19 @@ int zn_batch_create(const zn_job* jobs, uint32_t n_jobs, int device, zn_batch** 
 }
 
 static int batch_enqueue(zn_batch* b, cudaStream_t st) {
-  ZN_CUDA(cudaMemsetAsync(b->d_counters, 0, 3 * sizeof(int), st));
+  ZN_CUDA(cudaMemsetAsync(b->d_counters, 0, 4 * sizeof(int), st));
   if (b->n_prep)
     ZN_CUDA(zn::launch_batch_prep(b->d_jobs, b->d_units, (int)b->n_prep, b->d_counters, b->prep_grid, b->prep_smem,
                                   st));
   if (b->n_small)
     ZN_CUDA(zn::launch_batch_encrypt(b->d_jobs, b->d_packets, (int)b->n_small, b->d_counters + 1, b->sms, st));
-  if (b->n_packets > b->n_small)
-    ZN_CUDA(zn::launch_batch_encrypt_quarter(b->d_jobs, b->d_packets + b->n_small, (int)(b->n_packets - b->n_small),
-                                             b->d_counters + 2, b->clusters, st));
+  if (b->n_mid)
+    ZN_CUDA(zn::launch_batch_encrypt_pair(b->d_jobs, b->d_packets + b->n_small, (int)b->n_mid, b->d_counters + 2,
+                                          b->pair_clusters, st));
+  const uint32_t n_big = b->n_packets - b->n_small - b->n_mid;
+  if (n_big)
+    ZN_CUDA(zn::launch_batch_encrypt_quarter(b->d_jobs, b->d_packets + b->n_small + b->n_mid, (int)n_big,
+                                             b->d_counters + 3, b->clusters, st));
   return ZN_OK;
 }
 

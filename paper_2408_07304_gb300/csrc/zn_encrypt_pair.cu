@@ -55,7 +55,85 @@ __global__ void __launch_bounds__(pair::kT, 3) k_encrypt_pair(DevParams P, EncAr
   else encrypt_pair_unit_q<ZINC, false>(P, A, i, h, b, sm, threadIdx.x);
 }
 
+// ---------------------------------------- persistent mixed-ring launch
+// Packet: one limb (ciphertext b0, prime `prime`) of a 2^14 job, run by one
+// two-CTA cluster.  Rank 0 takes the next packet from a global counter (zero
+// at launch) into its shared memory; a cluster barrier publishes it, both
+// CTAs read it through distributed shared memory, and a second barrier keeps
+// rank 0 from overwriting it (or exiting) before the other has read it.  No
+// cluster waits for any other.
+__device__ __forceinline__ int ld_cluster_s32(unsigned addr) {
+  int v;
+  asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+  return v;
+}
+
+__global__ void __launch_bounds__(pair::kT, 3) k_batch_encrypt_pair(const JobDesc* __restrict__ jobs,
+                                                                    const EncPacket* __restrict__ packets,
+                                                                    int n_packets, int* counter) {
+  extern __shared__ u64 sm[];
+  __shared__ int s_next;
+  const unsigned h = cluster::cluster_rank();
+  const unsigned next0 = cluster::map_rank(&s_next, 0);
+  for (;;) {
+    if (h == 0 && threadIdx.x == 0) s_next = atomicAdd(counter, 1);
+    cluster::cluster_sync();
+    const int p = ld_cluster_s32(next0);
+    cluster::cluster_sync();
+    if (p >= n_packets) break;
+    const EncPacket pk = packets[p];
+    const JobDesc& J = jobs[pk.job];
+    const bool relax = J.P.q[pk.prime] < kRelaxLimit;
+    if (J.zinc) {
+      if (relax) encrypt_pair_unit_q<true, true>(J.P, J.E, pk.prime, h, pk.b0, sm, threadIdx.x);
+      else encrypt_pair_unit_q<true, false>(J.P, J.E, pk.prime, h, pk.b0, sm, threadIdx.x);
+    } else {
+      if (relax) encrypt_pair_unit_q<false, true>(J.P, J.E, pk.prime, h, pk.b0, sm, threadIdx.x);
+      else encrypt_pair_unit_q<false, false>(J.P, J.E, pk.prime, h, pk.b0, sm, threadIdx.x);
+    }
+  }
+}
+
+cudaLaunchConfig_t batch_pair_config(int clusters, cudaStream_t st, cudaLaunchAttribute* attr) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2 * (unsigned)clusters);
+  cfg.blockDim = dim3(pair::kT);
+  cfg.dynamicSmemBytes = sizeof(u64) * pair::kH;
+  cfg.stream = st;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
 }  // namespace
+
+cudaError_t batch_pair_attributes() {
+  return cudaFuncSetAttribute(k_batch_encrypt_pair, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(sizeof(u64) * pair::kH));
+}
+
+// Clusters of the persistent 2^14 kernel that fit on the device at once (the
+// attribute must be set first); at least 1.
+cudaError_t batch_pair_clusters(int* clusters) {
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = batch_pair_config(1, 0, attr);
+  int n = 0;
+  cudaError_t e = cudaOccupancyMaxActiveClusters(&n, (void*)k_batch_encrypt_pair, &cfg);
+  *clusters = n > 0 ? n : 1;
+  return e;
+}
+
+// Capturable: the attribute is set beforehand (batch_pair_attributes).
+cudaError_t launch_batch_encrypt_pair(const JobDesc* jobs, const EncPacket* packets, int n_packets, int* counter,
+                                      int clusters, cudaStream_t st) {
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = batch_pair_config(clusters, st, attr);
+  return cudaLaunchKernelEx(&cfg, k_batch_encrypt_pair, jobs, packets, n_packets, counter);
+}
 
 cudaError_t launch_encrypt_pair(const DevParams& P, const EncArgs& A, bool zinc, uint32_t batch, cudaStream_t st) {
   if (batch == 0) return cudaSuccess;

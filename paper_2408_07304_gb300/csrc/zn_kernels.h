@@ -73,6 +73,11 @@ cudaError_t launch_batch_encrypt_quarter(const JobDesc* jobs, const EncPacket* p
 
 // N = 2^14 on two-CTA clusters, one output half per CTA (kind 3 at 2^14).
 cudaError_t launch_encrypt_pair(const DevParams& P, const EncArgs& A, bool zinc, uint32_t batch, cudaStream_t st);
+// 2^14 rings: persistent two-CTA clusters, one limb per packet.
+cudaError_t batch_pair_attributes();
+cudaError_t batch_pair_clusters(int* clusters);
+cudaError_t launch_batch_encrypt_pair(const JobDesc* jobs, const EncPacket* packets, int n_packets, int* counter,
+                                      int clusters, cudaStream_t st);
 // variant = 2 * kind + order.  order 0 = prime-major grid, 1 =
 // ciphertext-major grid (all blocks of a wave share one prime's twiddles and
 // keys); kind 0 = per-polynomial kernel, 1 = multi-polynomial kernel, 2 and

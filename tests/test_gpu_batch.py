@@ -62,10 +62,10 @@ def test_batch_matches_single_ring(graph):
     b = api.zn_batch_create(jobs)
     expect_packets = 0
     for log_n, bits, _, _, count, _ in JOBS:
-        # 2^(13 - log_n) limbs per 256-thread block below 2^14; output halves at
-        # 2^14; one limb per four-CTA cluster at 2^15
+        # 2^(13 - log_n) limbs per 256-thread block below 2^14; one limb per
+        # two-CTA cluster at 2^14 and per four-CTA cluster at 2^15
         per = 1 << (13 - log_n) if log_n <= 13 else 1
-        expect_packets += len(bits) * (-(-count // per) if log_n <= 13 else 2 * count if log_n == 14 else count)
+        expect_packets += len(bits) * (-(-count // per) if log_n <= 13 else count)
     assert b.prep_units == sum(j[4] for j in JOBS) and b.packets == expect_packets
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
