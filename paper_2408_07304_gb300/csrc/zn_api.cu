@@ -200,14 +200,15 @@ struct TimedLaunch {
 };
 
 // Messages encoded per launch pair: the int64 scratch is kept within
-// 256 MiB (2048 ciphertexts at N = 2^14).  Large launches amortise each
+// 512 MiB (4096 ciphertexts at N = 2^14).  Large launches amortise each
 // launch's partial last wave (the prep grid of 256 ciphertexts filled 0.84 of
 // a wave); the kernels are bound by integer arithmetic, so scratch that no
 // longer stays in L2 costs nothing measurable (measured at N = 2^14: 256, 512,
-// 1024, 2048 ciphertexts per launch -> 234.5k, 238.7k, 244.4k, 246.2k enc/s).
+// 1024, 2048 ciphertexts per launch -> 234.5k, 238.7k, 244.4k, 246.2k enc/s
+// with the half kernels; 2048 -> 4096 with the pair kernels 260.9k -> 262.7k).
 uint32_t encode_chunk(const zn_ctx* c) {
   size_t per = sizeof(i64) * c->n;
-  size_t k = (256ull << 20) / per;
+  size_t k = (512ull << 20) / per;
   if (k < 1) k = 1;
   if (k > 65535) k = 65535;
   return (uint32_t)k;
@@ -320,9 +321,10 @@ int ms_key_forms(zn_ctx* c, zn_pk* k) {
 // the batch split into equal chunks so that no launch is a small tail wave.
 // The data kernel re-reads the scratch once per prime; DRAM has ample
 // headroom, and measured at N = 2^14 (4096 ciphertexts) larger chunks win:
-// 133 k/s at 32 MiB, 165 k/s at 128 MiB, 171 k/s at 512 MiB.
+// 133 k/s at 32 MiB, 165 k/s at 128 MiB, 171 k/s at 512 MiB; with the pair
+// kernels 512 -> 1024 MiB (two launches of 2048) 193.5 k -> 196.9 k.
 #ifndef ZN_MS_SCRATCH_MIB
-#define ZN_MS_SCRATCH_MIB 512
+#define ZN_MS_SCRATCH_MIB 1024
 #endif
 uint32_t ms_chunk(const zn_ctx* c, uint32_t batch) {
   const size_t per = (size_t)c->n * (27 + (c->prm.log_n == 15 ? 16 : 0));
@@ -434,9 +436,9 @@ void int_dec_consts(const zn_ctx* c, uint64_t t, zn::IntDec& D) {
 }
 
 // Ciphertexts per prep/encrypt launch pair: me (8N) + small (3N) within
-// 352 MiB (2048 ciphertexts at N = 2^14, as the CKKS path), in equal chunks.
+// 704 MiB (4096 ciphertexts at N = 2^14, as the CKKS path), in equal chunks.
 uint32_t int_chunk(const zn_ctx* c, uint32_t batch) {
-  size_t k = (352ull << 20) / (11 * (size_t)c->n);
+  size_t k = (704ull << 20) / (11 * (size_t)c->n);
   if (k < 1) k = 1;
   if (k > 65535) k = 65535;
   const size_t chunks = (batch + k - 1) / k;

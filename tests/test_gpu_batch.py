@@ -3,7 +3,7 @@ first and last ciphertext equal, residue for residue, the oracle's (Eq. 8 and
 Algorithm 1 in the coefficient domain, then the definitional transform), and
 every job's ciphertexts equal, bit for bit, those of the single-ring entry
 points.  Ragged job sizes exercise partially filled packets (idle sub-groups)
-and both halves of 2^15 rings."""
+and the persistent cluster kernels of 2^14 and 2^15 rings in both modes."""
 import functools
 
 import numpy as np
@@ -31,6 +31,7 @@ JOBS = [  # (log_n, bits, log2_delta, zinc, count, n_slots)
     (12, (36, 36, 36), 30, True, 3, 100),
     (13, (60, 40, 40, 60), 40, True, 7, 4096),
     (14, (60, 50, 50, 60), 50, False, 2, 8192),
+    (14, (60, 50, 50, 60), 50, True, 3, 5000),
     (15, (55, 55, 60), 55, False, 1, 16384),
     (15, (55, 55, 60), 55, True, 2, 3000),
     (10, (40, 41), 30, True, 17, 512),
@@ -138,13 +139,15 @@ def test_batch_rejects_bad_jobs():
                               "out": torch.empty((1, 2, 1, 512), dtype=torch.int64, device="cuda:0")}])
 
 
-@pytest.mark.parametrize("pinned", [True, False])
-def test_host_pipeline_matches_device_api(pinned):
-    """zn_encrypt_host (host buffers, chunked copy/compute overlap) gives the
-    device entry points' ciphertexts, with a ragged last chunk."""
-    ctx, _, pk, zc = ring(13, (60, 40, 40, 60), 40)
+@pytest.mark.parametrize("pinned,log_n,bits", [(True, 13, (60, 40, 40, 60)), (False, 13, (60, 40, 40, 60)),
+                                               (True, 14, (60, 50, 60))])
+def test_host_pipeline_matches_device_api(pinned, log_n, bits):
+    """zn_encrypt_host (host buffers, chunked copy/compute overlap on three
+    streams) gives the device entry points' ciphertexts, with a ragged last
+    chunk; at 2^14 the chunks' cluster kernels run concurrently."""
+    ctx, _, pk, zc = ring(log_n, bits, 40)
     B, ns = 37, 1500
-    w = workloads.small(13, (60, 40, 40, 60), 40, B, ns, seed=77)
+    w = workloads.small(log_n, bits, 40, B, ns, seed=77)
     z = torch.tensor(workloads.slots(w), dtype=torch.float64)
     idx = torch.arange(B, dtype=torch.int64) * 5 + 3
     if pinned:

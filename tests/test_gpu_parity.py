@@ -274,9 +274,9 @@ def _check_whole(w, ct, zinc, z, idx, rows, seed):
         assert np.array_equal(got[b], ref), (b, zinc)
 
 
-# rows compared in full: the first and last ciphertext of the call, two in
-# between, and at N = 2^14 both sides of the boundary between the call's two
-# launches (prep scratch of 256 MiB: 2048 ciphertexts per launch)
+# rows compared in full: the first and last ciphertext of the call and two
+# in between (every workload's call is one launch pair: up to 512 MiB of
+# prepared words; launch boundaries are checked in test_gpu_ragged.py)
 WHOLE_ROWS = {"batched": {False: (0, 255, 256, 1023), True: (0, 255, 256, 1023)},
               "throughput": {False: (0, 2047, 2048, 4095), True: (0, 2047, 2048, 4095)},
               "large": {False: (511,), True: (0,)}}

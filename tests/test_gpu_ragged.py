@@ -83,10 +83,11 @@ def test_encrypt_ragged_matches_oracle_and_padded(log_n, bits, ld):
 
 
 def test_encrypt_ragged_two_launches():
-    # N = 2^15 holds at most 1024 ciphertexts per launch, so 1030 run as two
-    # equal launches of 515: rows on both sides of the boundary are checked
+    # N = 2^15 holds at most 2048 ciphertexts per launch (512 MiB of prepared
+    # words), so 2050 run as two equal launches of 1025: rows on both sides of
+    # the boundary are checked
     ctx, sk, pk, zc = ring(15, (55, 60), 55)
-    B, half = 1030, 1 << 14
+    B, half = 2050, 1 << 14
     rng = np.random.default_rng(3)
     counts = rng.integers(0, half + 1, B).astype(np.int32)
     stride = int(counts.max())
@@ -96,7 +97,7 @@ def test_encrypt_ragged_two_launches():
     idx = torch.arange(B, dtype=torch.int64, device="cuda:0")
     cz = api.zinc_encrypt_ragged(ctx, zc, zd, nd, 8, idx)
     api.zn_sync_status(ctx)
-    for b in (0, 514, 515, B - 1):
+    for b in (0, 1024, 1025, B - 1):
         k = int(counts[b])
         one = api.zinc_encrypt(ctx, zc, torch.tensor(z[b:b + 1, :k], device="cuda:0"), 8, idx[b:b + 1])
         assert torch.equal(cz[b:b + 1], one), b
