@@ -3,9 +3,10 @@
 // the modulus-switched vanilla encryption (zn_encrypt_ms.cu) and the BFV / BGV
 // encryptions and their Zinc forms (zn_encrypt_int.cu).
 //
-// A unit is one RNS limb (or output half of one) of one ciphertext.  Its two
-// transform inputs come from functors v0(k), v1(k) returning the residue of
-// coefficient k in [0, 2q):
+// A unit is one RNS limb of one ciphertext (N <= 2^13 here; the cluster
+// units at 2^14 and 2^15, zn_pair.cuh and zn_quarter.cuh, take the same
+// functors).  Its two transform inputs come from functors v0(k), v1(k)
+// returning the residue of coefficient k in [0, 2q):
 //   vanilla shape:  c0 = k0 * NTT(u) + NTT(v0),   c1 = k1 * NTT(u) + NTT(v1)
 //   Zinc shape:     c0 = z0 + NTT(v0),            c1 = z1 + NTT(v1)
 // with the schedules of the plain units (zn_encrypt_unit.cuh): radix 2^KM,
@@ -31,25 +32,6 @@ __device__ __forceinline__ void gen_val_top(u64* sm, int t, int nt, V& v, u64 q,
     bfly<RELAX>(x, y, w1, q);
     sm[swz<LOGN, KM>(k)] = x;
     sm[swz<LOGN, KM>(k + H)] = y;
-  }
-}
-
-template <int LOGH, int KM, class V>
-__device__ __forceinline__ void gen_val_half(u64* sm, int t, int nt, int h, V& v, u64 q, u64 w1, u64 w1s) {
-  constexpr int HALF = 1 << LOGH;
-  for (int k = t; k < HALF; k += nt) sm[swz<LOGH, KM>(k)] = first_stage(v(k), v(k + HALF), h, w1, w1s, q);
-}
-
-template <int LOGH, int KM, bool RELAX, class V>
-__device__ __forceinline__ void gen_val_half2(u64* sm, int t, int nt, int h, V& v, u64 q, ulonglong2 w1,
-                                              ulonglong2 w2) {
-  constexpr int HALF = 1 << LOGH, Q2 = HALF / 2;
-  for (int k = t; k < Q2; k += nt) {
-    u64 x = first_stage(v(k), v(k + HALF), h, w1.x, w1.y, q);
-    u64 y = first_stage(v(k + Q2), v(k + Q2 + HALF), h, w1.x, w1.y, q);
-    bfly<RELAX>(x, y, w2, q);
-    sm[swz<LOGH, KM>(k)] = x;
-    sm[swz<LOGH, KM>(k + Q2)] = y;
   }
 }
 
@@ -117,44 +99,5 @@ __device__ __forceinline__ void fn_unit_q(const ulonglong2* tw, u64 q, const FnL
   ntt_chain<LOGN, LOGPER, HI, RELAX, decltype(st_1), KM, true, KM == 3>(sm, t, tw, 1, q, st_1);
 }
 
-// Output half h, N = 2^(LOGH+1): the generators run the first stage
-// (distance N/2) for the half; o's outputs and keys point at the half, o.u
-// and the functors index the whole ring.
-template <int LOGH, int LOGPER, bool RELAX, int KM, bool ZINC, bool STREAM, class V0, class V1>
-__device__ __forceinline__ void fn_half_unit_q(const ulonglong2* tw, u64 q, int h, const FnLimb& o, const V0& v0,
-                                               const V1& v1, u64* sm, int t) {
-  using S = NttShape<LOGH, LOGPER>;
-  constexpr bool RAW = !RELAX || 4 + 2 * LOGH + 2 <= 32;
-  constexpr bool TOP = KM == 3 && LOGH % 3 == 1;
-  constexpr int HI = TOP ? LOGH - 1 : LOGH;
-  const ulonglong2 w1p = __ldg(tw + 1);
-  const int tmul = 2 + h;
-  u64* c0 = o.c0;
-  u64* c1 = o.c1;
-  const u64* k0 = o.k0;
-  const u64* k1 = o.k1;
-  auto sum = [&](u64 a, u64 x) { return RAW ? reduce_sum<RELAX>(a + x, q) : reduce4(a + x, q); };
-  if constexpr (!ZINC) {
-    const u64* k0s = o.k0s;
-    const u64* k1s = o.k1s;
-    if constexpr (TOP) gen_i8_half2<LOGH, KM, RELAX, true>(sm, t, S::T, h, o.u, q, w1p, __ldg(tw + tmul), __ldg(tw + 5 - tmul));
-    else gen_i8_half<LOGH, KM, true>(sm, t, S::T, h, o.u, q, w1p.x, w1p.y);
-    auto st_u = [&](int idx, u64 uh) {
-      c0[idx] = mul_shoup(uh, __ldg(k0 + idx), __ldg(k0s + idx), q);
-      c1[idx] = mul_shoup(uh, __ldg(k1 + idx), __ldg(k1s + idx), q);
-    };
-    ntt_chain<LOGH, LOGPER, HI, RELAX, decltype(st_u), KM, true, KM == 3>(sm, t, tw, tmul, q, st_u);
-    __syncthreads();
-  }
-  if constexpr (TOP) gen_val_half2<LOGH, KM, RELAX>(sm, t, S::T, h, v0, q, w1p, __ldg(tw + tmul));
-  else gen_val_half<LOGH, KM>(sm, t, S::T, h, v0, q, w1p.x, w1p.y);
-  auto st_0 = [&](int idx, u64 x) { put_ct<STREAM>(c0 + idx, sum(ZINC ? __ldg(k0 + idx) : c0[idx], x)); };
-  ntt_chain<LOGH, LOGPER, HI, RELAX, decltype(st_0), KM, RAW, KM == 3>(sm, t, tw, tmul, q, st_0);
-  __syncthreads();
-  if constexpr (TOP) gen_val_half2<LOGH, KM, RELAX>(sm, t, S::T, h, v1, q, w1p, __ldg(tw + tmul));
-  else gen_val_half<LOGH, KM>(sm, t, S::T, h, v1, q, w1p.x, w1p.y);
-  auto st_1 = [&](int idx, u64 x) { put_ct<STREAM>(c1 + idx, sum(ZINC ? __ldg(k1 + idx) : c1[idx], x)); };
-  ntt_chain<LOGH, LOGPER, HI, RELAX, decltype(st_1), KM, RAW, KM == 3>(sm, t, tw, tmul, q, st_1);
-}
 
 }  // namespace zn

@@ -127,25 +127,6 @@ __device__ __forceinline__ void int_unit_q(const DevParams& P, const IntArgs& A,
   fn_unit_q<LOGN, LOGPER, RELAX, KM, ZINC, false>(P.twp + (size_t)i * N, P.q[i], o, v0, v1, sm, t);
 }
 
-template <int LOGH, int LOGPER, bool RELAX, int KM, bool BGV, bool ZINC>
-__device__ __forceinline__ void int_half_unit_q(const DevParams& P, const IntArgs& A, int i, int h, size_t b, u64* sm,
-                                                int t) {
-  constexpr int N = 2 << LOGH, HALF = 1 << LOGH;
-  const int L = P.L;
-  const size_t off = (size_t)h * HALF;
-  FnLimb o;
-  o.c0 = A.out + (b * 2 * L + i) * N + off;
-  o.c1 = o.c0 + (size_t)L * N;
-  o.k0 = A.key + (size_t)i * N + off;
-  o.k1 = o.k0 + (size_t)L * N;
-  o.k0s = ZINC ? nullptr : A.keys + (size_t)i * N + off;
-  o.k1s = ZINC ? nullptr : o.k0s + (size_t)L * N;
-  o.u = A.small + b * 3 * N;
-  IntV0<BGV> v0;
-  IntV1<BGV> v1;
-  int_inputs<BGV, ZINC>(P, A, i, b, N, v0, v1);
-  fn_half_unit_q<LOGH, LOGPER, RELAX, KM, ZINC, false>(P.twp + (size_t)i * N, P.q[i], h, o, v0, v1, sm, t);
-}
 
 // N = 2^15: output quarter j of prime i on a four-CTA cluster (zn_quarter.cuh).
 template <bool RELAX, bool BGV, bool ZINC>
@@ -231,16 +212,6 @@ __global__ void __launch_bounds__(NttShape<LOGN, LOGPER>::T, MINB) k_encrypt_int
   else int_unit_q<LOGN, LOGPER, false, KM, BGV, ZINC>(P, A, i, b, sm, threadIdx.x);
 }
 
-// grid (2L, B), or (B, 2L) when A.swap; unit 2i + h is output half h of prime i
-template <int LOGH, int LOGPER, int MINB, int KM, bool BGV, bool ZINC>
-__global__ void __launch_bounds__(NttShape<LOGH, LOGPER>::T, MINB) k_encrypt_int_half(DevParams P, IntArgs A) {
-  extern __shared__ u64 sm[];
-  const int u = A.swap ? blockIdx.y : blockIdx.x;
-  const size_t b = A.swap ? blockIdx.x : blockIdx.y;
-  const int i = u >> 1, h = u & 1;
-  if (P.q[i] < kRelaxLimit) int_half_unit_q<LOGH, LOGPER, true, KM, BGV, ZINC>(P, A, i, h, b, sm, threadIdx.x);
-  else int_half_unit_q<LOGH, LOGPER, false, KM, BGV, ZINC>(P, A, i, h, b, sm, threadIdx.x);
-}
 
 // ------------------------------------------------------------- decoding
 // x_i = coefficient residues of c0 + c1 s.  With Q/q_i and y_i = (Q/q_i)^-1 mod q_i:
@@ -335,17 +306,6 @@ static cudaError_t int_full(const DevParams& P, const IntArgs& A, uint32_t batch
   return cudaGetLastError();
 }
 
-template <int LOGH, int LOGPER, int MINB, int KM, bool BGV, bool ZINC>
-static cudaError_t int_half(const DevParams& P, const IntArgs& A, uint32_t batch, cudaStream_t st) {
-  using S = NttShape<LOGH, LOGPER>;
-  const size_t smem = sizeof(u64) * S::N;
-  auto kern = k_encrypt_int_half<LOGH, LOGPER, MINB, KM, BGV, ZINC>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  const dim3 grid = A.swap ? dim3(batch, 2 * P.L) : dim3(2 * P.L, batch);
-  kern<<<grid, S::T, smem, st>>>(P, A);
-  return cudaGetLastError();
-}
 
 template <bool BGV, bool ZINC>
 static cudaError_t int_pair(const DevParams& P, const IntArgs& A, uint32_t batch, cudaStream_t st) {

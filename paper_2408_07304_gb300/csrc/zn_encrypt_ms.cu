@@ -14,8 +14,10 @@
 // u, the key product and an inverse transform back to coefficients (r_j).
 //
 // Kernels: k_ms_special (one block per component and ciphertext; N = 2^15 as
-// two half blocks plus k_ms_special_top), then k_encrypt_ms (the data primes,
-// in the launch shapes of the plain encryption's radix-8 kernels).
+// two half blocks plus k_ms_special_top), then the data primes in the launch
+// shapes of the plain encryption's default kernels: k_encrypt_ms (radix 8,
+// N <= 2^13), k_encrypt_ms_pair (two-CTA clusters, 2^14), k_encrypt_ms_quarter
+// (four-CTA clusters, 2^15).
 #include "zn_encrypt_fn.cuh"
 #include "zn_pair.cuh"
 #include "zn_quarter.cuh"
@@ -216,30 +218,6 @@ __device__ __forceinline__ void ms_unit_q(const DevParams& P, const MsArgs& A, i
   fn_unit_q<LOGN, LOGPER, RELAX, KM, false, true>(P.twp + (size_t)i * N, q, o, v0, v1, sm, t);
 }
 
-// Output half h of data prime i, N = 2^(LOGH+1).  Streaming stores for the
-// finished words: at N = 2^14 they took the kernel's DRAM traffic from 1.84x
-// to 1.14x of its bytes (the lazily reduced key products and the per-
-// ciphertext scratch stay in L2) and its launch 4.62 -> 4.57 ms per 1024.
-template <int LOGH, int LOGPER, bool RELAX, int KM>
-__device__ __forceinline__ void ms_half_unit_q(const DevParams& P, const MsArgs& A, int i, int h, size_t b, u64* sm,
-                                               int t) {
-  constexpr int N = 2 << LOGH, HALF = 1 << LOGH;
-  const int Ld = P.L - 1;
-  const u64 q = P.q[i];
-  const size_t off = (size_t)h * HALF;
-  FnLimb o;
-  o.c0 = A.out + (b * 2 * Ld + i) * N + off;
-  o.c1 = o.c0 + (size_t)Ld * N;
-  o.k0 = A.keyms + (size_t)i * N + off;
-  o.k1 = o.k0 + (size_t)Ld * N;
-  o.k0s = o.k0 + 2 * (size_t)Ld * N;
-  o.k1s = o.k1 + 2 * (size_t)Ld * N;
-  o.u = A.small + b * 3 * N;
-  const MsVal v0{A.d + b * 2 * N, A.m + b * N, q, P.mu[i], A.pinv[i], A.pinvs[i], A.kc0[i]};
-  const MsVal v1{A.d + b * 2 * N + N, nullptr, q, P.mu[i], A.pinv[i], A.pinvs[i], A.kc1[i]};
-  fn_half_unit_q<LOGH, LOGPER, RELAX, KM, false, true>(P.twp + (size_t)i * N, q, h, o, v0, v1, sm, t);
-}
-
 // grid (L-1, B), or (B, L-1) when A.swap
 template <int LOGN, int LOGPER, int MINB, int KM>
 __global__ void __launch_bounds__(NttShape<LOGN, LOGPER>::T, MINB) k_encrypt_ms(DevParams P, MsArgs A) {
@@ -253,17 +231,6 @@ __global__ void __launch_bounds__(NttShape<LOGN, LOGPER>::T, MINB) k_encrypt_ms(
     }
   }
   ms_unit_q<LOGN, LOGPER, false, KM>(P, A, i, b, sm, threadIdx.x);
-}
-
-// grid (2(L-1), B), or (B, 2(L-1)) when A.swap; unit 2i + h is output half h of prime i
-template <int LOGH, int LOGPER, int MINB, int KM>
-__global__ void __launch_bounds__(NttShape<LOGH, LOGPER>::T, MINB) k_encrypt_ms_half(DevParams P, MsArgs A) {
-  extern __shared__ u64 sm[];
-  const int u = A.swap ? blockIdx.y : blockIdx.x;
-  const size_t b = A.swap ? blockIdx.x : blockIdx.y;
-  const int i = u >> 1, h = u & 1;
-  if (P.q[i] < kRelaxLimit) ms_half_unit_q<LOGH, LOGPER, true, KM>(P, A, i, h, b, sm, threadIdx.x);
-  else ms_half_unit_q<LOGH, LOGPER, false, KM>(P, A, i, h, b, sm, threadIdx.x);
 }
 
 // N = 2^15: output quarter j of data prime i on a four-CTA cluster
@@ -433,18 +400,6 @@ static cudaError_t data_full(const DevParams& P, const MsArgs& A, uint32_t batch
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   const dim3 grid = A.swap ? dim3(batch, P.L - 1) : dim3(P.L - 1, batch);
-  kern<<<grid, S::T, smem, st>>>(P, A);
-  return cudaGetLastError();
-}
-
-template <int LOGH, int LOGPER, int MINB, int KM>
-static cudaError_t data_half(const DevParams& P, const MsArgs& A, uint32_t batch, cudaStream_t st) {
-  using S = NttShape<LOGH, LOGPER>;
-  const size_t smem = sizeof(u64) * S::N;
-  auto kern = k_encrypt_ms_half<LOGH, LOGPER, MINB, KM>;
-  cudaError_t e = set_smem(kern, smem);
-  if (e != cudaSuccess) return e;
-  const dim3 grid = A.swap ? dim3(batch, 2 * (P.L - 1)) : dim3(2 * (P.L - 1), batch);
   kern<<<grid, S::T, smem, st>>>(P, A);
   return cudaGetLastError();
 }
