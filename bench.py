@@ -44,18 +44,14 @@ UNIT = "encryptions/s"
 # is unchanged and selected.
 NCU_TRAFFIC_PER_CT = {
     ("throughput", "k_encrypt_pair<vanilla,2-CTA cluster,radix-8,3 blocks/SM>"): (99.60192e6 + 1098.81e6) / 512,
-    ("throughput", "k_encrypt_pair<Zinc,2-CTA cluster,radix-8,3 blocks/SM>"): (79.885824e6 + 1031.35e6) / 512,
-    ("paper", "k_encrypt_quarter<vanilla,4-CTA cluster,radix-8,3 blocks/SM>"): (51.651072e6 + 482.746624e6) / 64,
-    ("paper", "k_encrypt_quarter<Zinc,4-CTA cluster,radix-8,3 blocks/SM>"): (37.274112e6 + 479.471616e6) / 64,
+    ("paper", "k_encrypt_quarter<vanilla,4-CTA cluster,radix-8,3 blocks/SM>"): (51.4816e6 + 481.318912e6) / 64,
 }
 # Busy fraction of the SM's integer multiply-add pipe (ncu
 # sm__pipe_fmaheavy_cycles_active, which is also the kernel's
-# sm__throughput: the busiest unit of the SM) in the same capture.
+# sm__throughput: the busiest unit of the SM) in the same captures.
 NCU_INT_PIPE = {
     ("throughput", "k_encrypt_pair<vanilla,2-CTA cluster,radix-8,3 blocks/SM>"): 0.7209,
-    ("throughput", "k_encrypt_pair<Zinc,2-CTA cluster,radix-8,3 blocks/SM>"): 0.7019,
-    ("paper", "k_encrypt_quarter<vanilla,4-CTA cluster,radix-8,3 blocks/SM>"): 0.7405,
-    ("paper", "k_encrypt_quarter<Zinc,4-CTA cluster,radix-8,3 blocks/SM>"): 0.7111,
+    ("paper", "k_encrypt_quarter<vanilla,4-CTA cluster,radix-8,3 blocks/SM>"): 0.7392,
 }
 VARIANT_KERNEL = {6: "k_encrypt_pair<{mode},2-CTA cluster,radix-8,3 blocks/SM>",
                   7: "k_encrypt_pair<{mode},2-CTA cluster,radix-8,3 blocks/SM,ciphertext-major>"}
