@@ -89,3 +89,10 @@ def test_alloc_fault_injector_arguments(built):
     with pytest.raises(api.ZincError) as e:
         api.zn_inject_alloc_failures(-1)
     assert e.value.status == api.ZN_EINVAL
+
+
+def test_wait_probe_arguments_without_gpu(built):
+    # a null context is refused before any device call
+    lib = api.lib()
+    assert lib.zn_probe_wait_timeout(None, 1, None) == api.ZN_EINVAL
+    assert lib.zn_probe_wait_timeout(None, 0, None) == api.ZN_EINVAL
